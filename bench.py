@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput of the whole PROJECTION hot path (Algorithm 2 + Section 5.1 EM)
+on one GB300, on seeded synthetic planted-motif inputs.
+
+A step is one motif search over one instance: pack-resident 2-bit input ->
+Philox positions, projection, hashing and bucket counts for all m trials ->
+enriched-bucket lists -> theta^0 -> EM for every enriched bucket -> FP64
+ranking, consensus, sites.  Default workload: planted (15,4), t = 20 x n = 600,
+k = 7, s = 4, m = 172 (the Section 5 bound at q = 0.95), 5 EM iterations,
+pseudocount 0.25.
+
+Prints one JSON line.  `value` is EM l-mer x PWM scores per second over the
+whole step (scores per step = x * C * (em_iters + 1), C = enriched buckets);
+hashes/s and instances/s are reported beside it.
+
+--impl reference times the CPU oracle (the FP64 statement of the method) on
+the same workload: all m trials hashed, EM on a deterministic candidate
+sample, time extrapolated linearly in the candidate count.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from synth import instance_for_config  # noqa: E402
+
+METRIC = "l-mer hashes/s, EM l-mer×PWM scores/s; batched instances/s vs plain at same motif"
+UNIT = "scores/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+SMS = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+FLUSH_BYTES = 512 << 20  # > 2x the 129 MB L2
+
+
+def resolve(inst, p):
+    """k, s, m as the library resolves them (0 = Section 5 choice)."""
+    import paper_1605_06904_gb300 as P
+    return P.projection_default_params(inst.lens, inst.l, inst.d, p.get("k", 0), p.get("s", 0),
+                                       p.get("m", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "bf16_tflops": FALLBACK_BF16_TFLOPS}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+
+def oracle_step(inst, k, s, m, seed, iters, beta, max_sample=6000, nthreads=None):
+    """One oracle step on a bounded sample; returns (seconds for the whole step,
+    extrapolated; details)."""
+    import oracle as O
+    nthreads = nthreads or os.cpu_count() or 1
+    codes = O.encode(inst.ascii)
+    off = inst.seq_off
+    t0 = time.perf_counter()
+    h = O.hash_trials(codes, off, inst.l, k, s, seed, 0, m)
+    t_hash = time.perf_counter() - t0
+    C = int(h["cand_key"].size)
+    stride = max(1, math.ceil(C / max_sample))
+    idx = np.arange(0, C, stride)
+    t0 = time.perf_counter()
+    bg = O.background(codes)
+    th0 = np.stack([O.theta0(codes, off, inst.l,
+                             h["members"][h["cand_off"][c]:h["cand_off"][c + 1]], beta)
+                    for c in idx]) if idx.size else np.zeros((0, inst.l, 4))
+    t_th0 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    if idx.size:
+        O.em(codes, off, inst.l, bg, th0, iters, beta, nthreads=nthreads)
+    t_em = time.perf_counter() - t0
+    scale = C / max(1, idx.size)
+    total = t_hash + (t_th0 + t_em) * scale
+    return total, {"C": C, "sample": int(idx.size), "stride": stride, "t_hash": t_hash,
+                   "t_theta0": t_th0, "t_em": t_em, "threads": nthreads}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    inst = instance_for_config(args.config, 0)
+    p = dict(inst.params)
+    import oracle as O
+    k, s, m = O.default_params(inst.lens, inst.l, inst.d, p.get("k", 0), p.get("s", 0),
+                               p.get("m", 0))
+    iters, beta, seed = p["em_iters"], p["beta"], 1000 + args.config
+    for _ in range(args.warmup):
+        oracle_step(inst, k, s, m, seed, iters, beta, max_sample=args.ref_sample)
+    times, det = [], None
+    for _ in range(args.steps):
+        tt, det = oracle_step(inst, k, s, m, seed, iters, beta, max_sample=args.ref_sample)
+        times.append(tt)
+    T = float(np.mean(times))
+    x = inst.n_lmers
+    scores = x * det["C"] * (iters + 1)
+    value = scores / T
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": T * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(args, inst, k, s, m, iters, beta),
+        "hashes_per_s": m * x / T, "instances_per_s": 1.0 / T,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": det["threads"], "kind": "oracle",
+                         "sample": sample_text(det, m)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def sample_text(det, m):
+    return (f"all {m} trials hashed; theta0 + EM on every {det['stride']}th candidate "
+            f"({det['sample']} of {det['C']}) on {det['threads']} threads, that time scaled "
+            f"by C/sample")
+
+
+def config_dict(args, inst, k, s, m, iters, beta):
+    return {"workload": f"planted({inst.l},{inst.d}) t={inst.t} n={int(inst.lens[0])} k={k} s={s} "
+                        f"m={m} em_iters={iters} pseudocount={beta}",
+            "config_index": args.config, "t": inst.t, "n": int(inst.lens[0]), "l": inst.l,
+            "d": inst.d, "k": k, "s": s, "m": m, "em_iters": iters, "x_lmers": inst.n_lmers,
+            "precision": args.precision, "l2": "flushed between steps (512 MB write)",
+            "parallelism": f"independent instances, one per GPU"}
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--precision", choices=["fp32", "bf16split"], default="fp32")
+    ap.add_argument("--ref-sample", type=int, default=6000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1605_06904_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    inst = instance_for_config(args.config, rank)  # weak scaling: one instance per GPU
+    p = dict(inst.params)
+    k, s, m = resolve(inst, p)
+    iters, beta, seed = p["em_iters"], p["beta"], 1000 + args.config
+    prec = P.PROJ_EM_FP32 if args.precision == "fp32" else P.PROJ_EM_BF16_SPLIT
+    off = inst.seq_off
+    x = inst.n_lmers
+
+    ascii_host = torch.from_numpy(inst.ascii).pin_memory()
+    packed = P.projection_pack(ascii_host.to(dev))  # resident input for the device leg
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return P.projection_find_packed(packed, off, inst.l, inst.d, k, s, m, seed=seed,
+                                        em_iters=iters, pseudocount=beta, precision=prec)
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+    C = res["n_candidates"]
+
+    # ---- timed region: K steps, L2 flushed between steps, per-step events
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    P.projection_trace_enable(True)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        res = step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    P.projection_trace_enable(False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    T = float(np.sum(step_ms)) / 1e3
+
+    scores_step = x * C * (iters + 1)
+    em_name = "em_fp32" if prec == P.PROJ_EM_FP32 else "em_tc"
+    em_ms, em_launches = P.projection_trace_read(em_name)
+    _, all_launches = P.projection_trace_read("")
+
+    tot = torch.tensor([scores_step * args.steps, m * x * args.steps, args.steps, 0.0],
+                       dtype=torch.float64, device=dev)
+    tmax = torch.tensor([T], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    T_job = float(tmax.item())
+    value = float(tot[0].item()) / T_job
+    hashes = float(tot[1].item()) / T_job
+    inst_rate = float(tot[2].item()) / T_job
+
+    # ---- roofline of the dominant kernel (EM)
+    pk, pk_kind = peaks()
+    if prec == P.PROJ_EM_FP32:
+        # algorithmic FP32 operations: per score l gather-adds (E) + exp and sum
+        # (2) + l weighted adds (M-step launches only)
+        ops = args.steps * x * C * (iters * (2 * inst.l + 2) + (inst.l + 2))
+        achieved = ops / (em_ms / 1e3) / 1e12 if em_ms > 0 else None
+        peak = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "em_fp32_kernel", "launches": em_launches,
+                "avg_launch_ms": em_ms / max(1, em_launches),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (derived)"}
+    else:
+        k_pad = 16 * math.ceil(4 * inst.l / 16)
+        flops = args.steps * x * C * (iters * 2 * 2 * k_pad * 2 + 2 * 2 * k_pad)
+        achieved = flops / (em_ms / 1e3) / 1e12 if em_ms > 0 else None
+        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "em_tc_kernel", "launches": em_launches,
+                "avg_launch_ms": em_ms / max(1, em_launches),
+                "peak_source": f"bf16_tflops_sustained ({pk_kind})"}
+
+    # ---- end to end through the public API: host ASCII in, result out
+    e2e_times = []
+    for i in range(max(3, min(args.steps, 10))):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r2 = P.projection_find(ascii_host, off, inst.l, inst.d, k, s, m, seed=seed,
+                               em_iters=iters, pseudocount=beta, precision=prec)
+        e2e_times.append(time.perf_counter() - t0)
+    assert r2["consensus"] == res["consensus"]
+    e2e_T = float(np.mean(e2e_times))
+    h2d = int(inst.ascii.size) + 2 * 4 * (inst.t + 1)
+    d2h = 8 + 16 + 8 + 4 * inst.t + inst.l + 4 + 16 * inst.l + 8 + 4 + 4
+    e2e = {"value": scores_step / e2e_T, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_T * 1e3}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": T_job * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == P.PROJ_EM_FP32 else "bf16-split",
+        "data": "synthetic", "config": config_dict(args, inst, k, s, m, iters, beta),
+        "hashes_per_s": hashes, "instances_per_s": inst_rate,
+        "n_candidates": C, "scores_per_step": scores_step,
+        "motif_found": res["consensus"], "motif_planted": inst.motif,
+        "wall_ms_per_step": wall * 1e3 / args.steps,
+        "roofline": roof, "clocks": clk, "e2e": e2e,
+        "gpu_launches": all_launches / max(1, args.steps),
+        "cpu_baseline": None,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        tt, det = oracle_step(inst, k, s, m, seed, iters, beta, max_sample=args.ref_sample)
+        line["cpu_baseline"] = {"value": scores_step / tt, "unit": UNIT, "cores": det["threads"],
+                                "kind": "oracle", "sample": sample_text(det, m),
+                                "seconds_per_step_extrapolated": tt}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

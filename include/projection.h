@@ -1,0 +1,226 @@
+/*
+ * projection.h -- C ABI of the GB300 (sm_103a) PROJECTION motif finder.
+ *
+ * The method is PROJECTION (Buhler & Tompa) as restated by Clemente, Cabarle &
+ * Adorna, "PROJECTION Algorithm for Motif Finding on GPUs" (arXiv 1605.06904):
+ * for each of m random trials, project every l-mer of the t input sequences
+ * onto k of its l positions (Section 5, random projection h_k), hash the
+ * projected k-mer in base 4 (Section 6, A:0 C:1 T:2 G:3, most significant
+ * digit first) into 4^k buckets (Algorithm 2 step 2c), keep the buckets holding
+ * at least s l-mers (Algorithm 2 step 3; Section 6), and refine each enriched
+ * bucket's position weight matrix by EM (Section 5.1) under the
+ * one-occurrence-per-sequence model.
+ *
+ * Conventions for every call:
+ *   - Pointers named *_dev are device pointers on the current CUDA device;
+ *     every other pointer is host memory.  The caller owns all buffers passed
+ *     in; the library never frees them.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device work
+ *     is enqueued on it; calls return once their work is enqueued unless the
+ *     description says they synchronise.
+ *   - Scratch memory is allocated with cudaMallocAsync on `stream` and freed
+ *     on the same stream before the call returns.
+ *   - Return value: PROJ_OK (0) or a negative PROJ_E* status.  No C++
+ *     exception crosses this boundary.  projection_last_error() returns a
+ *     human-readable message for the calling thread's last failure.
+ *   - Sequences are given in linear form (Section 6): one concatenated buffer
+ *     plus seq_off[t+1], sequence i occupying [seq_off[i], seq_off[i+1]).
+ *     Every sequence must hold at least one l-mer (n_i >= l).  The concatenated
+ *     length and the number of l-mers x = sum_i (n_i - l + 1) are below 2^31.
+ *   - Global l-mer id: l-mer S_{i,j} (0-based start j in sequence i) has id
+ *     sum_{i'<i} (n_{i'} - l + 1) + j.
+ *   - PWMs are float [l][4] in code order A, C, T, G; columns sum to 1.
+ *   - Limits: 1 <= k <= l <= 32, k <= 10, 1 <= t.
+ */
+#ifndef PROJECTION_H
+#define PROJECTION_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PROJ_OK 0
+#define PROJ_EINVAL (-1)    /* an argument is out of range */
+#define PROJ_ENOMEM (-2)    /* a device allocation failed */
+#define PROJ_ECAPACITY (-3) /* a caller buffer is too small (needed size written back) */
+#define PROJ_ECUDA (-4)     /* a CUDA runtime call failed */
+#define PROJ_ETIMEOUT (-5)  /* a bounded device wait expired */
+#define PROJ_EBADCHAR (-6)  /* the input holds a character other than A/C/G/T */
+#define PROJ_ENOTSUP (-7)   /* parameters outside what the kernels implement */
+
+/* ---- EM arithmetic ------------------------------------------------------ */
+#define PROJ_EM_FP32 0       /* scores, exp and M-step sums in FP32 on CUDA cores */
+#define PROJ_EM_BF16_SPLIT 1 /* scoring and M-step contractions on tcgen05 tensor cores,
+                                BF16 hi+lo split operands, FP32 accumulation */
+
+/* Message of the calling thread's most recent failure ("" if none). */
+const char *projection_last_error(void);
+
+/* ---- host-side helpers (no device work) -------------------------------- */
+
+/* Number of 32-bit words projection_pack writes for `total_bases` bases:
+ * ceil(total_bases / 16).  Base b sits in word b/16 at bits 2*(b%16)..+1. */
+int64_t projection_packed_words(int64_t total_bases);
+
+/* Algorithm 2 step 1 ("if not specified") with the Section 5 choices: an
+ * input of 0 in *k, *s or *m is replaced by k = l-d-1,
+ * s = max(3, ceil(2 x / 4^k)) (twice the mean bucket size, floored at the
+ * paper's empirical 3), m = ceil(log(1-q) / log B(s)) with q = 0.95,
+ * t_hat = t, p_hat = C(l-d,k)/C(l,k), B(s) = P[Binomial(t_hat, p_hat) < s].
+ * lens[t] are the sequence lengths.  Returns PROJ_EINVAL if no valid value
+ * exists (e.g. k > l-d makes p_hat = 0) or the bound exceeds 2^24 trials. */
+int projection_default_params(int t, const int64_t *lens, int l, int d, int *k, int *s, int *m);
+
+/* ---- step a1: pack (Section 6, linear 2-bit form) ----------------------- */
+
+/* Packs `total_bases` ASCII bases (A/C/G/T, either case) into 2-bit codes
+ * A0 C1 T2 G3, ceil(total_bases/16) words, high bits of the last word zero.
+ * *bad_index_dev (int64, device) receives -1, or the smallest index of a
+ * character that is not A/C/G/T (its word is then unspecified). */
+int projection_pack(const uint8_t *ascii_dev, int64_t total_bases, uint32_t *packed_dev,
+                    int64_t *bad_index_dev, void *stream);
+
+/* Background model of Section 5.1 (column 0 of theta): the 0-order base
+ * frequencies of the whole packed input, as double[4] in code order; a base
+ * that never occurs is counted once.  Writes bg_dev[0..3]. */
+int projection_background(const uint32_t *packed_dev, int64_t total_bases, double *bg_dev,
+                          void *stream);
+
+/* ---- step a2: projection positions (Algorithm 2 step 2a) ---------------- */
+
+/* For trials trial_begin .. trial_begin+n_trials-1 writes the k projected
+ * positions (0-based, increasing) to pos_dev[n][k] (uint8).  The l-k excluded
+ * positions are distinct, chosen by a partial Fisher-Yates shuffle of 0..l-1
+ * driven by Philox4x32-10 with key (seed lo, seed hi) and counter
+ * (trial lo, block, trial hi, 0); word w of the draw picks swap partner
+ * i + floor(u_w * (l - i) / 2^32). */
+int projection_positions(uint64_t seed, int64_t trial_begin, int64_t n_trials, int l, int k,
+                         uint8_t *pos_dev, void *stream);
+
+/* ---- steps a2-a5: project, hash, count, enrich (Algorithm 2 steps 2-3) -- */
+
+/* Runs trials trial_begin .. trial_begin+n_trials-1 in one pass.
+ *   packed_dev     2-bit input from projection_pack
+ *   seq_off        host int64[t+1] base offsets of the sequences
+ *   positions_in   host int32[k]: if not NULL every trial uses these projected
+ *                  positions instead of drawing them (worked examples, tests)
+ *   positions_out_dev  device uint8[n_trials][k] or NULL
+ *   counts_out_dev device uint32[n_trials][4^k] bucket sizes, or NULL
+ * Output: the enriched buckets (size >= s) of all trials in (trial, key)
+ * order, as a CSR list in caller buffers of capacity cap_cand / cap_members:
+ *   cand_trial_dev int32[cap_cand], cand_key_dev uint32[cap_cand],
+ *   cand_cnt_dev int32[cap_cand], cand_off_dev int64[cap_cand+1]
+ *   (members of candidate c are members_dev[cand_off[c] .. cand_off[c+1]),
+ *   members_dev int32[cap_members] global l-mer ids, ascending per candidate.
+ * totals_dev (int64[2], device) receives the full candidate and member counts
+ * even when they exceed the capacities; entries beyond a capacity are not
+ * written and the caller must retry with larger buffers.  Asynchronous. */
+int trial_hash(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l, int k, int s,
+               uint64_t seed, int64_t trial_begin, int64_t n_trials, const int32_t *positions_in,
+               uint8_t *positions_out_dev, uint32_t *counts_out_dev, int64_t cap_cand,
+               int64_t cap_members, int32_t *cand_trial_dev, uint32_t *cand_key_dev,
+               int32_t *cand_cnt_dev, int64_t *cand_off_dev, int32_t *members_dev,
+               int64_t *totals_dev, void *stream);
+
+/* ---- step a6: initial model theta^0 (Example 1, Figure 4) -------------- */
+
+/* theta0_dev[c][p][a] = (#members of candidate c with base a at position p
+ * + pseudocount) / (cnt_c + 4 pseudocount), for c < C, from the CSR list of
+ * trial_hash (cand_off_dev, members_dev). */
+int theta0_build(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
+                 const int64_t *cand_off_dev, const int32_t *members_dev, int64_t C,
+                 float pseudocount, float *theta0_dev, void *stream);
+
+/* ---- steps a7-a8: EM refinement (Section 5.1, OOPS) --------------------- */
+
+/* For each of C starting models theta0_dev[C][l][4] runs em_iters EM
+ * iterations and a final E-step.  With W_c[p][a] = log theta_c[p][a] -
+ * log bg[a] and r(i,j) = sum_p W_c[p][x_{i,j+p}]:
+ *   E-step: z(i,j) = exp(r(i,j)) / sum_j' exp(r(i,j'))   (per sequence)
+ *   M-step: theta[p][a] = (sum_{i,j} z(i,j) [x_{i,j+p} = a] + pseudocount)
+ *                         / (t + 4 pseudocount)
+ * theta_out_dev[C][l][4] receives the model after em_iters M-steps (it may
+ * alias theta0_dev) and loglik_dev[C] (double) the log-likelihood ratio of
+ * that model against the background,
+ *   LL = sum_i [ log sum_j exp r(i,j) - log(n_i - l + 1) ],
+ * per-sequence log-sum-exp in FP32, sum over sequences in FP64.
+ * bg_dev: double[4] from projection_background.  precision: PROJ_EM_FP32 or
+ * PROJ_EM_BF16_SPLIT.  pseudocount must be > 0. */
+int em_refine(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
+              const double *bg_dev, const float *theta0_dev, int64_t C, int em_iters,
+              float pseudocount, int precision, float *theta_out_dev, double *loglik_dev,
+              void *stream);
+
+/* ---- step a9: rank and finalise ----------------------------------------- */
+
+/* Picks the best candidate (largest loglik, FP64; a tie goes to the smaller
+ * index, i.e. the earlier (trial, key)) and, for its model theta_dev[best]:
+ *   sites_dev int32[t]   per sequence the first start maximising r(i,j),
+ *                        evaluated in FP64;
+ *   consensus_dev uint8[l] ASCII consensus, per column the base of largest
+ *                        weight, ties to the lowest code (A, C, T, G);
+ *   score_dev int32[1]   Score(s, DNA) of Section 2 for those sites;
+ *   best_dev int64[1]    the chosen candidate index (-1 when C == 0). */
+int projection_finalize(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
+                        const double *bg_dev, const float *theta_dev, const double *loglik_dev,
+                        int64_t C, int64_t *best_dev, int32_t *sites_dev, uint8_t *consensus_dev,
+                        int32_t *score_dev, void *stream);
+
+/* ---- whole path --------------------------------------------------------- */
+
+typedef struct {
+    int status;            /* PROJ_OK or the failing status */
+    int t, l, k, s, m;     /* resolved parameters */
+    int64_t n_candidates;  /* enriched buckets over all trials */
+    int64_t n_members;     /* l-mers in them */
+    int64_t win_index;     /* index of the winner in (trial, key) order, -1 if none */
+    int win_trial;
+    uint32_t win_key;
+    double loglik;         /* winner's log-likelihood ratio */
+    int score;             /* Score(s, DNA) of the winner's sites */
+    float *pwm;            /* [l][4], allocated by the library */
+    char *consensus;       /* l letters + NUL, allocated by the library */
+    int32_t *sites;        /* [t] 0-based starts, allocated by the library */
+} projection_result;
+
+/* The paper's problem statement (Algorithm 2: INPUT t sequences, l, n, d;
+ * OUTPUT motif): from host ASCII sequences in linear form (ascii[seq_off[t]],
+ * seq_off[t+1]) runs pack, k/s/m defaults (0 = derive), m trials of
+ * projection + hashing, theta^0 and EM for every enriched bucket, and ranking.
+ * Copies in, computes, copies the small result out, and synchronises
+ * `stream`.  `out` is filled on success and on failure (out->status); its
+ * arrays are released by projection_result_free. */
+int projection_find(const uint8_t *ascii, const int64_t *seq_off, int t, int l, int d, int k,
+                    int s, int m, uint64_t seed, int em_iters, float pseudocount, int precision,
+                    projection_result *out, void *stream);
+
+/* As projection_find, with the input already packed on the device. */
+int projection_find_packed(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
+                           int d, int k, int s, int m, uint64_t seed, int em_iters,
+                           float pseudocount, int precision, projection_result *out,
+                           void *stream);
+
+void projection_result_free(projection_result *r);
+
+/* ---- tracing (CUDA-event timers per kernel) ----------------------------- */
+
+/* on != 0: start recording a CUDA event pair around every kernel the library
+ * launches (on the stream it launches on) and clear earlier records; on == 0:
+ * stop recording.  Off by default; costs two event records per launch. */
+int projection_trace_enable(int on);
+
+/* Sums the records of kernels whose name starts with `prefix` ("" = all):
+ * *total_ms = summed device time, *launches = number of launches.  Waits for
+ * the recorded events.  Kernel names: pack, background, positions,
+ * hash_count, hash_scan, hash_fill, theta0, em_fp32, em_reduce, em_tc,
+ * finalize. */
+int projection_trace_read(const char *prefix, double *total_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PROJECTION_H */

@@ -1,0 +1,378 @@
+// Steps a6-a9: initial model theta^0 (Section 5.1, Example 1 / Figure 4),
+// OOPS EM refinement of every enriched bucket (Section 5.1), and the FP64
+// ranking and finalisation (Section 2's consensus and Score).
+//
+// FP32 path (PROJ_EM_FP32): one thread per candidate model; the threads of a
+// CTA walk the same l-mers in lockstep, so the l-mer's codes are warp-uniform
+// and the per-candidate tables W[4l][cand] and acc[4l][cand] in shared memory
+// are read and written without bank conflicts.  Per sequence the posterior
+// weights are accumulated against a running maximum (rescaled when it grows),
+// then normalised by the sequence's sum: the E- and M-steps of one iteration
+// read each l-mer once.  Sequences are split into G groups across CTAs when
+// there are too few candidates to fill the GPU; partial sums are reduced in a
+// fixed order, so results do not depend on timing.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace proj {
+
+int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const float *theta0,
+              int64_t C, int iters, float beta, float *theta_out, double *ll, cudaStream_t st);
+
+namespace {
+
+constexpr int kEmThreads = 64;  // candidates per CTA in the FP32 path
+
+// ---------------------------------------------------------------------------
+// theta^0: column frequencies of the bucket's l-mers plus pseudocount.
+// ---------------------------------------------------------------------------
+__global__ void theta0_kernel(const uint32_t *__restrict__ packed, int64_t nwords,
+                              const int32_t *__restrict__ seq_off,
+                              const int32_t *__restrict__ lmer_off, int t, int l,
+                              const int64_t *__restrict__ cand_off,
+                              const int32_t *__restrict__ members, int64_t C, float beta,
+                              float *__restrict__ theta0) {
+    extern __shared__ float cnt[];  // [4l][blockDim]
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t c = blockIdx.x * (int64_t)nt + tid;
+    const int L4 = 4 * l;
+    for (int q = 0; q < L4; ++q) cnt[q * nt + tid] = 0.f;
+    if (c >= C) return;
+    const int64_t e0 = cand_off[c], e1 = cand_off[c + 1];
+    for (int64_t e = e0; e < e1; ++e) {
+        const int g = members[e];
+        int lo = 0, hi = t - 1;  // last i with lmer_off[i] <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(lmer_off + mid) <= g) lo = mid; else hi = mid - 1;
+        }
+        const int64_t b0 = (int64_t)__ldg(seq_off + lo) + (g - __ldg(lmer_off + lo));
+        const uint64_t win = window64(packed, nwords, b0);
+        for (int p = 0; p < l; ++p) cnt[(p * 4 + (int)((win >> (2 * p)) & 3u)) * nt + tid] += 1.f;
+    }
+    const float den = (float)(e1 - e0) + 4.f * beta;
+    for (int q = 0; q < L4; ++q) theta0[c * L4 + q] = (cnt[q * nt + tid] + beta) / den;
+}
+
+// ---------------------------------------------------------------------------
+// One EM iteration (E-step + optional M-step) in FP32 for a tile of
+// candidates and one group of sequences.
+// ---------------------------------------------------------------------------
+struct EmParams {
+    const uint32_t *packed;
+    int64_t nwords;
+    const int32_t *seq_off;
+    int t, l, G;
+    const double *bg;
+    const float *theta_in;
+    float *theta_out;   // G == 1: final model
+    double *ll_out;     // G == 1: final LL
+    float *part_acc;    // G > 1: [G][C][4l]
+    double *part_ll;    // G > 1: [G][C]
+    int64_t C;
+    float beta;
+    int mstep;
+};
+
+template <int LMAX>
+__global__ void __launch_bounds__(kEmThreads) em_fp32_kernel(const EmParams P) {
+    extern __shared__ float sm[];
+    constexpr int NT = kEmThreads;
+    const int tid = threadIdx.x;
+    const int l = P.l, L4 = 4 * l;
+    float *Ws = sm;                 // [4l][NT]
+    float *acc = sm + L4 * NT;      // [4l][NT]
+    float *tot = sm + 2 * L4 * NT;  // [4l][NT]
+    const int64_t c = blockIdx.x * (int64_t)NT + tid;
+    const bool valid = c < P.C;
+    const int g = blockIdx.y;
+
+    float lbg[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) lbg[a] = (float)log(P.bg[a]);
+    for (int q = 0; q < L4; ++q) {
+        Ws[q * NT + tid] = valid ? logf(P.theta_in[c * L4 + q]) - lbg[q & 3] : 0.f;
+        tot[q * NT + tid] = 0.f;
+    }
+    double ll = 0.0;
+    const int i0 = (int)((int64_t)P.t * g / P.G), i1 = (int)((int64_t)P.t * (g + 1) / P.G);
+    for (int i = i0; i < i1; ++i) {
+        const int64_t base = P.seq_off[i];
+        const int ns = P.seq_off[i + 1] - P.seq_off[i] - l + 1;
+        for (int q = 0; q < L4; ++q) acc[q * NT + tid] = 0.f;
+        float m = -INFINITY, S = 0.f;
+        uint64_t win = window64(P.packed, P.nwords, base);
+        for (int j = 0; j < ns; ++j) {
+            if (j > 0) win = (win >> 2) | ((uint64_t)code_at(P.packed, P.nwords, base + j + 31) << 62);
+            float r = 0.f;
+#pragma unroll
+            for (int p = 0; p < LMAX; ++p)
+                if (p < l) r += Ws[(p * 4 + (int)((win >> (2 * p)) & 3u)) * NT + tid];
+            if (r > m) {
+                const float sc = __expf(m - r);  // 0 on the first l-mer
+                S *= sc;
+                if (P.mstep)
+                    for (int q = 0; q < L4; ++q) acc[q * NT + tid] *= sc;
+                m = r;
+            }
+            const float e = __expf(r - m);
+            S += e;
+            if (P.mstep) {
+#pragma unroll
+                for (int p = 0; p < LMAX; ++p)
+                    if (p < l) acc[(p * 4 + (int)((win >> (2 * p)) & 3u)) * NT + tid] += e;
+            }
+        }
+        const float lse = m + logf(S);
+        ll += (double)lse - log((double)ns);
+        if (P.mstep) {
+            const float inv = 1.f / S;
+            for (int q = 0; q < L4; ++q) tot[q * NT + tid] += acc[q * NT + tid] * inv;
+        }
+    }
+    if (!valid) return;
+    if (P.G == 1) {
+        if (P.mstep) {
+            const float den = (float)P.t + 4.f * P.beta;
+            for (int q = 0; q < L4; ++q) P.theta_out[c * L4 + q] = (tot[q * NT + tid] + P.beta) / den;
+        }
+        P.ll_out[c] = ll;
+    } else {
+        if (P.mstep)
+            for (int q = 0; q < L4; ++q) P.part_acc[((int64_t)g * P.C + c) * L4 + q] = tot[q * NT + tid];
+        P.part_ll[(int64_t)g * P.C + c] = ll;
+    }
+}
+
+// Sum of the G partial results in group order (fixed, so deterministic).
+__global__ void em_reduce_kernel(const float *__restrict__ part_acc,
+                                 const double *__restrict__ part_ll, int G, int64_t C, int L4,
+                                 int t, float beta, int mstep, float *__restrict__ theta_out,
+                                 double *__restrict__ ll_out) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (mstep && idx < C * L4) {
+        float s = 0.f;
+        for (int g = 0; g < G; ++g) s += part_acc[(int64_t)g * C * L4 + idx];
+        theta_out[idx] = (s + beta) / ((float)t + 4.f * beta);
+    }
+    if (idx < C) {
+        double s = 0.0;
+        for (int g = 0; g < G; ++g) s += part_ll[(int64_t)g * C + idx];
+        ll_out[idx] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Ranking and finalisation (one CTA).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) finalize_kernel(
+    const uint32_t *__restrict__ packed, int64_t nwords, const int32_t *__restrict__ seq_off,
+    int t, int l, const double *__restrict__ bg, const float *__restrict__ theta,
+    const double *__restrict__ ll, int64_t C, int64_t *__restrict__ best_out,
+    int32_t *__restrict__ sites, uint8_t *__restrict__ consensus, int32_t *__restrict__ score) {
+    __shared__ double s_v[32];
+    __shared__ long long s_i[32];
+    __shared__ double W[32 * 4];
+    __shared__ long long s_best;
+    __shared__ int s_score[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // argmax of the FP64 log-likelihoods; ties to the smaller index
+    double bv = -INFINITY;
+    long long bi = -1;
+    for (int64_t c = tid; c < C; c += blockDim.x) {
+        const double v = ll[c];
+        if (bi < 0 || v > bv) { bv = v; bi = c; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const long long oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { s_v[warp] = bv; s_i[warp] = bi; }
+    __syncthreads();
+    if (warp == 0) {
+        bv = lane < (int)(blockDim.x / 32) ? s_v[lane] : -INFINITY;
+        bi = lane < (int)(blockDim.x / 32) ? s_i[lane] : -1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+            const long long oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+        }
+        if (lane == 0) s_best = bi;
+    }
+    __syncthreads();
+    const long long b = s_best;
+    if (tid == 0) *best_out = b;
+    if (b < 0) {
+        if (tid == 0) *score = 0;
+        for (int i = tid; i < t; i += blockDim.x) sites[i] = -1;
+        for (int p = tid; p < l; p += blockDim.x) consensus[p] = 'N';
+        return;
+    }
+    const float *th = theta + b * (int64_t)(4 * l);
+    if (tid < 4 * l) W[tid] = log((double)th[tid]) - log(bg[tid & 3]);
+    if (tid < l) {
+        int a = 0;
+        for (int q = 1; q < 4; ++q) if (th[tid * 4 + q] > th[tid * 4 + a]) a = q;
+        consensus[tid] = (uint8_t)("ACTG"[a]);
+    }
+    __syncthreads();
+    // sites: first start maximising r(i,j), in FP64
+    for (int i = warp; i < t; i += blockDim.x / 32) {
+        const int64_t base = seq_off[i];
+        const int ns = seq_off[i + 1] - seq_off[i] - l + 1;
+        double best = -INFINITY;
+        int bj = 0x7fffffff;
+        for (int j = lane; j < ns; j += 32) {
+            const uint64_t win = window64(packed, nwords, base + j);
+            double r = 0.0;
+            for (int p = 0; p < l; ++p) r += W[p * 4 + (int)((win >> (2 * p)) & 3u)];
+            if (r > best) { best = r; bj = j; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_down_sync(0xffffffffu, best, o);
+            const int oj = __shfl_down_sync(0xffffffffu, bj, o);
+            if (ob > best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+        }
+        if (lane == 0) sites[i] = ns > 0 ? bj : -1;
+    }
+    __syncthreads();
+    // Score(s, DNA): sum over columns of the largest base count
+    int colmax = 0;
+    if (tid < l) {
+        int cnt[4] = {0, 0, 0, 0};
+        for (int i = 0; i < t; ++i) {
+            const int a = sites[i];
+            if (a >= 0) ++cnt[code_at(packed, nwords, (int64_t)seq_off[i] + a + tid)];
+        }
+        colmax = max(max(cnt[0], cnt[1]), max(cnt[2], cnt[3]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) colmax += __shfl_down_sync(0xffffffffu, colmax, o);
+    if (lane == 0) s_score[warp] = colmax;
+    __syncthreads();
+    if (tid == 0) {
+        int sc = 0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) sc += s_score[w];
+        *score = sc;
+    }
+}
+
+template <int LMAX>
+int launch_em_fp32_iter(const EmParams &P, cudaStream_t st) {
+    const size_t smem = (size_t)3 * 4 * P.l * kEmThreads * sizeof(float);
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(em_fp32_kernel<LMAX>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)((P.C + kEmThreads - 1) / kEmThreads), (unsigned)P.G);
+    {
+        TraceSpan ts_("em_fp32", st);
+        em_fp32_kernel<LMAX><<<grid, kEmThreads, smem, st>>>(P);
+    }
+    PROJ_LAUNCH_CHECK("em_fp32_kernel");
+    return PROJ_OK;
+}
+
+}  // namespace
+
+int launch_theta0(const uint32_t *packed, const Layout &L, const int64_t *cand_off,
+                  const int32_t *members, int64_t C, float beta, float *theta0, cudaStream_t st) {
+    if (C == 0) return PROJ_OK;
+    const int nt = 128;
+    const size_t smem = (size_t)4 * L.l * nt * sizeof(float);
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(theta0_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    {
+        TraceSpan ts_("theta0", st);
+        theta0_kernel<<<(unsigned)((C + nt - 1) / nt), nt, smem, st>>>(
+            packed, L.nwords, L.seq_off_dev(), L.lmer_off_dev(), L.t, L.l, cand_off, members, C, beta,
+            theta0);
+    }
+    PROJ_LAUNCH_CHECK("theta0_kernel");
+    return PROJ_OK;
+}
+
+int run_em(const uint32_t *packed, const Layout &L, const double *bg, const float *theta0,
+           int64_t C, int iters, float beta, int precision, float *theta_out, double *ll,
+           cudaStream_t st) {
+    PROJ_REQUIRE(iters >= 0 && iters <= 1000, "em_iters out of range: %d", iters);
+    PROJ_REQUIRE(beta > 0.f, "pseudocount must be > 0");
+    PROJ_REQUIRE(precision == PROJ_EM_FP32 || precision == PROJ_EM_BF16_SPLIT,
+                 "unknown precision %d", precision);
+    if (C == 0) return PROJ_OK;
+    if (precision == PROJ_EM_BF16_SPLIT)
+        return run_em_tc(packed, L, bg, theta0, C, iters, beta, theta_out, ll, st);
+
+    const int L4 = 4 * L.l;
+    if (theta_out != theta0)
+        PROJ_CUDA_TRY(cudaMemcpyAsync(theta_out, theta0, (size_t)C * L4 * sizeof(float),
+                                      cudaMemcpyDeviceToDevice, st));
+    // enough (candidate-tile, sequence-group) units to fill every SM a few times
+    const int64_t tiles = (C + kEmThreads - 1) / kEmThreads;
+    const int64_t want = (int64_t)sm_count() * 8;
+    int G = (int)std::min<int64_t>(L.t, std::max<int64_t>(1, (want + tiles - 1) / tiles));
+    DevBuf part;
+    if (G > 1) PROJ_TRY(part.alloc((size_t)G * C * (L4 * sizeof(float) + sizeof(double)), st));
+    DevBuf tmp;  // next-iteration model (the kernel reads theta while others write)
+    PROJ_TRY(tmp.alloc((size_t)C * L4 * sizeof(float), st));
+
+    EmParams P{};
+    P.packed = packed;
+    P.nwords = L.nwords;
+    P.seq_off = L.seq_off_dev();
+    P.t = L.t;
+    P.l = L.l;
+    P.G = G;
+    P.bg = bg;
+    P.C = C;
+    P.beta = beta;
+    P.part_ll = G > 1 ? part.as<double>() : nullptr;
+    P.part_acc = G > 1 ? reinterpret_cast<float *>(part.as<double>() + (size_t)G * C) : nullptr;
+    float *cur = theta_out, *nxt = tmp.as<float>();
+    for (int it = 0; it <= iters; ++it) {
+        P.theta_in = cur;
+        P.theta_out = nxt;
+        P.ll_out = ll;
+        P.mstep = it < iters;
+        int rc;
+        if (L.l <= 8) rc = launch_em_fp32_iter<8>(P, st);
+        else if (L.l <= 16) rc = launch_em_fp32_iter<16>(P, st);
+        else if (L.l <= 24) rc = launch_em_fp32_iter<24>(P, st);
+        else rc = launch_em_fp32_iter<32>(P, st);
+        if (rc != PROJ_OK) return rc;
+        if (G > 1) {
+            const int64_t n = P.mstep ? C * L4 : C;
+            {
+                TraceSpan ts_("em_reduce", st);
+                em_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                    P.part_acc, P.part_ll, G, C, L4, L.t, beta, P.mstep, nxt, ll);
+            }
+            PROJ_LAUNCH_CHECK("em_reduce_kernel");
+        }
+        if (P.mstep) { float *sw = cur; cur = nxt; nxt = sw; }
+    }
+    if (cur != theta_out)
+        PROJ_CUDA_TRY(cudaMemcpyAsync(theta_out, cur, (size_t)C * L4 * sizeof(float),
+                                      cudaMemcpyDeviceToDevice, st));
+    return PROJ_OK;
+}
+
+int launch_finalize(const uint32_t *packed, const Layout &L, const double *bg,
+                    const float *theta, const double *ll, int64_t C, int64_t *best,
+                    int32_t *sites, uint8_t *consensus, int32_t *score, cudaStream_t st) {
+    {
+        TraceSpan ts_("finalize", st);
+        finalize_kernel<<<1, 1024, 0, st>>>(packed, L.nwords, L.seq_off_dev(), L.t, L.l, bg, theta, ll,
+                                            C, best, sites, consensus, score);
+    }
+    PROJ_LAUNCH_CHECK("finalize_kernel");
+    return PROJ_OK;
+}
+
+}  // namespace proj

@@ -1,0 +1,461 @@
+// Steps a2-a5: random projection h_k, base-4 hashing and bucket counting
+// (Algorithm 2 steps 2a-2c; Section 6's base-|Sigma| conversion, A:0 C:1 T:2
+// G:3, first projected position most significant), and the enriched buckets
+// of Algorithm 2 step 3 (a bucket is enriched when it holds >= s l-mers).
+//
+// Design (GB300): all trials run in one launch, one 1024-thread CTA per
+// (trial, key-range part).  The packed input (2 bits per base) and the
+// sequence offsets are staged in shared memory with vectorised loads; each
+// thread builds the keys of its l-mers from a 64-bit window of packed codes
+// and increments a shared-memory histogram (u32 counters, or u16 pairs when
+// 4^k counters of 4 bytes do not fit and no bucket can exceed 65535).  When
+// 4^k counters do not fit in one CTA the key space is split into parts, each
+// CTA counting only keys in its range.
+//
+// Two passes give exact, deterministic output without atomics deciding any
+// order: pass 1 counts enriched buckets and members per (trial, part); a scan
+// gives every (trial, part) its output offsets; pass 2 recounts, writes the
+// candidate table in key order, compacts the enriched l-mers in l-mer-id order
+// (block-wide ballot scan), and places each one at its bucket's cursor with a
+// single warp walking that list (match_any ranks equal keys within a step), so
+// members come out ascending within every bucket.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace proj {
+namespace {
+
+constexpr int kThreads = 1024;
+constexpr int kWarps = kThreads / 32;
+constexpr int kHistBytes = 128 * 1024;    // shared-memory histogram budget
+constexpr int kSmemLimit = 226 * 1024;    // dynamic shared memory per CTA (227 KB opt-in
+                                          // minus room for the static arrays)
+
+struct HashParams {
+    const uint32_t *packed;
+    int64_t nwords;
+    const int32_t *seq_off;   // [t+1]
+    const int32_t *lmer_off;  // [t+1]
+    int t, l, k, s, x;
+    uint64_t seed;
+    int64_t trial_begin;
+    int parts;                // CTAs per trial
+    int hb;                   // buckets per part
+    int hist16;               // u16 counters
+    int stage_words;          // packed words staged in smem (0 = read global)
+    int fixed_pos;            // positions given by the caller
+    int pos_in[16];
+    uint8_t *pos_out;
+    uint32_t *counts_out;
+    // pass 1 outputs
+    int32_t *part_nb, *part_nm;
+    // pass 2 inputs/outputs
+    const int64_t *cand_base, *mem_base;
+    int64_t cap_cand, cap_members;
+    int32_t *cand_trial;
+    uint32_t *cand_key;
+    int32_t *cand_cnt;
+    int64_t *cand_off;
+    int32_t *members;
+    uint32_t *scratch_key;    // [cap_members]
+    int32_t *scratch_gid;     // [cap_members]
+};
+
+struct SmemLayout {
+    int hist_bytes, bitmap_bytes, off_bytes, words_bytes, total;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(const HashParams &P, bool fill) {
+    SmemLayout S;
+    S.hist_bytes = (P.hist16 ? 2 : 4) * P.hb;
+    S.hist_bytes = (S.hist_bytes + 15) & ~15;
+    S.bitmap_bytes = fill ? (((P.hb + 31) / 32) * 4 + 15) & ~15 : 0;
+    S.off_bytes = ((2 * (P.t + 1) * 4) + 15) & ~15;
+    S.words_bytes = P.stage_words ? ((P.stage_words + 2) * 4 + 15) & ~15 : 0;
+    S.total = S.hist_bytes + S.bitmap_bytes + S.off_bytes + S.words_bytes;
+    return S;
+}
+
+__device__ __forceinline__ uint32_t lmer_key(uint64_t win, const int *pos, int k) {
+    uint32_t key = 0u;
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        if (q < k) key = (key << 2) | (uint32_t)((win >> (2 * pos[q])) & 3u);
+    return key;
+}
+
+// Block-wide exclusive scan of two ints; returns the prefixes and the totals.
+__device__ inline void block_scan2(int a, int b, int &pa, int &pb, int &ta, int &tb,
+                                   int2 *warp_tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int va = __shfl_up_sync(0xffffffffu, ia, o);
+        const int vb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) { ia += va; ib += vb; }
+    }
+    if (lane == 31) warp_tot[warp] = make_int2(ia, ib);
+    __syncthreads();
+    if (warp == 0) {
+        int2 v = lane < kWarps ? warp_tot[lane] : make_int2(0, 0);
+        int sa = v.x, sb = v.y;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int va = __shfl_up_sync(0xffffffffu, sa, o);
+            const int vb = __shfl_up_sync(0xffffffffu, sb, o);
+            if (lane >= o) { sa += va; sb += vb; }
+        }
+        if (lane < kWarps) warp_tot[lane] = make_int2(sa - v.x, sb - v.y);  // exclusive
+        if (lane == kWarps - 1) warp_tot[kWarps] = make_int2(sa, sb);        // totals
+    }
+    __syncthreads();
+    pa = warp_tot[warp].x + ia - a;
+    pb = warp_tot[warp].y + ib - b;
+    ta = warp_tot[kWarps].x;
+    tb = warp_tot[kWarps].y;
+    __syncthreads();
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(kThreads, 1) hash_kernel(const HashParams P) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ int s_pos[16];
+    __shared__ int2 s_warp[kWarps + 1];
+    __shared__ int s_round[kWarps + 1];
+
+    const SmemLayout S = smem_layout(P, FILL);
+    uint32_t *hist32 = reinterpret_cast<uint32_t *>(smem);
+    uint16_t *hist16 = reinterpret_cast<uint16_t *>(smem);
+    uint32_t *bitmap = reinterpret_cast<uint32_t *>(smem + S.hist_bytes);
+    int32_t *s_seq = reinterpret_cast<int32_t *>(smem + S.hist_bytes + S.bitmap_bytes);
+    int32_t *s_lmer = s_seq + (P.t + 1);
+    uint32_t *s_words =
+        reinterpret_cast<uint32_t *>(smem + S.hist_bytes + S.bitmap_bytes + S.off_bytes);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int trial_local = blockIdx.x / P.parts;
+    const int part = blockIdx.x % P.parts;
+    const uint64_t trial = (uint64_t)(P.trial_begin + trial_local);
+    const uint32_t lo_key = (uint32_t)part * (uint32_t)P.hb;
+    const uint32_t hb = (uint32_t)P.hb;
+
+    // projection positions of this trial (Algorithm 2 step 2a)
+    if (tid == 0) {
+        if (P.fixed_pos) {
+            for (int q = 0; q < P.k; ++q) s_pos[q] = P.pos_in[q];
+        } else {
+            draw_positions(P.seed, trial, P.l, P.k, s_pos);
+        }
+        if (!FILL && P.pos_out && part == 0)
+            for (int q = 0; q < P.k; ++q) P.pos_out[(int64_t)trial_local * P.k + q] = (uint8_t)s_pos[q];
+    }
+    for (int i = tid; i <= P.t; i += kThreads) {
+        s_seq[i] = P.seq_off[i];
+        s_lmer[i] = P.lmer_off[i];
+    }
+    const uint32_t *words = P.packed;
+    int64_t nwords = P.nwords;
+    if (P.stage_words) {
+        const int nw = P.stage_words;
+        if ((reinterpret_cast<uintptr_t>(P.packed) & 15u) == 0) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(P.packed);
+            uint4 *dst = reinterpret_cast<uint4 *>(s_words);
+            for (int v = tid; v < nw / 4; v += kThreads) dst[v] = __ldg(src + v);
+            for (int w = (nw / 4) * 4 + tid; w < nw + 2; w += kThreads)
+                s_words[w] = w < nw ? __ldg(P.packed + w) : 0u;
+        } else {
+            for (int w = tid; w < nw + 2; w += kThreads) s_words[w] = w < nw ? __ldg(P.packed + w) : 0u;
+        }
+        words = s_words;
+        nwords = nw + 2;
+    }
+    const int hist_words = S.hist_bytes / 4;
+    for (int w = tid; w < hist_words; w += kThreads) hist32[w] = 0u;
+    if (FILL)
+        for (int w = tid; w < S.bitmap_bytes / 4; w += kThreads) bitmap[w] = 0u;
+    __syncthreads();
+
+    int pos[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) pos[q] = q < P.k ? s_pos[q] : 0;
+
+    // Algorithm 2 steps 2b-2c: project every l-mer and count its bucket.
+    {
+        int i = 0;
+        for (int gid = tid; gid < P.x; gid += kThreads) {
+            while (s_lmer[i + 1] <= gid) ++i;
+            const int64_t b0 = (int64_t)s_seq[i] + (gid - s_lmer[i]);
+            const uint32_t rel = lmer_key(window64(words, nwords, b0), pos, P.k) - lo_key;
+            if (rel < hb) {
+                if (P.hist16) atomicAdd(&hist32[rel >> 1], 1u << (16 * (rel & 1u)));
+                else atomicAdd(&hist32[rel], 1u);
+            }
+        }
+    }
+    __syncthreads();
+
+    if (!FILL && P.counts_out) {
+        uint32_t *dst = P.counts_out + (((int64_t)trial_local) << (2 * P.k)) + lo_key;
+        for (uint32_t b = tid; b < hb; b += kThreads) dst[b] = P.hist16 ? hist16[b] : hist32[b];
+    }
+
+    // Algorithm 2 step 3: enriched buckets (count >= s) of this key range.
+    const int chunk = (P.hb + kThreads - 1) / kThreads;
+    const int b_begin = min(tid * chunk, P.hb), b_end = min(b_begin + chunk, P.hb);
+    int nb = 0, nm = 0;
+    for (int b = b_begin; b < b_end; ++b) {
+        const int c = P.hist16 ? hist16[b] : (int)hist32[b];
+        if (c >= P.s) { ++nb; nm += c; }
+    }
+    int rb, rm, NB, NM;
+    block_scan2(nb, nm, rb, rm, NB, NM, s_warp);
+
+    if (!FILL) {
+        if (tid == 0) {
+            P.part_nb[blockIdx.x] = NB;
+            P.part_nm[blockIdx.x] = NM;
+        }
+        return;
+    }
+
+    // pass 2: candidate table in key order, bucket cursors, enriched bitmap
+    const int64_t cbase = P.cand_base[blockIdx.x];
+    const int64_t mbase = P.mem_base[blockIdx.x];
+    for (int b = b_begin; b < b_end; ++b) {
+        const int c = P.hist16 ? hist16[b] : (int)hist32[b];
+        if (c >= P.s) {
+            const int64_t ci = cbase + rb;
+            if (ci < P.cap_cand) {
+                P.cand_trial[ci] = (int32_t)trial;
+                P.cand_key[ci] = lo_key + (uint32_t)b;
+                P.cand_cnt[ci] = c;
+                P.cand_off[ci] = mbase + rm;
+            }
+            if (P.hist16) hist16[b] = (uint16_t)rm; else hist32[b] = (uint32_t)rm;
+            atomicOr(&bitmap[b >> 5], 1u << (b & 31));
+            ++rb;
+            rm += c;
+        }
+    }
+    __syncthreads();
+    if (mbase + NM > P.cap_members || NM == 0) return;  // block-uniform
+
+    // enriched l-mers in id order -> scratch[mbase .. mbase+NM)
+    {
+        int i = 0, running = 0;
+        for (int base = 0; base < P.x; base += kThreads) {
+            const int gid = base + tid;
+            bool e = false;
+            uint32_t rel = 0u;
+            if (gid < P.x) {
+                while (s_lmer[i + 1] <= gid) ++i;
+                const int64_t b0 = (int64_t)s_seq[i] + (gid - s_lmer[i]);
+                rel = lmer_key(window64(words, nwords, b0), pos, P.k) - lo_key;
+                e = rel < hb && ((bitmap[rel >> 5] >> (rel & 31u)) & 1u);
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, e);
+            if (lane == 0) s_round[warp] = __popc(bal);
+            __syncthreads();
+            if (warp == 0) {
+                const int v = lane < kWarps ? s_round[lane] : 0;
+                int sc = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, sc, o);
+                    if (lane >= o) sc += u;
+                }
+                if (lane < kWarps) s_round[lane] = sc - v;
+                if (lane == kWarps - 1) s_round[kWarps] = sc;
+            }
+            __syncthreads();
+            if (e) {
+                const int q = running + s_round[warp] + __popc(bal & ((1u << lane) - 1u));
+                P.scratch_key[mbase + q] = rel;
+                P.scratch_gid[mbase + q] = gid;
+            }
+            running += s_round[kWarps];
+            __syncthreads();
+        }
+    }
+    __threadfence_block();
+    __syncthreads();
+
+    // stable placement at the bucket cursors, one warp walking the list
+    if (warp == 0) {
+        for (int q0 = 0; q0 < NM; q0 += 32) {
+            const int q = q0 + lane;
+            const bool act = q < NM;
+            const unsigned amask = __ballot_sync(0xffffffffu, act);
+            uint32_t rel = 0u;
+            int gid = 0, cur = 0, rank = 0;
+            unsigned grp = 0u;
+            if (act) {
+                rel = P.scratch_key[mbase + q];
+                gid = P.scratch_gid[mbase + q];
+                grp = __match_any_sync(amask, rel);
+                rank = __popc(grp & ((1u << lane) - 1u));
+                cur = P.hist16 ? (int)hist16[rel] : (int)hist32[rel];
+            }
+            __syncwarp();
+            if (act) {
+                P.members[mbase + cur + rank] = gid;
+                if (rank == 0) {
+                    const int nxt = cur + __popc(grp);
+                    if (P.hist16) hist16[rel] = (uint16_t)nxt; else hist32[rel] = (uint32_t)nxt;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Exclusive scan over the (trial, part) counts in launch order, which is
+// (trial, key) order: candidate and member offsets plus the totals.
+__global__ void __launch_bounds__(1024) hash_scan_kernel(const int32_t *__restrict__ nb,
+                                                         const int32_t *__restrict__ nm, int n,
+                                                         int64_t *__restrict__ cbase,
+                                                         int64_t *__restrict__ mbase,
+                                                         int64_t *__restrict__ totals,
+                                                         int64_t cap_cand,
+                                                         int64_t *__restrict__ cand_off) {
+    __shared__ long long s_a[1024], s_b[1024];
+    const int tid = threadIdx.x;
+    const int chunk = (n + 1023) / 1024;
+    const int lo = min(tid * chunk, n), hi = min(lo + chunk, n);
+    long long a = 0, b = 0;
+    for (int e = lo; e < hi; ++e) { a += nb[e]; b += nm[e]; }
+    s_a[tid] = a;
+    s_b[tid] = b;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        long long va = tid >= o ? s_a[tid - o] : 0, vb = tid >= o ? s_b[tid - o] : 0;
+        __syncthreads();
+        s_a[tid] += va;
+        s_b[tid] += vb;
+        __syncthreads();
+    }
+    long long pa = s_a[tid] - a, pb = s_b[tid] - b;
+    for (int e = lo; e < hi; ++e) {
+        cbase[e] = pa;
+        mbase[e] = pb;
+        pa += nb[e];
+        pb += nm[e];
+    }
+    if (tid == 1023) {
+        totals[0] = s_a[1023];
+        totals[1] = s_b[1023];
+        if (s_a[1023] <= cap_cand) cand_off[s_a[1023]] = s_b[1023];
+    }
+}
+
+}  // namespace
+
+int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64_t seed,
+                   int64_t trial_begin, int64_t n_trials, const int32_t *positions_in,
+                   const HashOut &out, cudaStream_t st) {
+    PROJ_REQUIRE(k >= 1 && k <= 10 && k <= L.l, "need 1 <= k <= min(l, 10), got k=%d l=%d", k, L.l);
+    PROJ_REQUIRE(s >= 1, "need s >= 1, got %d", s);
+    PROJ_REQUIRE(n_trials >= 0 && n_trials <= (int64_t)1 << 24, "n_trials out of range");
+    PROJ_REQUIRE(trial_begin >= 0, "trial_begin must be >= 0");
+    PROJ_REQUIRE(out.totals != nullptr, "totals_dev must not be NULL");
+    PROJ_REQUIRE(out.cap_cand >= 0 && out.cap_members >= 0, "capacities must be >= 0");
+    PROJ_REQUIRE(out.cap_cand == 0 || (out.cand_trial && out.cand_key && out.cand_cnt),
+                 "candidate buffers must not be NULL");
+    PROJ_REQUIRE(out.cand_off != nullptr, "cand_off_dev must not be NULL");
+    PROJ_REQUIRE(out.cap_members == 0 || out.members, "members_dev must not be NULL");
+
+    HashParams P{};
+    P.packed = packed;
+    P.nwords = L.nwords;
+    P.seq_off = L.seq_off_dev();
+    P.lmer_off = L.lmer_off_dev();
+    P.t = L.t; P.l = L.l; P.k = k; P.s = s; P.x = (int)L.x;
+    P.seed = seed;
+    P.trial_begin = trial_begin;
+    const int64_t nbuck = (int64_t)1 << (2 * k);
+    // u32 counters when they fit; else u16 pairs if no bucket can pass 65535
+    if (nbuck * 4 <= kHistBytes) {
+        P.hist16 = 0; P.hb = (int)nbuck; P.parts = 1;
+    } else if (L.x <= 65535) {
+        P.hist16 = 1; P.hb = (int)std::min<int64_t>(nbuck, kHistBytes / 2); P.parts = (int)(nbuck / P.hb);
+    } else {
+        P.hist16 = 0; P.hb = kHistBytes / 4; P.parts = (int)(nbuck / P.hb);
+    }
+    if (positions_in) {
+        P.fixed_pos = 1;
+        for (int q = 0; q < k; ++q) {
+            PROJ_REQUIRE(positions_in[q] >= 0 && positions_in[q] < L.l &&
+                             (q == 0 || positions_in[q] > positions_in[q - 1]),
+                         "positions_in must be increasing and in [0, l)");
+            P.pos_in[q] = positions_in[q];
+        }
+    }
+    P.pos_out = out.positions;
+    P.counts_out = out.counts;
+    // stage the packed input when it fits next to the histogram
+    {
+        HashParams Q = P;
+        Q.stage_words = (int)L.nwords;
+        if (smem_layout(Q, true).total <= kSmemLimit) P.stage_words = (int)L.nwords;
+    }
+    const SmemLayout S1 = smem_layout(P, false), S2 = smem_layout(P, true);
+    PROJ_REQUIRE(S2.total <= kSmemLimit, "too many sequences for the shared-memory layout (t=%d)", L.t);
+
+    const int64_t n_units = n_trials * P.parts;
+    if (n_units == 0) {
+        PROJ_CUDA_TRY(cudaMemsetAsync(out.totals, 0, 2 * sizeof(int64_t), st));
+        PROJ_CUDA_TRY(cudaMemcpyAsync(out.cand_off, out.totals, sizeof(int64_t),
+                                      cudaMemcpyDeviceToDevice, st));
+        return PROJ_OK;
+    }
+    PROJ_REQUIRE(n_units < (int64_t)1 << 31, "too many (trial, part) units");
+    DevBuf meta;
+    PROJ_TRY(meta.alloc((size_t)n_units * (4 + 4 + 8 + 8), st));
+    P.part_nb = meta.as<int32_t>();
+    P.part_nm = P.part_nb + n_units;
+    int64_t *cbase = reinterpret_cast<int64_t *>(P.part_nm + n_units);
+    int64_t *mbase = cbase + n_units;
+    P.cand_base = cbase;
+    P.mem_base = mbase;
+
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+    {
+        TraceSpan ts_("hash_count", st);
+        hash_kernel<false><<<(unsigned)n_units, kThreads, S1.total, st>>>(P);
+    }
+    PROJ_LAUNCH_CHECK("hash_kernel<count>");
+    {
+        TraceSpan ts_("hash_scan", st);
+        hash_scan_kernel<<<1, 1024, 0, st>>>(P.part_nb, P.part_nm, (int)n_units, cbase, mbase,
+                                             out.totals, out.cap_cand, out.cand_off);
+    }
+    PROJ_LAUNCH_CHECK("hash_scan_kernel");
+    if (out.count_only) return PROJ_OK;
+
+    DevBuf scratch;
+    if (out.cap_members > 0) PROJ_TRY(scratch.alloc((size_t)out.cap_members * 8, st));
+    P.cap_cand = out.cap_cand;
+    P.cap_members = out.cap_members;
+    P.cand_trial = out.cand_trial;
+    P.cand_key = out.cand_key;
+    P.cand_cnt = out.cand_cnt;
+    P.cand_off = out.cand_off;
+    P.members = out.members;
+    P.scratch_key = scratch.as<uint32_t>();
+    P.scratch_gid = reinterpret_cast<int32_t *>(P.scratch_key + out.cap_members);
+    P.counts_out = nullptr;
+    P.pos_out = nullptr;
+    {
+        TraceSpan ts_("hash_fill", st);
+        hash_kernel<true><<<(unsigned)n_units, kThreads, S2.total, st>>>(P);
+    }
+    PROJ_LAUNCH_CHECK("hash_kernel<fill>");
+    return PROJ_OK;
+}
+
+}  // namespace proj

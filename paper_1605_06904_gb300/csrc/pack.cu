@@ -1,0 +1,127 @@
+// Step a1 (linear 2-bit input, Section 6), the background frequencies of the
+// motif model's column 0 (Section 5.1), and the per-trial projection positions
+// of Algorithm 2 step 2a.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace proj {
+namespace {
+
+// One thread per output word: 16 ASCII bases -> 16 two-bit codes A0 C1 T2 G3.
+// HBM-bound (1 byte read + 0.25 byte written per base).
+__global__ void pack_kernel(const uint8_t *__restrict__ ascii, int64_t total,
+                            uint32_t *__restrict__ packed,
+                            unsigned long long *__restrict__ bad) {
+    const int64_t nw = (total + 15) >> 4;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b0 = w << 4;
+        const int nb = (int)(total - b0 < 16 ? total - b0 : 16);
+        uint8_t ch[16];
+        if (nb == 16 && ((reinterpret_cast<uintptr_t>(ascii + b0) & 15u) == 0)) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(ascii + b0);
+            memcpy(ch, &v, 16);
+        } else {
+            for (int q = 0; q < 16; ++q) ch[q] = q < nb ? ascii[b0 + q] : (uint8_t)'A';
+        }
+        uint32_t word = 0u;
+        int first_bad = -1;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const uint8_t u = ch[q] & 0xDFu;  // upper case
+            uint32_t c;
+            if (u == 'A') c = 0u;
+            else if (u == 'C') c = 1u;
+            else if (u == 'T') c = 2u;
+            else if (u == 'G') c = 3u;
+            else { c = 0u; if (first_bad < 0 && q < nb) first_bad = q; }
+            if (q < nb) word |= c << (2 * q);
+        }
+        packed[w] = word;
+        if (first_bad >= 0) atomicMin(bad, (unsigned long long)(b0 + first_bad));
+    }
+}
+
+// Base counts by popcount over packed words (single CTA; the input is a few
+// hundred KB at most for the workloads in scope).
+__global__ void background_kernel(const uint32_t *__restrict__ packed, int64_t total,
+                                  double *__restrict__ bg) {
+    __shared__ unsigned long long cnt[4];
+    if (threadIdx.x < 4) cnt[threadIdx.x] = 0ull;
+    __syncthreads();
+    unsigned long long c1 = 0, c2 = 0, c3 = 0;  // C, T, G (A = rest)
+    const int64_t nw = (total + 15) >> 4;
+    for (int64_t w = threadIdx.x; w < nw; w += blockDim.x) {
+        uint32_t v = packed[w];
+        const int nb = (int)(total - (w << 4) < 16 ? total - (w << 4) : 16);
+        const uint32_t valid = nb == 16 ? 0x55555555u : ((1u << (2 * nb)) - 1u) & 0x55555555u;
+        const uint32_t lo = v & valid, hi = (v >> 1) & valid;
+        c1 += __popc(lo & ~hi);
+        c2 += __popc(hi & ~lo);
+        c3 += __popc(lo & hi);
+    }
+    atomicAdd(&cnt[1], c1);
+    atomicAdd(&cnt[2], c2);
+    atomicAdd(&cnt[3], c3);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long c[4];
+        c[1] = cnt[1]; c[2] = cnt[2]; c[3] = cnt[3];
+        c[0] = (unsigned long long)total - c[1] - c[2] - c[3];
+        unsigned long long tot = 0;
+        for (int a = 0; a < 4; ++a) { if (c[a] == 0) c[a] = 1; tot += c[a]; }
+        for (int a = 0; a < 4; ++a) bg[a] = (double)c[a] / (double)tot;
+    }
+}
+
+__global__ void positions_kernel(uint64_t seed, int64_t trial_begin, int64_t n_trials, int l,
+                                 int k, uint8_t *__restrict__ pos) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_trials) return;
+    int p[32];
+    draw_positions(seed, (uint64_t)(trial_begin + i), l, k, p);
+    for (int q = 0; q < k; ++q) pos[i * k + q] = (uint8_t)p[q];
+}
+
+}  // namespace
+
+int launch_pack(const uint8_t *ascii, int64_t total, uint32_t *packed, int64_t *bad,
+                cudaStream_t st) {
+    PROJ_CUDA_TRY(cudaMemsetAsync(bad, 0xFF, sizeof(int64_t), st));
+    if (total == 0) return PROJ_OK;
+    const int64_t nw = (total + 15) >> 4;
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((nw + threads - 1) / threads, (int64_t)sm_count() * 8);
+    {
+        TraceSpan ts_("pack", st);
+        pack_kernel<<<(unsigned)blocks, threads, 0, st>>>(
+            ascii, total, packed, reinterpret_cast<unsigned long long *>(bad));
+    }
+    PROJ_LAUNCH_CHECK("pack_kernel");
+    return PROJ_OK;
+}
+
+int launch_background(const uint32_t *packed, int64_t total, double *bg, cudaStream_t st) {
+    {
+        TraceSpan ts_("background", st);
+        background_kernel<<<1, 1024, 0, st>>>(packed, total, bg);
+    }
+    PROJ_LAUNCH_CHECK("background_kernel");
+    return PROJ_OK;
+}
+
+int launch_positions(uint64_t seed, int64_t trial_begin, int64_t n_trials, int l, int k,
+                     uint8_t *pos, cudaStream_t st) {
+    if (n_trials <= 0) return PROJ_OK;
+    const int threads = 128;
+    {
+        TraceSpan ts_("positions", st);
+        positions_kernel<<<(unsigned)((n_trials + threads - 1) / threads), threads, 0, st>>>(
+            seed, trial_begin, n_trials, l, k, pos);
+    }
+    PROJ_LAUNCH_CHECK("positions_kernel");
+    return PROJ_OK;
+}
+
+}  // namespace proj

@@ -24,3 +24,19 @@ def golden_lines(name):
 def fig1():
     """Figure 1's seven sequences as a list of str."""
     return golden_lines("fig1_sequences.txt")
+
+
+@pytest.fixture(scope="session")
+def native_lib():
+    """The CUDA library, built for sm_103a if it is missing or stale."""
+    from paper_1605_06904_gb300 import _build, _native
+    _build.build()
+    return _native.lib()
+
+
+def ll_tol(want, t, rel=1e-6):
+    """Tolerance on a log-likelihood ratio: `rel` relative, with the scale
+    floored at t (one nat per sequence; LL is a sum of t per-sequence terms
+    each rounded at FP32 precision)."""
+    import numpy as np
+    return rel * np.maximum(np.abs(want), t)
