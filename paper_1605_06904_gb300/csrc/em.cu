@@ -60,6 +60,13 @@ __global__ void theta0_kernel(const uint32_t *__restrict__ packed, int64_t nword
 // ---------------------------------------------------------------------------
 // One EM iteration (E-step + optional M-step) in FP32 for a tile of
 // candidates and one group of sequences.
+//
+// Accuracy: the per-sequence sum S = sum_j exp(r - m) and the weighted counts
+// acc[p][a] are compensated (Kahan) sums, exp is the accurate expf, and the
+// per-sequence normalised counts and log-sum-exp are accumulated in FP64.
+// Plain FP32 running sums over the ~10^3 l-mers of a sequence leave relative
+// errors near n * 2^-24 in S, which the log-likelihood amplifies through the
+// small PWM entries; compensation keeps it at a few ulp.
 // ---------------------------------------------------------------------------
 struct EmParams {
     const uint32_t *packed;
@@ -68,14 +75,18 @@ struct EmParams {
     int t, l, G;
     const double *bg;
     const float *theta_in;
-    float *theta_out;   // G == 1: final model
-    double *ll_out;     // G == 1: final LL
-    float *part_acc;    // G > 1: [G][C][4l]
-    double *part_ll;    // G > 1: [G][C]
+    double *part_acc;   // [G][C][4l] normalised counts of this group's sequences
+    double *part_ll;    // [G][C]
     int64_t C;
-    float beta;
     int mstep;
 };
+
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float v) {
+    const float y = v - comp;
+    const float s = sum + y;
+    comp = (s - sum) - y;
+    sum = s;
+}
 
 template <int LMAX>
 __global__ void __launch_bounds__(kEmThreads) em_fp32_kernel(const EmParams P) {
@@ -85,78 +96,85 @@ __global__ void __launch_bounds__(kEmThreads) em_fp32_kernel(const EmParams P) {
     const int l = P.l, L4 = 4 * l;
     float *Ws = sm;                 // [4l][NT]
     float *acc = sm + L4 * NT;      // [4l][NT]
-    float *tot = sm + 2 * L4 * NT;  // [4l][NT]
+    float *cmp = sm + 2 * L4 * NT;  // [4l][NT] Kahan compensation of acc
     const int64_t c = blockIdx.x * (int64_t)NT + tid;
     const bool valid = c < P.C;
     const int g = blockIdx.y;
+    double *tot = P.part_acc + ((int64_t)g * P.C + (valid ? c : 0)) * L4;
 
     float lbg[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) lbg[a] = (float)log(P.bg[a]);
     for (int q = 0; q < L4; ++q) {
         Ws[q * NT + tid] = valid ? logf(P.theta_in[c * L4 + q]) - lbg[q & 3] : 0.f;
-        tot[q * NT + tid] = 0.f;
+        if (valid && P.mstep) tot[q] = 0.0;
     }
     double ll = 0.0;
     const int i0 = (int)((int64_t)P.t * g / P.G), i1 = (int)((int64_t)P.t * (g + 1) / P.G);
     for (int i = i0; i < i1; ++i) {
         const int64_t base = P.seq_off[i];
         const int ns = P.seq_off[i + 1] - P.seq_off[i] - l + 1;
-        for (int q = 0; q < L4; ++q) acc[q * NT + tid] = 0.f;
-        float m = -INFINITY, S = 0.f;
+        if (P.mstep)
+            for (int q = 0; q < L4; ++q) { acc[q * NT + tid] = 0.f; cmp[q * NT + tid] = 0.f; }
+        float m = -INFINITY, S = 0.f, Sc = 0.f;
         uint64_t win = window64(P.packed, P.nwords, base);
+        // next base to shift in is base+32; its word is cached in `nxt`
+        int64_t nb = base + 32;
+        uint32_t nxt = (nb >> 4) < P.nwords ? __ldg(P.packed + (nb >> 4)) : 0u;
         for (int j = 0; j < ns; ++j) {
-            if (j > 0) win = (win >> 2) | ((uint64_t)code_at(P.packed, P.nwords, base + j + 31) << 62);
+            if (j > 0) {
+                win = (win >> 2) | ((uint64_t)((nxt >> (2 * (nb & 15))) & 3u) << 62);
+                ++nb;
+                if ((nb & 15) == 0) nxt = (nb >> 4) < P.nwords ? __ldg(P.packed + (nb >> 4)) : 0u;
+            }
             float r = 0.f;
 #pragma unroll
             for (int p = 0; p < LMAX; ++p)
                 if (p < l) r += Ws[(p * 4 + (int)((win >> (2 * p)) & 3u)) * NT + tid];
             if (r > m) {
-                const float sc = __expf(m - r);  // 0 on the first l-mer
+                const float sc = expf(m - r);  // 0 on the first l-mer
                 S *= sc;
+                Sc *= sc;
                 if (P.mstep)
-                    for (int q = 0; q < L4; ++q) acc[q * NT + tid] *= sc;
+                    for (int q = 0; q < L4; ++q) { acc[q * NT + tid] *= sc; cmp[q * NT + tid] *= sc; }
                 m = r;
             }
-            const float e = __expf(r - m);
-            S += e;
+            const float e = expf(r - m);
+            kahan_add(S, Sc, e);
             if (P.mstep) {
 #pragma unroll
                 for (int p = 0; p < LMAX; ++p)
-                    if (p < l) acc[(p * 4 + (int)((win >> (2 * p)) & 3u)) * NT + tid] += e;
+                    if (p < l) {
+                        const int q = (p * 4 + (int)((win >> (2 * p)) & 3u)) * NT + tid;
+                        float a = acc[q], cc = cmp[q];
+                        kahan_add(a, cc, e);
+                        acc[q] = a;
+                        cmp[q] = cc;
+                    }
             }
         }
-        const float lse = m + logf(S);
-        ll += (double)lse - log((double)ns);
-        if (P.mstep) {
-            const float inv = 1.f / S;
-            for (int q = 0; q < L4; ++q) tot[q * NT + tid] += acc[q * NT + tid] * inv;
+        const double Sd = (double)S - (double)Sc;
+        ll += (double)m + log(Sd) - log((double)ns);
+        if (P.mstep && valid) {
+            const double inv = 1.0 / Sd;
+            for (int q = 0; q < L4; ++q)
+                tot[q] += ((double)acc[q * NT + tid] - (double)cmp[q * NT + tid]) * inv;
         }
     }
-    if (!valid) return;
-    if (P.G == 1) {
-        if (P.mstep) {
-            const float den = (float)P.t + 4.f * P.beta;
-            for (int q = 0; q < L4; ++q) P.theta_out[c * L4 + q] = (tot[q * NT + tid] + P.beta) / den;
-        }
-        P.ll_out[c] = ll;
-    } else {
-        if (P.mstep)
-            for (int q = 0; q < L4; ++q) P.part_acc[((int64_t)g * P.C + c) * L4 + q] = tot[q * NT + tid];
-        P.part_ll[(int64_t)g * P.C + c] = ll;
-    }
+    if (valid) P.part_ll[(int64_t)g * P.C + c] = ll;
 }
 
-// Sum of the G partial results in group order (fixed, so deterministic).
-__global__ void em_reduce_kernel(const float *__restrict__ part_acc,
+// Sum of the G partial results in group order (fixed, so deterministic), then
+// the M-step theta = (counts + pseudocount) / (t + 4 pseudocount).
+__global__ void em_reduce_kernel(const double *__restrict__ part_acc,
                                  const double *__restrict__ part_ll, int G, int64_t C, int L4,
                                  int t, float beta, int mstep, float *__restrict__ theta_out,
                                  double *__restrict__ ll_out) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (mstep && idx < C * L4) {
-        float s = 0.f;
+        double s = 0.0;
         for (int g = 0; g < G; ++g) s += part_acc[(int64_t)g * C * L4 + idx];
-        theta_out[idx] = (s + beta) / ((float)t + 4.f * beta);
+        theta_out[idx] = (float)((s + (double)beta) / ((double)t + 4.0 * (double)beta));
     }
     if (idx < C) {
         double s = 0.0;
@@ -310,17 +328,16 @@ int run_em(const uint32_t *packed, const Layout &L, const double *bg, const floa
         return run_em_tc(packed, L, bg, theta0, C, iters, beta, theta_out, ll, st);
 
     const int L4 = 4 * L.l;
-    if (theta_out != theta0)
-        PROJ_CUDA_TRY(cudaMemcpyAsync(theta_out, theta0, (size_t)C * L4 * sizeof(float),
-                                      cudaMemcpyDeviceToDevice, st));
     // enough (candidate-tile, sequence-group) units to fill every SM a few times
     const int64_t tiles = (C + kEmThreads - 1) / kEmThreads;
     const int64_t want = (int64_t)sm_count() * 8;
-    int G = (int)std::min<int64_t>(L.t, std::max<int64_t>(1, (want + tiles - 1) / tiles));
+    const int G = (int)std::min<int64_t>(L.t, std::max<int64_t>(1, (want + tiles - 1) / tiles));
     DevBuf part;
-    if (G > 1) PROJ_TRY(part.alloc((size_t)G * C * (L4 * sizeof(float) + sizeof(double)), st));
-    DevBuf tmp;  // next-iteration model (the kernel reads theta while others write)
+    PROJ_TRY(part.alloc((size_t)G * C * (L4 + 1) * sizeof(double), st));
+    DevBuf tmp;  // model of the current iteration (theta_out may alias theta0)
     PROJ_TRY(tmp.alloc((size_t)C * L4 * sizeof(float), st));
+    PROJ_CUDA_TRY(cudaMemcpyAsync(tmp.as<float>(), theta0, (size_t)C * L4 * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, st));
 
     EmParams P{};
     P.packed = packed;
@@ -331,14 +348,10 @@ int run_em(const uint32_t *packed, const Layout &L, const double *bg, const floa
     P.G = G;
     P.bg = bg;
     P.C = C;
-    P.beta = beta;
-    P.part_ll = G > 1 ? part.as<double>() : nullptr;
-    P.part_acc = G > 1 ? reinterpret_cast<float *>(part.as<double>() + (size_t)G * C) : nullptr;
-    float *cur = theta_out, *nxt = tmp.as<float>();
+    P.part_ll = part.as<double>();
+    P.part_acc = part.as<double>() + (size_t)G * C;
+    P.theta_in = tmp.as<float>();
     for (int it = 0; it <= iters; ++it) {
-        P.theta_in = cur;
-        P.theta_out = nxt;
-        P.ll_out = ll;
         P.mstep = it < iters;
         int rc;
         if (L.l <= 8) rc = launch_em_fp32_iter<8>(P, st);
@@ -346,20 +359,16 @@ int run_em(const uint32_t *packed, const Layout &L, const double *bg, const floa
         else if (L.l <= 24) rc = launch_em_fp32_iter<24>(P, st);
         else rc = launch_em_fp32_iter<32>(P, st);
         if (rc != PROJ_OK) return rc;
-        if (G > 1) {
-            const int64_t n = P.mstep ? C * L4 : C;
-            {
-                TraceSpan ts_("em_reduce", st);
-                em_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-                    P.part_acc, P.part_ll, G, C, L4, L.t, beta, P.mstep, nxt, ll);
-            }
-            PROJ_LAUNCH_CHECK("em_reduce_kernel");
+        const int64_t n = P.mstep ? C * L4 : C;
+        {
+            TraceSpan ts_("em_reduce", st);
+            em_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                P.part_acc, P.part_ll, G, C, L4, L.t, beta, P.mstep, tmp.as<float>(), ll);
         }
-        if (P.mstep) { float *sw = cur; cur = nxt; nxt = sw; }
+        PROJ_LAUNCH_CHECK("em_reduce_kernel");
     }
-    if (cur != theta_out)
-        PROJ_CUDA_TRY(cudaMemcpyAsync(theta_out, cur, (size_t)C * L4 * sizeof(float),
-                                      cudaMemcpyDeviceToDevice, st));
+    PROJ_CUDA_TRY(cudaMemcpyAsync(theta_out, tmp.as<float>(), (size_t)C * L4 * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, st));
     return PROJ_OK;
 }
 

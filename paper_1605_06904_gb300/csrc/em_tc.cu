@@ -1,13 +1,436 @@
-// EM scoring and M-step contractions on the tcgen05 tensor cores (BF16 hi+lo
-// split operands, FP32 accumulation in tensor memory).
+// EM refinement (Section 5.1, OOPS) with both contractions on the tcgen05
+// tensor cores: PROJ_EM_BF16_SPLIT.
+//
+// The E-step score of candidate c on l-mer j, r(c,j) = sum_p W_c[p][x_{j+p}],
+// is the product of the log-odds matrix W [C x 4l] with the one-hot encoding
+// X [x x 4l] of the l-mers (exact in BF16).  The M-step counts
+// N_c[p][a] = sum_j z(c,j) [x_{j+p} = a] are the product of the posteriors
+// Z [C x x] with the same X.  Together they have the shape of attention with
+// one-hot keys and values: per sequence a softmax over the starts j.
+//
+// One CTA (128 threads) owns 128 candidates = the 128 lanes of tensor memory
+// and one group of sequences.  Per tile of NT l-mers of one sequence:
+//   1. the CTA writes the one-hot tile X [NT x KP] to shared memory;
+//   2. one thread issues S = W_hi X^T + W_lo X^T (M=128, N=NT, K=KP, FP32
+//      accumulation in tensor memory; W split into BF16 hi + lo parts so the
+//      product carries ~16 mantissa bits of W);
+//   3. thread i reads row i of S, keeps a running maximum and a compensated
+//      running sum of 2^(S - max) for its candidate, rescales its row of O when
+//      the maximum grows, and writes P = 2^(S - max) as BF16 hi + lo parts;
+//   4. one thread issues O += P_hi X + P_lo X (M=128, N=KP, K=NT) with X read
+//      in MN-major form from the same shared-memory tile.
+// At the end of a sequence O / sum is added (FP64) to the candidate's counts
+// and max + log2(sum) to its log-likelihood.  Scores are kept in log2 units
+// (W = log2 theta - log2 bg) so the exponentials are exp2.
+//
+// Every wait on an MMA completion is bounded; when a bound expires the CTA
+// stops, records the failure in a device flag (returned as PROJ_ETIMEOUT) and
+// frees its tensor memory.
+#include <math.h>
+
+#include <algorithm>
+
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace proj {
+namespace {
 
-int run_em_tc(const uint32_t *, const Layout &, const double *, const float *, int64_t, int,
-              float, float *, double *, cudaStream_t) {
-    set_error("PROJ_EM_BF16_SPLIT is not available in this build");
-    return PROJ_ENOTSUP;
+constexpr int kTcThreads = 128;
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait on a tensor-core completion
+
+struct EmTcParams {
+    const uint32_t *packed;
+    int64_t nwords;
+    const int32_t *seq_off;
+    int t, l, G;
+    const double *bg;
+    const float *theta_in;  // [C][l][4]
+    double *part_acc;       // [G][C][4l]
+    double *part_ll;        // [G][C]
+    int64_t C;
+    int mstep;
+    int *err;
+};
+
+template <int KP, int NT>
+struct TcLayout {
+    static constexpr int W_BYTES = 128 * KP * 2;  // each of W_hi, W_lo
+    static constexpr int X_BYTES = NT * KP * 2;
+    static constexpr int P_BYTES = 128 * NT * 2;  // each of P_hi, P_lo
+    static constexpr int OFF_WHI = 0;
+    static constexpr int OFF_WLO = OFF_WHI + W_BYTES;
+    static constexpr int OFF_X = OFF_WLO + W_BYTES;
+    static constexpr int OFF_PHI = OFF_X + X_BYTES;
+    static constexpr int OFF_PLO = OFF_PHI + P_BYTES;
+    static constexpr int TOTAL = OFF_PLO + P_BYTES;
+    static constexpr uint32_t TMEM_COLS = (NT + KP <= 128) ? 128u : 256u;
+};
+
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void kahan(float &sum, float &comp, float v) {
+    const float y = v - comp;
+    const float s = sum + y;
+    comp = (s - sum) - y;
+    sum = s;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+template <int KP, int NT>
+__global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
+    using LY = TcLayout<KP, NT>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int l = P.l, L4 = 4 * l;
+    const int64_t c = (int64_t)blockIdx.x * kTcThreads + tid;
+    const bool valid = c < P.C;
+    const int g = blockIdx.y;
+    uint8_t *sWhi = smem + LY::OFF_WHI, *sWlo = smem + LY::OFF_WLO, *sX = smem + LY::OFF_X;
+    uint8_t *sPhi = smem + LY::OFF_PHI, *sPlo = smem + LY::OFF_PLO;
+
+    // W_c = log2 theta_c - log2 bg, split into BF16 hi + lo (row tid, K-major)
+    double lbg[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) lbg[a] = log2(P.bg[a]);
+    for (int k8 = 0; k8 < KP; k8 += 8) {
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+            float h2[2], l2[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int k = k8 + q + u;
+                double w = 0.0;
+                if (valid && k < L4) w = log2((double)P.theta_in[c * L4 + k]) - lbg[k & 3];
+                const float h = __bfloat162float(__float2bfloat16_rn((float)w));
+                h2[u] = h;
+                l2[u] = (float)(w - (double)h);
+            }
+            hi[q / 2] = pack_bf16(h2[0], h2[1]);
+            lo[q / 2] = pack_bf16(l2[0], l2[1]);
+        }
+        *reinterpret_cast<uint4 *>(sWhi + tc::kmajor_off(tid, k8, KP)) =
+            make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4 *>(sWlo + tc::kmajor_off(tid, k8, KP)) =
+            make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+    if (tid == 0) {
+        tc::mbar_init(&mbar, 1);
+        tc::mbar_fence_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_slot, LY::TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tm = tmem_slot;
+    const uint32_t tS = tm, tO = tm + NT;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    const uint32_t aWhi = tc::smem_addr(sWhi), aWlo = tc::smem_addr(sWlo);
+    const uint32_t aX = tc::smem_addr(sX), aPhi = tc::smem_addr(sPhi), aPlo = tc::smem_addr(sPlo);
+    constexpr uint32_t IDESC_S = tc::idesc_bf16(128, NT);
+    constexpr uint32_t IDESC_O = tc::idesc_bf16(128, KP, true);
+
+    double *tot = P.part_acc + ((int64_t)g * P.C + (valid ? c : 0)) * L4;
+    if (valid && P.mstep)
+        for (int q = 0; q < L4; ++q) tot[q] = 0.0;
+    double ll = 0.0;
+    uint32_t phase = 0;
+    bool abort = false;
+
+    const int i0 = (int)((int64_t)P.t * g / P.G), i1 = (int)((int64_t)P.t * (g + 1) / P.G);
+    for (int i = i0; i < i1 && !abort; ++i) {
+        const int64_t base = P.seq_off[i];
+        const int ns = P.seq_off[i + 1] - P.seq_off[i] - l + 1;
+        float m = -INFINITY, Ssum = 0.f, Scmp = 0.f;
+        bool first = true;
+        for (int j0 = 0; j0 < ns; j0 += NT) {
+            const int nvalid = min(NT, ns - j0);
+            // 1. one-hot tile X[j][p*4+a] = [x_{j0+j+p} = a]
+            for (int item = tid; item < NT * (KP / 8); item += kTcThreads) {
+                const int j = item % NT, kb = item / NT;
+                // two positions per 16-byte chunk: p = 2kb (words 0-1), 2kb+1 (words 2-3);
+                // BF16 1.0 (0x3F80) in the slot of the base's code
+                uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
+                if (j < nvalid) {
+                    const uint64_t win = window64(P.packed, P.nwords, base + j0 + j);
+                    const int p0 = 2 * kb, p1 = 2 * kb + 1;
+                    if (p0 < l) {
+                        const uint32_t code = (uint32_t)(win >> (2 * p0)) & 3u;
+                        const uint32_t v = 0x3F80u << (16 * (code & 1u));
+                        if (code >> 1) w1 = v; else w0 = v;
+                    }
+                    if (p1 < l) {
+                        const uint32_t code = (uint32_t)(win >> (2 * p1)) & 3u;
+                        const uint32_t v = 0x3F80u << (16 * (code & 1u));
+                        if (code >> 1) w3 = v; else w2 = v;
+                    }
+                }
+                *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(j, 8 * kb, KP)) =
+                    make_uint4(w0, w1, w2, w3);
+            }
+            tc::fence_async_smem();
+            __syncthreads();
+            // 2. S = W_hi X^T + W_lo X^T
+            if (tid == 0) {
+                tc::fence_after_sync();
+#pragma unroll
+                for (int s = 0; s < KP / 16; ++s)
+                    tc::mma_bf16(tS, tc::sdesc(aWhi + 256 * s, 128, KP * 16),
+                                 tc::sdesc(aX + 256 * s, 128, KP * 16), IDESC_S, s > 0);
+#pragma unroll
+                for (int s = 0; s < KP / 16; ++s)
+                    tc::mma_bf16(tS, tc::sdesc(aWlo + 256 * s, 128, KP * 16),
+                                 tc::sdesc(aX + 256 * s, 128, KP * 16), IDESC_S, 1);
+                tc::mma_commit(&mbar);
+            }
+            bool ok = tc::mbar_wait(&mbar, phase, kWaitNs);
+            phase ^= 1u;
+            abort = __syncthreads_or(!ok);
+            if (abort) break;
+            tc::fence_after_sync();
+            // 3. running max / compensated sum, P = 2^(S - max) as hi + lo
+            float tmax = -INFINITY;
+#pragma unroll
+            for (int c0 = 0; c0 < NT; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(tS + lane_base + c0, v);
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    if (c0 + q < nvalid) tmax = fmaxf(tmax, v[q]);
+            }
+            // the maximum of each row may grow; the tensor-memory accesses below are
+            // .sync.aligned, so the rescale of O runs warp-uniformly (scale 1 for
+            // rows whose maximum did not grow)
+            const bool grow = tmax > m;
+            const float sc = grow ? ex2(m - tmax) : 1.f;  // 0 on the first tile (m = -inf)
+            if (grow) {
+                Ssum *= sc;
+                Scmp *= sc;
+                m = tmax;
+            }
+            if (P.mstep && !first && __any_sync(0xffffffffu, grow)) {
+#pragma unroll
+                for (int c0 = 0; c0 < KP; c0 += 16) {
+                    float v[16];
+                    tc::tmem_ld16(tO + lane_base + c0, v);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] *= sc;
+                    tc::tmem_st16(tO + lane_base + c0, v);
+                }
+            }
+#pragma unroll
+            for (int c0 = 0; c0 < NT; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(tS + lane_base + c0, v);
+                uint32_t hi[16], lo[16];
+#pragma unroll
+                for (int q = 0; q < 32; q += 2) {
+                    const float p0 = (c0 + q < nvalid) ? ex2(v[q] - m) : 0.f;
+                    const float p1 = (c0 + q + 1 < nvalid) ? ex2(v[q + 1] - m) : 0.f;
+                    kahan(Ssum, Scmp, p0);
+                    kahan(Ssum, Scmp, p1);
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(p0, p1);
+                    const float2 hf = __bfloat1622float2(h);
+                    hi[q / 2] = *reinterpret_cast<const uint32_t *>(&h);
+                    lo[q / 2] = pack_bf16(p0 - hf.x, p1 - hf.y);
+                }
+                if (P.mstep) {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        *reinterpret_cast<uint4 *>(sPhi + tc::kmajor_off(tid, c0 + 8 * b, NT)) =
+                            make_uint4(hi[4 * b], hi[4 * b + 1], hi[4 * b + 2], hi[4 * b + 3]);
+                        *reinterpret_cast<uint4 *>(sPlo + tc::kmajor_off(tid, c0 + 8 * b, NT)) =
+                            make_uint4(lo[4 * b], lo[4 * b + 1], lo[4 * b + 2], lo[4 * b + 3]);
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            if (P.mstep) {
+                // 4. O += P_hi X + P_lo X
+                tc::fence_async_smem();
+                __syncthreads();
+                if (tid == 0) {
+                    tc::fence_after_sync();
+#pragma unroll
+                    for (int s = 0; s < NT / 16; ++s)
+                        tc::mma_bf16(tO, tc::sdesc(aPhi + 256 * s, 128, NT * 16),
+                                     tc::sdesc(aX + s * 2 * KP * 16, KP * 16, 128), IDESC_O,
+                                     (s > 0 || !first) ? 1u : 0u);
+#pragma unroll
+                    for (int s = 0; s < NT / 16; ++s)
+                        tc::mma_bf16(tO, tc::sdesc(aPlo + 256 * s, 128, NT * 16),
+                                     tc::sdesc(aX + s * 2 * KP * 16, KP * 16, 128), IDESC_O, 1u);
+                    tc::mma_commit(&mbar);
+                }
+                ok = tc::mbar_wait(&mbar, phase, kWaitNs);
+                phase ^= 1u;
+                abort = __syncthreads_or(!ok);
+                if (abort) break;
+                tc::fence_after_sync();
+            } else {
+                __syncthreads();  // every row of S is read before the next tile rewrites it
+            }
+            first = false;
+        }
+        if (abort) break;
+        const double Sd = (double)Ssum - (double)Scmp;
+        ll += ((double)m + log2(Sd)) * 0.69314718055994530942 - log((double)ns);
+        if (P.mstep) {
+            const double inv = 1.0 / Sd;
+#pragma unroll
+            for (int c0 = 0; c0 < KP; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tO + lane_base + c0, v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (valid && c0 + q < L4) tot[c0 + q] += (double)v[q] * inv;
+            }
+            tc::fence_before_sync();
+            __syncthreads();  // O is read before the next sequence restarts it
+        }
+    }
+    if (abort) {
+        if (tid == 0) atomicExch(P.err, 1);
+        // let any MMA still in flight finish (bounded) before freeing its memory:
+        // the phase that was being waited for has parity phase ^ 1
+        tc::mbar_wait(&mbar, phase ^ 1u, kWaitNs);
+    } else if (valid) {
+        P.part_ll[(int64_t)g * P.C + c] = ll;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tm, LY::TMEM_COLS);
+    }
+}
+
+__global__ void em_tc_reduce_kernel(const double *__restrict__ part_acc,
+                                    const double *__restrict__ part_ll, int G, int64_t C, int L4,
+                                    int t, float beta, int mstep, float *__restrict__ theta_out,
+                                    double *__restrict__ ll_out) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (mstep && idx < C * L4) {
+        double s = 0.0;
+        for (int g = 0; g < G; ++g) s += part_acc[(int64_t)g * C * L4 + idx];
+        theta_out[idx] = (float)((s + (double)beta) / ((double)t + 4.0 * (double)beta));
+    }
+    if (idx < C) {
+        double s = 0.0;
+        for (int g = 0; g < G; ++g) s += part_ll[(int64_t)g * C + idx];
+        ll_out[idx] = s;
+    }
+}
+
+template <int KP, int NT>
+int launch_tc(const EmTcParams &P, cudaStream_t st) {
+    using LY = TcLayout<KP, NT>;
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(em_tc_kernel<KP, NT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, LY::TOTAL));
+    dim3 grid((unsigned)((P.C + kTcThreads - 1) / kTcThreads), (unsigned)P.G);
+    {
+        TraceSpan ts_("em_tc", st);
+        em_tc_kernel<KP, NT><<<grid, kTcThreads, LY::TOTAL, st>>>(P);
+    }
+    PROJ_LAUNCH_CHECK("em_tc_kernel");
+    return PROJ_OK;
+}
+
+template <int NT>
+int ctas_per_sm(int kp) {
+    int smem = 0;
+    switch (kp) {
+        case 16: smem = TcLayout<16, NT>::TOTAL; break;
+        case 32: smem = TcLayout<32, NT>::TOTAL; break;
+        case 48: smem = TcLayout<48, NT>::TOTAL; break;
+        case 64: smem = TcLayout<64, NT>::TOTAL; break;
+        case 80: smem = TcLayout<80, NT>::TOTAL; break;
+        case 96: smem = TcLayout<96, NT>::TOTAL; break;
+        case 112: smem = TcLayout<112, NT>::TOTAL; break;
+        default: smem = TcLayout<128, NT>::TOTAL; break;
+    }
+    const int cols = (NT + kp <= 128) ? 128 : 256;
+    return std::max(1, std::min(228 * 1024 / (smem + 1024), 512 / cols));
+}
+
+int dispatch(int kp, const EmTcParams &P, cudaStream_t st) {
+    switch (kp) {
+        case 16: return launch_tc<16, 64>(P, st);
+        case 32: return launch_tc<32, 64>(P, st);
+        case 48: return launch_tc<48, 64>(P, st);
+        case 64: return launch_tc<64, 64>(P, st);
+        case 80: return launch_tc<80, 64>(P, st);
+        case 96: return launch_tc<96, 64>(P, st);
+        case 112: return launch_tc<112, 64>(P, st);
+        default: return launch_tc<128, 64>(P, st);
+    }
+}
+
+}  // namespace
+
+int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const float *theta0,
+              int64_t C, int iters, float beta, float *theta_out, double *ll, cudaStream_t st) {
+    const int L4 = 4 * L.l;
+    const int kp = 16 * ((L4 + 15) / 16);
+    const int64_t tiles = (C + kTcThreads - 1) / kTcThreads;
+    const int64_t want = (int64_t)sm_count() * ctas_per_sm<64>(kp) * 2;
+    const int G = (int)std::min<int64_t>(L.t, std::max<int64_t>(1, (want + tiles - 1) / tiles));
+    DevBuf part, tmp, flag;
+    PROJ_TRY(part.alloc((size_t)G * C * (L4 + 1) * sizeof(double), st));
+    PROJ_TRY(tmp.alloc((size_t)C * L4 * sizeof(float), st));
+    PROJ_TRY(flag.alloc(sizeof(int), st));
+    PROJ_CUDA_TRY(cudaMemsetAsync(flag.as<int>(), 0, sizeof(int), st));
+    PROJ_CUDA_TRY(cudaMemcpyAsync(tmp.as<float>(), theta0, (size_t)C * L4 * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, st));
+    EmTcParams P{};
+    P.packed = packed;
+    P.nwords = L.nwords;
+    P.seq_off = L.seq_off_dev();
+    P.t = L.t;
+    P.l = L.l;
+    P.G = G;
+    P.bg = bg;
+    P.theta_in = tmp.as<float>();
+    P.part_ll = part.as<double>();
+    P.part_acc = part.as<double>() + (size_t)G * C;
+    P.C = C;
+    P.err = flag.as<int>();
+    for (int it = 0; it <= iters; ++it) {
+        P.mstep = it < iters;
+        PROJ_TRY(dispatch(kp, P, st));
+        const int64_t n = P.mstep ? C * L4 : C;
+        {
+            TraceSpan ts_("em_reduce", st);
+            em_tc_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                P.part_acc, P.part_ll, G, C, L4, L.t, beta, P.mstep, tmp.as<float>(), ll);
+        }
+        PROJ_LAUNCH_CHECK("em_tc_reduce_kernel");
+    }
+    PROJ_CUDA_TRY(cudaMemcpyAsync(theta_out, tmp.as<float>(), (size_t)C * L4 * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, st));
+    int err = 0;
+    PROJ_CUDA_TRY(cudaMemcpyAsync(&err, flag.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    PROJ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (err) {
+        set_error("a bounded wait for tensor-core completion expired in em_tc_kernel");
+        return PROJ_ETIMEOUT;
+    }
+    return PROJ_OK;
 }
 
 }  // namespace proj

@@ -348,28 +348,31 @@ def test_find_rejects_bad_input(P):
     assert e.value.status == -1  # a sequence shorter than l
 
 
-def test_find_config2_full_size_sampled(P):
-    """Config 2 at full size through the step-wise ABI (the kernels the whole
-    path launches, in the same configuration): every trial's buckets
-    bit-exact, EM on a sample of candidates against the oracle, and the
-    winner's motif equal to the planted one."""
+def test_find_config2_full_size(P):
+    """Config 2 at full size: the whole path (projection_find) against the
+    oracle's whole path, plus the step-wise ABI (the kernels the whole path
+    launches, in the same configuration) with every trial's buckets bit-exact
+    and EM on a sample of candidates."""
     inst = instance_for_config(2)
     prm = inst.params
     k, s, m = O.default_params(inst.lens, inst.l, inst.d, prm["k"], prm["s"], 0)
     assert m == 172
     codes, off = inst_arrays(inst)
+    got = P.projection_find(inst.ascii, off, inst.l, inst.d, prm["k"], prm["s"], 0, seed=1002,
+                            em_iters=5, pseudocount=0.25)
+    want = O.find([q.decode() for q in inst.seqs], inst.l, inst.d, prm["k"], prm["s"], 0,
+                  seed=1002, em_iters=5, beta=0.25, nthreads=16, with_hash=True)
+    _check_find(got, want, inst, codes)
     packed = upload(P, inst.ascii)
     h = P.trial_hash(packed, off, inst.l, k, s, 1002, 0, m)
-    want = O.hash_trials(codes, off, inst.l, k, s, 1002, 0, m)
-    assert_hash_equal(hash_np(h), want)
+    assert_hash_equal(hash_np(h), want["hash"])
     C = h["n_candidates"]
     th0 = P.theta0_build(packed, off, inst.l, h["cand_off"], h["members"], C, 0.25)
     bg = P.projection_background(packed, off[-1])
     th, ll = P.em_refine(packed, off, inst.l, bg, th0, 5, 0.25)
     fin = P.projection_finalize(packed, off, inst.l, bg, th, ll)
     sample = np.unique(np.concatenate([np.arange(0, C, 97), [fin["best"]]]))
-    w_pwm, w_ll = O.em(codes, off, inst.l, O.background(codes),
-                       th0.cpu().numpy()[sample].astype(np.float64), 5, 0.25, nthreads=8)
-    assert np.max(np.abs(th.cpu().numpy()[sample] - w_pwm)) <= PWM_TOL
-    assert np.all(np.abs(ll.cpu().numpy()[sample] - w_ll) <= ll_tol(w_ll, inst.t))
-    assert fin["consensus"] == inst.motif
+    assert np.max(np.abs(th.cpu().numpy()[sample] - want["pwm_all"][sample])) <= PWM_TOL
+    assert np.all(np.abs(ll.cpu().numpy()[sample] - want["ll_all"][sample]) <=
+                  ll_tol(want["ll_all"][sample], inst.t))
+    assert fin["consensus"] == want["consensus"]
