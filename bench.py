@@ -260,13 +260,17 @@ def main():
     time.sleep(0.3)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     P.projection_trace_enable(True)
     wall0 = time.perf_counter()
     for i in range(args.steps):
+        evf[i][0].record(stream)
         flush.fill_(i & 0xFF)
+        evf[i][1].record(stream)
         ev[i][0].record(stream)
         res = step()
         ev[i][1].record(stream)
@@ -277,6 +281,7 @@ def main():
     P.projection_trace_enable(False)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    flush_ms = [a.elapsed_time(b) for a, b in evf]
     T = float(np.sum(step_ms)) / 1e3
 
     scores_step = x * C * (iters + 1)
@@ -345,6 +350,7 @@ def main():
         "n_candidates": C, "scores_per_step": scores_step,
         "motif_found": res["consensus"], "motif_planted": inst.motif,
         "wall_ms_per_step": wall * 1e3 / args.steps,
+        "flush_ms_per_step": float(np.mean(flush_ms)),
         "roofline": roof, "clocks": clk, "e2e": e2e,
         "gpu_launches": all_launches / max(1, args.steps),
         "cpu_baseline": None,

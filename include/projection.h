@@ -18,8 +18,9 @@
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device work
  *     is enqueued on it; calls return once their work is enqueued unless the
  *     description says they synchronise.
- *   - Scratch memory is allocated with cudaMallocAsync on `stream` and freed
- *     on the same stream before the call returns.
+ *   - Scratch memory is allocated stream-ordered on `stream` from a memory
+ *     pool the library creates per device (freed blocks stay cached in that
+ *     pool for reuse) and freed on the same stream before the call returns.
  *   - Return value: PROJ_OK (0) or a negative PROJ_E* status.  No C++
  *     exception crosses this boundary.  projection_last_error() returns a
  *     human-readable message for the calling thread's last failure.

@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -25,12 +26,41 @@ void set_error(const char *fmt, ...) {
 
 void clear_error() { g_err[0] = 0; }
 
+// One stream-ordered memory pool per device, owned by the library, that keeps
+// freed blocks for reuse (release threshold = unlimited): scratch allocated and
+// freed on every call is then recycled instead of being unmapped and mapped
+// again at each synchronisation.  The process's default pool is not touched.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+
+static int library_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    PROJ_CUDA_TRY(cudaGetDevice(&dev));
+    PROJ_REQUIRE(dev >= 0 && dev < 64, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        PROJ_CUDA_TRY(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = ~0ull;
+        PROJ_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return PROJ_OK;
+}
+
 int DevBuf::alloc(size_t bytes, cudaStream_t st) {
     release();
     st_ = st;
     bytes_ = bytes;
     if (bytes == 0) return PROJ_OK;
-    cudaError_t e = cudaMallocAsync(&ptr_, bytes, st);
+    cudaMemPool_t pool;
+    PROJ_TRY(library_pool(&pool));
+    cudaError_t e = cudaMallocFromPoolAsync(&ptr_, bytes, pool, st);
     if (e != cudaSuccess) {
         ptr_ = nullptr;
         bytes_ = 0;
