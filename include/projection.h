@@ -127,6 +127,31 @@ int trial_hash(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
                int32_t *cand_cnt_dev, int64_t *cand_off_dev, int32_t *members_dev,
                int64_t *totals_dev, void *stream);
 
+/* The paper has no counterpart to this call; it serves callers of this library
+ * that cannot allocate device memory -- a service that gave all device memory
+ * to its own pool allocator at start-up, or a latency-critical path that must
+ * not pay for an allocation (cudaMalloc may synchronise the device).
+ * Same arguments, outputs and status codes as trial_hash, but no device memory
+ * is allocated: the scratch lives in one fixed array of
+ * PROJ_NOALLOC_SCRATCH_BYTES inside the library, held by every GPU that loads
+ * the library until the process exits.  Needs
+ *   8 (t+1) + 16 n_units + 8 cap_members   bytes (each part rounded up to 256),
+ * n_units = n_trials * ceil(4^k / 32768) (a single part when 4^k <= 32768, or
+ * when 4^k <= 65536 and x <= 65535); a request above the limit returns
+ * PROJ_ECAPACITY with a message and launches nothing.  All calls share the
+ * array: calls whose device work overlaps (other streams, other threads) race
+ * and must be serialised by the caller.  The first call on each device looks
+ * up the array's device address (once, with that device current); make that
+ * first call before any stream capture. */
+#define PROJ_NOALLOC_SCRATCH_BYTES (8u << 20)
+int trial_hash_noalloc(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l, int k,
+                       int s, uint64_t seed, int64_t trial_begin, int64_t n_trials,
+                       const int32_t *positions_in, uint8_t *positions_out_dev,
+                       uint32_t *counts_out_dev, int64_t cap_cand, int64_t cap_members,
+                       int32_t *cand_trial_dev, uint32_t *cand_key_dev, int32_t *cand_cnt_dev,
+                       int64_t *cand_off_dev, int32_t *members_dev, int64_t *totals_dev,
+                       void *stream);
+
 /* ---- step a6: initial model theta^0 (Example 1, Figure 4) -------------- */
 
 /* theta0_dev[c][p][a] = (#members of candidate c with base a at position p

@@ -16,7 +16,8 @@ from ._native import (PROJ_EM_BF16_SPLIT, PROJ_EM_FP32, ProjectionError,  # noqa
                       ProjectionResult, check, lib)
 
 __all__ = ["projection_packed_words", "projection_default_params", "projection_pack",
-           "projection_background", "projection_positions", "trial_hash", "theta0_build",
+           "projection_background", "projection_positions", "trial_hash",
+           "trial_hash_noalloc", "theta0_build",
            "em_refine", "projection_finalize", "projection_find", "projection_find_packed",
            "projection_trace_enable", "projection_trace_read", "ProjectionError",
            "PROJ_EM_FP32", "PROJ_EM_BF16_SPLIT", "seq_offsets"]
@@ -137,6 +138,37 @@ def trial_hash(packed, seq_off, l, k, s, seed, trial_begin, n_trials, positions_
     if want_counts:
         out["counts"] = cnt[:n_trials * 4 ** k].view(n_trials, 4 ** k)
     return out
+
+
+def trial_hash_noalloc(packed, seq_off, l, k, s, seed, trial_begin, n_trials, cap_cand,
+                       cap_members, positions_in=None, stream=None):
+    """trial_hash without device allocation inside the library (scratch in a
+    fixed array of PROJ_NOALLOC_SCRATCH_BYTES).  Output tensors are
+    allocated here, by the caller side, with fixed capacities; raises
+    ProjectionError(PROJ_ECAPACITY) when the scratch or a capacity is too
+    small."""
+    off = _off(seq_off)
+    t = off.size - 1
+    dev = packed.device
+    pin = None
+    if positions_in is not None:
+        pin = np.ascontiguousarray(np.asarray(positions_in, np.int32))
+    ct = _dev(max(1, cap_cand), torch.int32, dev)
+    ck = _dev(max(1, cap_cand), torch.int32, dev)
+    cc = _dev(max(1, cap_cand), torch.int32, dev)
+    co = _dev(cap_cand + 1, torch.int64, dev)
+    mem = _dev(max(1, cap_members), torch.int32, dev)
+    tot = _dev(2, torch.int64, dev)
+    check(lib().trial_hash_noalloc(_ptr(packed), _ptr(off), t, l, k, s, seed & (2**64 - 1),
+                                   trial_begin, n_trials, _ptr(pin), None, None, cap_cand,
+                                   cap_members, _ptr(ct), _ptr(ck), _ptr(cc), _ptr(co), _ptr(mem),
+                                   _ptr(tot), _stream(stream)))
+    C, M = (int(v) for v in tot.cpu())
+    if C > cap_cand or M > cap_members:
+        raise ProjectionError(_native.PROJ_ECAPACITY,
+                              f"need {C} candidates / {M} members, capacities {cap_cand} / {cap_members}")
+    return {"cand_trial": ct[:C], "cand_key": ck[:C], "cand_cnt": cc[:C], "cand_off": co[:C + 1],
+            "members": mem[:M], "n_candidates": C, "n_members": M}
 
 
 def theta0_build(packed, seq_off, l, cand_off, members, C, pseudocount, stream=None):

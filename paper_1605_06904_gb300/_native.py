@@ -44,6 +44,8 @@ SIGNATURES = {
     "projection_positions": ([u64, i64, i64, i32, i32, P, P], i32),
     "trial_hash": ([P, P, i32, i32, i32, i32, u64, i64, i64, P, P, P, i64, i64, P, P, P, P, P,
                     P, P], i32),
+    "trial_hash_noalloc": ([P, P, i32, i32, i32, i32, u64, i64, i64, P, P, P, i64, i64, P, P, P,
+                            P, P, P, P], i32),
     "theta0_build": ([P, P, i32, i32, P, P, i64, f32, P, P], i32),
     "em_refine": ([P, P, i32, i32, P, P, i64, i32, f32, i32, P, P, P], i32),
     "projection_finalize": ([P, P, i32, i32, P, P, P, i64, P, P, P, P, P], i32),

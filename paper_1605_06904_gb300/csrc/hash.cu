@@ -20,6 +20,8 @@
 // single warp walking that list (match_any ranks equal keys within a step), so
 // members come out ascending within every bucket.
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -459,3 +461,190 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
 }
 
 }  // namespace proj
+
+// ---------------------------------------------------------------------------
+// trial_hash_noalloc: trial_hash without any device allocation.
+//
+// Some callers cannot call cudaMalloc: services that hand all device memory to
+// their own pool allocator at start-up and forbid further allocations, and
+// latency-critical callers that must not pay for an allocation (cudaMalloc may
+// synchronise the whole device).  For them this entry point runs the same two
+// bucket-kernel passes as trial_hash, but keeps its scratch (sequence and
+// l-mer offsets, per-(trial, part) counts and output offsets, and the ordered
+// list of enriched l-mers) in a fixed array that lives in the library's device
+// image.  Every GPU that loads the library holds that array until the process
+// exits.
+// ---------------------------------------------------------------------------
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PROJ_NOALLOC_SCRATCH_BYTES];
+
+namespace proj {
+namespace {
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64];  // device address of g_noalloc_scratch per device ordinal
+
+// Looks up (once per device, with that device current) the device address of
+// the scratch array.  In host code the array's name is only a host-side
+// stand-in, so kernels must receive this address instead.
+int noalloc_scratch(void **out) {
+    int dev = 0;
+    PROJ_CUDA_TRY(cudaGetDevice(&dev));
+    PROJ_REQUIRE(dev >= 0 && dev < 64, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        PROJ_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return PROJ_OK;
+}
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace proj
+
+using namespace proj;
+
+extern "C" int trial_hash_noalloc(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
+                                  int k, int s, uint64_t seed, int64_t trial_begin,
+                                  int64_t n_trials, const int32_t *positions_in,
+                                  uint8_t *positions_out_dev, uint32_t *counts_out_dev,
+                                  int64_t cap_cand, int64_t cap_members, int32_t *cand_trial_dev,
+                                  uint32_t *cand_key_dev, int32_t *cand_cnt_dev,
+                                  int64_t *cand_off_dev, int32_t *members_dev,
+                                  int64_t *totals_dev, void *stream) {
+    clear_error();
+    cudaStream_t st = (cudaStream_t)stream;
+    PROJ_REQUIRE(packed_dev != nullptr && seq_off != nullptr, "NULL input");
+    PROJ_REQUIRE(t >= 1 && l >= 1 && l <= 32, "need t >= 1 and 1 <= l <= 32");
+    PROJ_REQUIRE(k >= 1 && k <= 10 && k <= l, "need 1 <= k <= min(l, 10), got k=%d l=%d", k, l);
+    PROJ_REQUIRE(s >= 1, "need s >= 1, got %d", s);
+    PROJ_REQUIRE(n_trials >= 0 && n_trials <= (int64_t)1 << 24 && trial_begin >= 0,
+                 "trial range out of range");
+    PROJ_REQUIRE(totals_dev && cand_off_dev, "totals_dev and cand_off_dev must not be NULL");
+    PROJ_REQUIRE(cap_cand >= 0 && cap_members >= 0, "capacities must be >= 0");
+    PROJ_REQUIRE(cap_cand == 0 || (cand_trial_dev && cand_key_dev && cand_cnt_dev),
+                 "candidate buffers must not be NULL");
+    PROJ_REQUIRE(cap_members == 0 || members_dev, "members_dev must not be NULL");
+    PROJ_REQUIRE(seq_off[0] == 0, "seq_off[0] must be 0");
+
+    // host-side offsets (no device allocation)
+    std::vector<int32_t> off(2 * (size_t)(t + 1));
+    int64_t x = 0;
+    for (int i = 0; i < t; ++i) {
+        const int64_t n = seq_off[i + 1] - seq_off[i];
+        PROJ_REQUIRE(n >= l, "sequence %d has length %lld < l = %d", i, (long long)n, l);
+        PROJ_REQUIRE(seq_off[i + 1] < ((int64_t)1 << 31), "input longer than 2^31 - 1 bases");
+        off[i + 1] = (int32_t)seq_off[i + 1];
+        x += n - l + 1;
+        off[t + 1 + i + 1] = (int32_t)x;
+    }
+    off[0] = 0;
+    off[t + 1] = 0;
+
+    HashParams P{};
+    P.packed = packed_dev;
+    P.nwords = (seq_off[t] + 15) / 16;
+    P.t = t; P.l = l; P.k = k; P.s = s; P.x = (int)x;
+    P.seed = seed;
+    P.trial_begin = trial_begin;
+    const int64_t nbuck = (int64_t)1 << (2 * k);
+    if (nbuck * 4 <= kHistBytes) {
+        P.hist16 = 0; P.hb = (int)nbuck; P.parts = 1;
+    } else if (x <= 65535) {
+        P.hist16 = 1; P.hb = (int)std::min<int64_t>(nbuck, kHistBytes / 2); P.parts = (int)(nbuck / P.hb);
+    } else {
+        P.hist16 = 0; P.hb = kHistBytes / 4; P.parts = (int)(nbuck / P.hb);
+    }
+    if (positions_in) {
+        P.fixed_pos = 1;
+        for (int q = 0; q < k; ++q) {
+            PROJ_REQUIRE(positions_in[q] >= 0 && positions_in[q] < l &&
+                             (q == 0 || positions_in[q] > positions_in[q - 1]),
+                         "positions_in must be increasing and in [0, l)");
+            P.pos_in[q] = positions_in[q];
+        }
+    }
+    P.pos_out = positions_out_dev;
+    P.counts_out = counts_out_dev;
+    {
+        HashParams Q = P;
+        Q.stage_words = (int)P.nwords;
+        if (smem_layout(Q, true).total <= kSmemLimit) P.stage_words = (int)P.nwords;
+    }
+    const SmemLayout S1 = smem_layout(P, false), S2 = smem_layout(P, true);
+    PROJ_REQUIRE(S2.total <= kSmemLimit, "too many sequences for the shared-memory layout (t=%d)", t);
+    const int64_t n_units = n_trials * P.parts;
+
+    // carve the fixed scratch array
+    const size_t b_off = align256(off.size() * sizeof(int32_t));
+    const size_t b_cnt = align256((size_t)n_units * 2 * sizeof(int32_t));
+    const size_t b_base = align256((size_t)n_units * 2 * sizeof(int64_t));
+    const size_t b_list = align256((size_t)cap_members * (sizeof(uint32_t) + sizeof(int32_t)));
+    const size_t need = b_off + b_cnt + b_base + b_list;
+    if (need > (size_t)PROJ_NOALLOC_SCRATCH_BYTES) {
+        set_error("trial_hash_noalloc needs %zu bytes of scratch for t=%d, %lld trials x %d parts "
+                  "and cap_members=%lld, above its fixed %u bytes; use fewer trials per call, a "
+                  "smaller cap_members, or trial_hash",
+                  need, t, (long long)n_trials, P.parts, (long long)cap_members,
+                  (unsigned)PROJ_NOALLOC_SCRATCH_BYTES);
+        return PROJ_ECAPACITY;
+    }
+    void *scr = nullptr;
+    PROJ_TRY(noalloc_scratch(&scr));
+    unsigned char *base = (unsigned char *)scr;
+    int32_t *d_off = (int32_t *)base;
+    P.seq_off = d_off;
+    P.lmer_off = d_off + (t + 1);
+    P.part_nb = (int32_t *)(base + b_off);
+    P.part_nm = P.part_nb + n_units;
+    int64_t *cbase = (int64_t *)(base + b_off + b_cnt);
+    int64_t *mbase = cbase + n_units;
+    P.cand_base = cbase;
+    P.mem_base = mbase;
+    P.scratch_key = (uint32_t *)(base + b_off + b_cnt + b_base);
+    P.scratch_gid = (int32_t *)(P.scratch_key + cap_members);
+    // every scratch word is written before it is read (offsets here, counts by
+    // pass 1, bases by the scan, the list by pass 2), so nothing is cleared
+    PROJ_CUDA_TRY(cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, st));
+
+    if (n_units == 0) {
+        PROJ_CUDA_TRY(cudaMemsetAsync(totals_dev, 0, 2 * sizeof(int64_t), st));
+        PROJ_CUDA_TRY(cudaMemsetAsync(cand_off_dev, 0, sizeof(int64_t), st));
+        return PROJ_OK;
+    }
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+    {
+        TraceSpan ts_("hash_count", st);
+        hash_kernel<false><<<(unsigned)n_units, kThreads, S1.total, st>>>(P);
+    }
+    PROJ_LAUNCH_CHECK("hash_kernel<count>");
+    {
+        TraceSpan ts_("hash_scan", st);
+        hash_scan_kernel<<<1, 1024, 0, st>>>(P.part_nb, P.part_nm, (int)n_units, cbase, mbase,
+                                             totals_dev, cap_cand, cand_off_dev);
+    }
+    PROJ_LAUNCH_CHECK("hash_scan_kernel");
+    P.cap_cand = cap_cand;
+    P.cap_members = cap_members;
+    P.cand_trial = cand_trial_dev;
+    P.cand_key = cand_key_dev;
+    P.cand_cnt = cand_cnt_dev;
+    P.cand_off = cand_off_dev;
+    P.members = members_dev;
+    P.counts_out = nullptr;
+    P.pos_out = nullptr;
+    {
+        TraceSpan ts_("hash_fill", st);
+        hash_kernel<true><<<(unsigned)n_units, kThreads, S2.total, st>>>(P);
+    }
+    PROJ_LAUNCH_CHECK("hash_kernel<fill>");
+    return PROJ_OK;
+}
