@@ -63,7 +63,9 @@ struct TcLayout {
     static constexpr int OFF_X = OFF_WLO + W_BYTES;
     static constexpr int OFF_PHI = OFF_X + X_BYTES;
     static constexpr int OFF_PLO = OFF_PHI + P_BYTES;
-    static constexpr int TOTAL = OFF_PLO + P_BYTES;
+    static constexpr int SEQ_WORDS = 512;  // staged packed words of one sequence (8K bases)
+    static constexpr int OFF_SEQ = OFF_PLO + P_BYTES;
+    static constexpr int TOTAL = OFF_SEQ + SEQ_WORDS * 4;
     static constexpr uint32_t TMEM_COLS = (NT + KP <= 128) ? 128u : 256u;
 };
 
@@ -99,10 +101,11 @@ __global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
     uint8_t *sWhi = smem + LY::OFF_WHI, *sWlo = smem + LY::OFF_WLO, *sX = smem + LY::OFF_X;
     uint8_t *sPhi = smem + LY::OFF_PHI, *sPlo = smem + LY::OFF_PLO;
 
-    // W_c = log2 theta_c - log2 bg, split into BF16 hi + lo (row tid, K-major)
-    double lbg[4];
+    // W_c = log2 theta_c - log2 bg in FP32 (~2^-23 relative, far below the
+    // 2^-16 of the BF16 hi + lo pair), split into BF16 hi + lo (row tid, K-major)
+    float lbg[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) lbg[a] = log2(P.bg[a]);
+    for (int a = 0; a < 4; ++a) lbg[a] = log2f((float)P.bg[a]);
     for (int k8 = 0; k8 < KP; k8 += 8) {
         uint32_t hi[4], lo[4];
 #pragma unroll
@@ -111,11 +114,11 @@ __global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int k = k8 + q + u;
-                double w = 0.0;
-                if (valid && k < L4) w = log2((double)P.theta_in[c * L4 + k]) - lbg[k & 3];
-                const float h = __bfloat162float(__float2bfloat16_rn((float)w));
+                float w = 0.f;
+                if (valid && k < L4) w = log2f(__ldg(P.theta_in + c * L4 + k)) - lbg[k & 3];
+                const float h = __bfloat162float(__float2bfloat16_rn(w));
                 h2[u] = h;
-                l2[u] = (float)(w - (double)h);
+                l2[u] = w - h;
             }
             hi[q / 2] = pack_bf16(h2[0], h2[1]);
             lo[q / 2] = pack_bf16(l2[0], l2[1]);
@@ -145,9 +148,11 @@ __global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
     constexpr uint32_t IDESC_S = tc::idesc_bf16(128, NT);
     constexpr uint32_t IDESC_O = tc::idesc_bf16(128, KP, true);
 
-    double *tot = P.part_acc + ((int64_t)g * P.C + (valid ? c : 0)) * L4;
-    if (valid && P.mstep)
-        for (int q = 0; q < L4; ++q) tot[q] = 0.0;
+    // this group's normalised counts of candidate c, summed over its sequences
+    float tot[KP];
+#pragma unroll
+    for (int q = 0; q < KP; ++q) tot[q] = 0.f;
+    uint32_t *sSeq = reinterpret_cast<uint32_t *>(smem + LY::OFF_SEQ);
     double ll = 0.0;
     uint32_t phase = 0;
     bool abort = false;
@@ -158,6 +163,15 @@ __global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
         const int ns = P.seq_off[i + 1] - P.seq_off[i] - l + 1;
         float m = -INFINITY, Ssum = 0.f, Scmp = 0.f;
         bool first = true;
+        // packed words covering this sequence (+2 for the 64-bit windows)
+        const int64_t w_first = base >> 4;
+        const int nw_seq = (int)(((base + P.seq_off[i + 1] - P.seq_off[i] + 15) >> 4) - w_first) + 2;
+        const bool staged = nw_seq <= LY::SEQ_WORDS;
+        __syncthreads();  // the previous sequence's words are no longer read
+        if (staged)
+            for (int w = tid; w < nw_seq; w += kTcThreads)
+                sSeq[w] = (w_first + w) < P.nwords ? __ldg(P.packed + w_first + w) : 0u;
+        __syncthreads();
         for (int j0 = 0; j0 < ns; j0 += NT) {
             const int nvalid = min(NT, ns - j0);
             // 1. one-hot tile X[j][p*4+a] = [x_{j0+j+p} = a]
@@ -167,7 +181,9 @@ __global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
                 // BF16 1.0 (0x3F80) in the slot of the base's code
                 uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
                 if (j < nvalid) {
-                    const uint64_t win = window64(P.packed, P.nwords, base + j0 + j);
+                    const uint64_t win =
+                        staged ? window64(sSeq, nw_seq, base + j0 + j - (w_first << 4))
+                               : window64(P.packed, P.nwords, base + j0 + j);
                     const int p0 = 2 * kb, p1 = 2 * kb + 1;
                     if (p0 < l) {
                         const uint32_t code = (uint32_t)(win >> (2 * p0)) & 3u;
@@ -209,9 +225,14 @@ __global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
             for (int c0 = 0; c0 < NT; c0 += 32) {
                 float v[32];
                 tc::tmem_ld32(tS + lane_base + c0, v);
+                float mx[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) mx[q] = -INFINITY;
 #pragma unroll
                 for (int q = 0; q < 32; ++q)
-                    if (c0 + q < nvalid) tmax = fmaxf(tmax, v[q]);
+                    if (nvalid == NT || c0 + q < nvalid) mx[q & 7] = fmaxf(mx[q & 7], v[q]);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) tmax = fmaxf(tmax, mx[q]);
             }
             // the maximum of each row may grow; the tensor-memory accesses below are
             // .sync.aligned, so the rescale of O runs warp-uniformly (scale 1 for
@@ -233,23 +254,35 @@ __global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
                     tc::tmem_st16(tO + lane_base + c0, v);
                 }
             }
+            // P = 2^(S - max): each 32-column chunk is summed as a tree (no long
+            // dependency chain) and the chunk sums are added with compensation
+            const bool full = nvalid == NT;  // only a sequence's last tile is ragged
 #pragma unroll
             for (int c0 = 0; c0 < NT; c0 += 32) {
                 float v[32];
                 tc::tmem_ld32(tS + lane_base + c0, v);
-                uint32_t hi[16], lo[16];
 #pragma unroll
-                for (int q = 0; q < 32; q += 2) {
-                    const float p0 = (c0 + q < nvalid) ? ex2(v[q] - m) : 0.f;
-                    const float p1 = (c0 + q + 1 < nvalid) ? ex2(v[q + 1] - m) : 0.f;
-                    kahan(Ssum, Scmp, p0);
-                    kahan(Ssum, Scmp, p1);
-                    const __nv_bfloat162 h = __floats2bfloat162_rn(p0, p1);
-                    const float2 hf = __bfloat1622float2(h);
-                    hi[q / 2] = *reinterpret_cast<const uint32_t *>(&h);
-                    lo[q / 2] = pack_bf16(p0 - hf.x, p1 - hf.y);
+                for (int q = 0; q < 32; ++q) {
+                    const float e = ex2(v[q] - m);
+                    v[q] = (full || c0 + q < nvalid) ? e : 0.f;
                 }
+                float part[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) part[q] = v[2 * q] + v[2 * q + 1];
+#pragma unroll
+                for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                    for (int q = 0; q < w; ++q) part[q] += part[q + w];
+                kahan(Ssum, Scmp, part[0]);
                 if (P.mstep) {
+                    uint32_t hi[16], lo[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const uint32_t h = pack_bf16(v[2 * q], v[2 * q + 1]);
+                        const float h0 = __uint_as_float(h << 16), h1 = __uint_as_float(h & 0xFFFF0000u);
+                        hi[q] = h;
+                        lo[q] = pack_bf16(v[2 * q] - h0, v[2 * q + 1] - h1);
+                    }
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         *reinterpret_cast<uint4 *>(sPhi + tc::kmajor_off(tid, c0 + 8 * b, NT)) =
@@ -288,17 +321,16 @@ __global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
             first = false;
         }
         if (abort) break;
-        const double Sd = (double)Ssum - (double)Scmp;
-        ll += ((double)m + log2(Sd)) * 0.69314718055994530942 - log((double)ns);
+        const float Sf = Ssum - Scmp;
+        ll += (double)((m + log2f(Sf)) * 0.69314718f - logf((float)ns));
         if (P.mstep) {
-            const double inv = 1.0 / Sd;
+            const float inv = 1.f / Sf;
 #pragma unroll
             for (int c0 = 0; c0 < KP; c0 += 16) {
                 float v[16];
                 tc::tmem_ld16(tO + lane_base + c0, v);
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (valid && c0 + q < L4) tot[c0 + q] += (double)v[q] * inv;
+                for (int q = 0; q < 16; ++q) tot[c0 + q] += v[q] * inv;
             }
             tc::fence_before_sync();
             __syncthreads();  // O is read before the next sequence restarts it
@@ -311,6 +343,12 @@ __global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
         tc::mbar_wait(&mbar, phase ^ 1u, kWaitNs);
     } else if (valid) {
         P.part_ll[(int64_t)g * P.C + c] = ll;
+        if (P.mstep) {
+            double *dst = P.part_acc + ((int64_t)g * P.C + c) * L4;
+#pragma unroll
+            for (int q = 0; q < KP; ++q)
+                if (q < L4) dst[q] = (double)tot[q];
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
