@@ -230,6 +230,21 @@ int projection_find_packed(const uint32_t *packed_dev, const int64_t *seq_off, i
                            float pseudocount, int precision, projection_result *out,
                            void *stream);
 
+/* Batched serving: n_inst independent searches in one call.  Instance i owns
+ * sequences inst_seq[i] .. inst_seq[i+1]-1 of the linear input (ascii,
+ * seq_off[inst_seq[n_inst]+1]); its parameters are l[i], d[i], k[i], s[i], m[i]
+ * (0 = the Section 5 choice) and seed[i].  The trials of all instances are
+ * hashed in one launch, the candidates of all instances are refined by one
+ * EM launch per iteration (work items of 128 candidates x a range of their own
+ * instance's sequences, taken in turn by a persistent grid), and each
+ * instance is ranked on its own.  Requires precision = PROJ_EM_BF16_SPLIT.
+ * Synchronises `stream`.  out[n_inst] is filled like projection_find's; each
+ * entry is released by projection_result_free. */
+int projection_find_batch(const uint8_t *ascii, const int64_t *seq_off, const int *inst_seq,
+                          int n_inst, const int *l, const int *d, const int *k, const int *s,
+                          const int *m, const uint64_t *seed, int em_iters, float pseudocount,
+                          int precision, projection_result *out, void *stream);
+
 void projection_result_free(projection_result *r);
 
 /* ---- tracing (CUDA-event timers per kernel) ----------------------------- */

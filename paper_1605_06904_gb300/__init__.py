@@ -19,6 +19,7 @@ __all__ = ["projection_packed_words", "projection_default_params", "projection_p
            "projection_background", "projection_positions", "trial_hash",
            "trial_hash_noalloc", "theta0_build",
            "em_refine", "projection_finalize", "projection_find", "projection_find_packed",
+           "projection_find_batch",
            "projection_trace_enable", "projection_trace_read", "ProjectionError",
            "PROJ_EM_FP32", "PROJ_EM_BF16_SPLIT", "seq_offsets"]
 
@@ -257,6 +258,34 @@ def projection_find_packed(packed, seq_off, l, d, k=0, s=0, m=0, seed=0, em_iter
         return _result_dict(r)
     finally:
         lib().projection_result_free(ctypes.byref(r))
+
+
+def projection_find_batch(instances, l, d, k=None, s=None, m=None, seeds=None, em_iters=5,
+                          pseudocount=0.25, precision=PROJ_EM_BF16_SPLIT, stream=None) -> list:
+    """Many independent searches in one call.  `instances` is a list of
+    instances, each a list of ASCII sequences (bytes); l, d, k, s, m, seeds are
+    per-instance sequences (k, s, m may be None or contain 0 = Section 5
+    choice).  Returns one result dict per instance."""
+    n = len(instances)
+    seqs = [q for inst in instances for q in inst]
+    ascii = np.frombuffer(b"".join(bytes(q) for q in seqs), dtype=np.uint8)
+    off = seq_offsets([len(q) for q in seqs])
+    inst_seq = np.zeros(n + 1, np.int32)
+    inst_seq[1:] = np.cumsum([len(inst) for inst in instances])
+    arr = lambda v, dt, dflt: np.ascontiguousarray(np.asarray(v if v is not None else [dflt] * n, dt))
+    L, D = arr(l, np.int32, 0), arr(d, np.int32, 0)
+    K, S, M = arr(k, np.int32, 0), arr(s, np.int32, 0), arr(m, np.int32, 0)
+    SE = np.ascontiguousarray(np.asarray(seeds if seeds is not None else np.arange(n), np.uint64))
+    res = (ProjectionResult * n)()
+    rc = lib().projection_find_batch(_ptr(ascii), _ptr(off), _ptr(inst_seq), n, _ptr(L), _ptr(D),
+                                     _ptr(K), _ptr(S), _ptr(M), _ptr(SE), em_iters,
+                                     float(pseudocount), precision, res, _stream(stream))
+    try:
+        check(rc)
+        return [_result_dict(r) for r in res]
+    finally:
+        for i in range(n):
+            lib().projection_result_free(ctypes.byref(res[i]))
 
 
 # ---- tracing -----------------------------------------------------------------

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "em_batch.cuh"
 
 namespace proj {
 
@@ -408,6 +409,231 @@ int projection_find(const uint8_t *ascii, const int64_t *seq_off, int t, int l, 
     rc = find_impl(packed, seq_off, t, l, d, k, s, m, seed, em_iters, pseudocount, precision, out, st);
     out->status = rc;
     return rc;
+}
+
+int projection_find_batch(const uint8_t *ascii, const int64_t *seq_off, const int *inst_seq,
+                          int n_inst, const int *l, const int *d, const int *k, const int *s,
+                          const int *m, const uint64_t *seed, int em_iters, float pseudocount,
+                          int precision, projection_result *out, void *stream) {
+    clear_error();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!out || n_inst < 1) { set_error("need out[] and n_inst >= 1"); return PROJ_EINVAL; }
+    for (int i = 0; i < n_inst; ++i) result_init(&out[i]);
+    auto fail = [&](int rc) {
+        for (int i = 0; i < n_inst; ++i) out[i].status = rc;
+        return rc;
+    };
+    if (!ascii || !seq_off || !inst_seq || !l || !d || !k || !s || !m || !seed) {
+        set_error("NULL argument");
+        return fail(PROJ_EINVAL);
+    }
+    if (precision != PROJ_EM_BF16_SPLIT) {
+        set_error("batched searches run the tensor-core EM (PROJ_EM_BF16_SPLIT); use "
+                  "projection_find per instance for PROJ_EM_FP32");
+        return fail(PROJ_ENOTSUP);
+    }
+    if (!(pseudocount > 0.f) || em_iters < 0 || em_iters > 1000) {
+        set_error("need pseudocount > 0 and 0 <= em_iters <= 1000");
+        return fail(PROJ_EINVAL);
+    }
+    const int n_seq = inst_seq[n_inst];
+    if (inst_seq[0] != 0 || n_seq < 1 || seq_off[0] != 0) { set_error("bad inst_seq/seq_off"); return fail(PROJ_EINVAL); }
+    const int64_t total = seq_off[n_seq];
+    if (total >= ((int64_t)1 << 31)) { set_error("input longer than 2^31 - 1 bases"); return fail(PROJ_EINVAL); }
+
+    // ---- host-side plan: per-instance parameters and offsets
+    std::vector<int> K(n_inst), S(n_inst), Mt(n_inst);
+    std::vector<int32_t> offs;           // per instance: [rel (t+1) | lmer (t+1) | global (t+1)]
+    std::vector<int64_t> off_pos(n_inst), base_range(2 * n_inst);
+    std::vector<int64_t> word_lo(n_inst), nwords_i(n_inst), xs(n_inst);
+    int l_max = 1, t_sum = 0, l_sum = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const int sb = inst_seq[i], se = inst_seq[i + 1], t = se - sb;
+        if (t < 1 || l[i] < 1 || l[i] > 32 || d[i] < 0 || d[i] >= l[i]) {
+            set_error("instance %d: need t >= 1, 1 <= l <= 32, 0 <= d < l", i);
+            return fail(PROJ_EINVAL);
+        }
+        std::vector<int64_t> lens(t);
+        for (int j = 0; j < t; ++j) {
+            lens[j] = seq_off[sb + j + 1] - seq_off[sb + j];
+            if (lens[j] < l[i]) {
+                set_error("instance %d: sequence %d is shorter than l = %d", i, j, l[i]);
+                return fail(PROJ_EINVAL);
+            }
+        }
+        K[i] = k[i]; S[i] = s[i]; Mt[i] = m[i];
+        int rc = projection_default_params(t, lens.data(), l[i], d[i], &K[i], &S[i], &Mt[i]);
+        if (rc) return fail(rc);
+        if (K[i] < 1 || K[i] > 10 || K[i] > l[i]) {
+            set_error("instance %d: need 1 <= k <= min(l, 10), got %d", i, K[i]);
+            return fail(PROJ_EINVAL);
+        }
+        word_lo[i] = seq_off[sb] >> 4;
+        nwords_i[i] = ((seq_off[se] + 15) >> 4) - word_lo[i];
+        base_range[2 * i] = seq_off[sb];
+        base_range[2 * i + 1] = seq_off[se];
+        off_pos[i] = (int64_t)offs.size();
+        int64_t x = 0;
+        for (int j = 0; j <= t; ++j) offs.push_back((int32_t)(seq_off[sb + j] - 16 * word_lo[i]));
+        offs.push_back(0);
+        for (int j = 0; j < t; ++j) { x += lens[j] - l[i] + 1; offs.push_back((int32_t)x); }
+        for (int j = 0; j <= t; ++j) offs.push_back((int32_t)seq_off[sb + j]);
+        xs[i] = x;
+        l_max = std::max(l_max, l[i]);
+        t_sum += t;
+        l_sum += l[i];
+        out[i].t = t; out[i].l = l[i]; out[i].k = K[i]; out[i].s = S[i]; out[i].m = Mt[i];
+    }
+    const int stride = 4 * l_max;
+
+    // ---- device: input, offsets, background
+    DevBuf in, offb, ranges, bgb;
+    int rc = in.alloc((size_t)total + (size_t)projection_packed_words(total) * 4 + 64, st);
+    if (rc) return fail(rc);
+    uint8_t *ascii_dev = in.as<uint8_t>();
+    int64_t *bad = reinterpret_cast<int64_t *>(ascii_dev + ((total + 15) & ~(int64_t)15));
+    uint32_t *packed = reinterpret_cast<uint32_t *>(bad + 2);
+    const int64_t nwords = (total + 15) / 16;
+#define BATCH_TRY(expr) do { int rc_ = (expr); if (rc_) return fail(rc_); } while (0)
+#define BATCH_CUDA(expr) do { cudaError_t e_ = (expr); if (e_ != cudaSuccess) { set_error("%s: %s", #expr, cudaGetErrorString(e_)); return fail(PROJ_ECUDA); } } while (0)
+    BATCH_CUDA(cudaMemcpyAsync(ascii_dev, ascii, (size_t)total, cudaMemcpyHostToDevice, st));
+    BATCH_TRY(launch_pack(ascii_dev, total, packed, bad, st));
+    BATCH_TRY(offb.alloc(offs.size() * sizeof(int32_t), st));
+    BATCH_CUDA(cudaMemcpyAsync(offb.as<int32_t>(), offs.data(), offs.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, st));
+    BATCH_TRY(ranges.alloc(base_range.size() * sizeof(int64_t), st));
+    BATCH_CUDA(cudaMemcpyAsync(ranges.as<int64_t>(), base_range.data(),
+                               base_range.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    BATCH_TRY(bgb.alloc((size_t)n_inst * 4 * sizeof(double), st));
+    BATCH_TRY(launch_background_batch(packed, ranges.as<int64_t>(), n_inst, bgb.as<double>(), st));
+    {
+        int64_t bad_h = -1;
+        BATCH_CUDA(cudaMemcpyAsync(&bad_h, bad, 8, cudaMemcpyDeviceToHost, st));
+        BATCH_CUDA(cudaStreamSynchronize(st));
+        if (bad_h >= 0) {
+            set_error("character %d at index %lld is not A/C/G/T", (int)ascii[bad_h], (long long)bad_h);
+            return fail(PROJ_EBADCHAR);
+        }
+    }
+
+    // ---- all trials of all instances
+    std::vector<HashInstSpec> spec(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+        const int t = inst_seq[i + 1] - inst_seq[i];
+        HashInstSpec &q = spec[i];
+        q.packed = packed + word_lo[i];
+        q.nwords = nwords_i[i];
+        q.seq_off_rel = offb.as<int32_t>() + off_pos[i];
+        q.lmer_off = q.seq_off_rel + (t + 1);
+        q.t = t; q.l = l[i]; q.k = K[i]; q.s = S[i]; q.m = Mt[i];
+        q.x = (int)xs[i];
+        q.seed = seed[i];
+    }
+    HashBatchOut H;
+    BATCH_TRY(run_hash_batch(spec, H, st));
+    const int64_t C = H.C;
+
+    // ---- theta^0, EM, finalise for all candidates
+    std::vector<BatchInst> bi(n_inst);
+    std::vector<EmInstHost> eh(n_inst);
+    std::vector<EmInst> ei(n_inst);
+    int64_t sites_off = 0, cons_off = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const int t = inst_seq[i + 1] - inst_seq[i];
+        const int32_t *rel = offb.as<int32_t>() + off_pos[i];
+        bi[i].seq_off = rel + 2 * (t + 1);  // global positions
+        bi[i].lmer_off = rel + (t + 1);
+        bi[i].bg = bgb.as<double>() + 4 * i;
+        bi[i].t = t;
+        bi[i].l = l[i];
+        bi[i].cand_begin = H.cand_begin[i];
+        bi[i].C = H.n_cand[i];
+        bi[i].sites_off = sites_off;
+        bi[i].cons_off = cons_off;
+        sites_off += t;
+        cons_off += l[i];
+        eh[i].t = t; eh[i].l = l[i]; eh[i].C = H.n_cand[i]; eh[i].cand_begin = H.cand_begin[i];
+        ei[i].seq_off = bi[i].seq_off; ei[i].bg = bi[i].bg; ei[i].t = t; ei[i].l = l[i];
+        ei[i].cand_begin = H.cand_begin[i];
+        out[i].n_candidates = H.n_cand[i];
+        out[i].n_members = H.n_mem[i];
+    }
+    DevBuf bib, eib, model, res;
+    BATCH_TRY(bib.alloc(bi.size() * sizeof(BatchInst), st));
+    BATCH_TRY(eib.alloc(ei.size() * sizeof(EmInst), st));
+    BATCH_CUDA(cudaMemcpyAsync(bib.as<BatchInst>(), bi.data(), bi.size() * sizeof(BatchInst),
+                               cudaMemcpyHostToDevice, st));
+    BATCH_CUDA(cudaMemcpyAsync(eib.as<EmInst>(), ei.data(), ei.size() * sizeof(EmInst),
+                               cudaMemcpyHostToDevice, st));
+    BATCH_TRY(model.alloc((size_t)C * stride * sizeof(float) + (size_t)C * sizeof(double) + 64, st));
+    double *ll = model.as<double>();
+    float *theta = reinterpret_cast<float *>(ll + C);
+    BATCH_TRY(launch_theta0_batch(packed, nwords, bib.as<BatchInst>(), n_inst, H.cand_off(),
+                                  H.members(), C, pseudocount, stride, theta, st));
+    BATCH_TRY(run_em_tc_batch(packed, nwords, eh, eib.as<EmInst>(), theta, C, stride, em_iters,
+                              pseudocount, theta, ll, st));
+    const size_t res_bytes = (size_t)n_inst * (8 + 4) + (size_t)t_sum * 4 + (size_t)l_sum + 64;
+    BATCH_TRY(res.alloc(res_bytes, st));
+    int64_t *best = res.as<int64_t>();
+    int32_t *score = reinterpret_cast<int32_t *>(best + n_inst);
+    int32_t *sites = score + n_inst;
+    uint8_t *cons = reinterpret_cast<uint8_t *>(sites + t_sum);
+    BATCH_TRY(launch_finalize_batch(packed, nwords, bib.as<BatchInst>(), n_inst, theta, stride, ll,
+                                    best, sites, cons, score, st));
+    std::vector<unsigned char> hres(res_bytes);
+    BATCH_CUDA(cudaMemcpyAsync(hres.data(), res.as<unsigned char>(), res_bytes,
+                               cudaMemcpyDeviceToHost, st));
+    BATCH_CUDA(cudaStreamSynchronize(st));
+    const int64_t *hbest = reinterpret_cast<const int64_t *>(hres.data());
+    const int32_t *hscore = reinterpret_cast<const int32_t *>(hbest + n_inst);
+    const int32_t *hsites = hscore + n_inst;
+    const uint8_t *hcons = reinterpret_cast<const uint8_t *>(hsites + t_sum);
+    // the winners' models, log-likelihoods, trials and keys
+    std::vector<int64_t> widx;
+    for (int i = 0; i < n_inst; ++i)
+        if (hbest[i] >= 0) widx.push_back(H.cand_begin[i] + hbest[i]);
+    std::vector<float> wpwm(widx.size() * stride);
+    std::vector<double> wll(widx.size());
+    std::vector<int32_t> wtrial(widx.size());
+    std::vector<uint32_t> wkey(widx.size());
+    for (size_t q = 0; q < widx.size(); ++q) {
+        BATCH_CUDA(cudaMemcpyAsync(&wpwm[q * stride], theta + widx[q] * stride, stride * sizeof(float),
+                                   cudaMemcpyDeviceToHost, st));
+        BATCH_CUDA(cudaMemcpyAsync(&wll[q], ll + widx[q], 8, cudaMemcpyDeviceToHost, st));
+        BATCH_CUDA(cudaMemcpyAsync(&wtrial[q], H.cand_trial() + widx[q], 4, cudaMemcpyDeviceToHost, st));
+        BATCH_CUDA(cudaMemcpyAsync(&wkey[q], H.cand_key() + widx[q], 4, cudaMemcpyDeviceToHost, st));
+    }
+    BATCH_CUDA(cudaStreamSynchronize(st));
+    size_t q = 0;
+    int64_t so = 0, co = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        projection_result &r = out[i];
+        const int t = r.t, li = r.l;
+        r.pwm = (float *)calloc((size_t)4 * li, sizeof(float));
+        r.consensus = (char *)calloc((size_t)li + 1, 1);
+        r.sites = (int32_t *)calloc((size_t)t, sizeof(int32_t));
+        if (!r.pwm || !r.consensus || !r.sites) { set_error("host allocation failed"); return fail(PROJ_ENOMEM); }
+        memcpy(r.sites, hsites + so, (size_t)t * 4);
+        memcpy(r.consensus, hcons + co, (size_t)li);
+        r.consensus[li] = 0;
+        r.score = hscore[i];
+        r.win_index = hbest[i];
+        if (hbest[i] >= 0) {
+            memcpy(r.pwm, &wpwm[q * stride], (size_t)4 * li * sizeof(float));
+            r.loglik = wll[q];
+            r.win_trial = wtrial[q];
+            r.win_key = wkey[q];
+            ++q;
+        } else {
+            r.loglik = -INFINITY;
+        }
+        r.status = PROJ_OK;
+        so += t;
+        co += li;
+    }
+#undef BATCH_TRY
+#undef BATCH_CUDA
+    return PROJ_OK;
 }
 
 void projection_result_free(projection_result *r) {

@@ -113,6 +113,55 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
                    int64_t trial_begin, int64_t n_trials, const int32_t *positions_in,
                    const HashOut &out, cudaStream_t st);
 
+// ---- batched motif searches ------------------------------------------------
+// One instance of a batched hash: its packed words start at `packed`
+// (positions in seq_off_rel are relative to that word), device offsets.
+struct HashInstSpec {
+    const uint32_t *packed = nullptr;
+    int64_t nwords = 0;
+    const int32_t *seq_off_rel = nullptr;  // device [t+1]
+    const int32_t *lmer_off = nullptr;     // device [t+1]
+    int t = 0, l = 0, k = 0, s = 0, x = 0, m = 0;
+    uint64_t seed = 0;
+};
+
+// Candidate lists of all instances of a batch, in (instance, trial, key) order.
+struct HashBatchOut {
+    std::vector<int64_t> cand_begin, n_cand, mem_begin, n_mem;  // per instance
+    int64_t C = 0, M = 0;
+    DevBuf cand;  // [cand_off (C+1) | cand_trial | cand_key | cand_cnt | members]
+    int64_t *cand_off() const { return cand.as<int64_t>(); }
+    int32_t *cand_trial() const { return reinterpret_cast<int32_t *>(cand_off() + C + 1); }
+    uint32_t *cand_key() const { return reinterpret_cast<uint32_t *>(cand_trial() + C); }
+    int32_t *cand_cnt() const { return reinterpret_cast<int32_t *>(cand_key() + C); }
+    int32_t *members() const { return cand_cnt() + C; }
+};
+
+// All trials of all instances: one count launch, a scan, one synchronisation
+// to size the lists, one fill launch.
+int run_hash_batch(const std::vector<HashInstSpec> &spec, HashBatchOut &out, cudaStream_t st);
+
+// Per-instance view used by the batched theta^0, background and finalise
+// kernels (device copy); positions are into the whole packed input.
+struct BatchInst {
+    const int32_t *seq_off;   // [t+1]
+    const int32_t *lmer_off;  // [t+1]
+    const double *bg;         // [4]
+    int t, l;
+    int64_t cand_begin, C;
+    int64_t sites_off;        // first entry of its sites in the batch's sites array
+    int64_t cons_off;         // first letter of its consensus in the batch's consensus array
+};
+int launch_theta0_batch(const uint32_t *packed, int64_t nwords, const BatchInst *inst, int n_inst,
+                        const int64_t *cand_off, const int32_t *members, int64_t C, float beta,
+                        int stride, float *theta0, cudaStream_t st);
+int launch_finalize_batch(const uint32_t *packed, int64_t nwords, const BatchInst *inst,
+                          int n_inst, const float *theta, int stride, const double *ll,
+                          int64_t *best, int32_t *sites, uint8_t *consensus, int32_t *score,
+                          cudaStream_t st);
+int launch_background_batch(const uint32_t *packed, const int64_t *base_range, int n_inst,
+                            double *bg, cudaStream_t st);
+
 int launch_theta0(const uint32_t *packed, const Layout &L, const int64_t *cand_off,
                   const int32_t *members, int64_t C, float beta, float *theta0, cudaStream_t st);
 

@@ -186,9 +186,9 @@ __global__ void em_reduce_kernel(const double *__restrict__ part_acc,
 // ---------------------------------------------------------------------------
 // Ranking and finalisation (one CTA).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) finalize_kernel(
+__device__ __forceinline__ void finalize_body(
     const uint32_t *__restrict__ packed, int64_t nwords, const int32_t *__restrict__ seq_off,
-    int t, int l, const double *__restrict__ bg, const float *__restrict__ theta,
+    int t, int l, const double *__restrict__ bg, const float *__restrict__ theta, int stride,
     const double *__restrict__ ll, int64_t C, int64_t *__restrict__ best_out,
     int32_t *__restrict__ sites, uint8_t *__restrict__ consensus, int32_t *__restrict__ score) {
     __shared__ double s_v[32];
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(
         for (int p = tid; p < l; p += blockDim.x) consensus[p] = 'N';
         return;
     }
-    const float *th = theta + b * (int64_t)(4 * l);
+    const float *th = theta + b * (int64_t)stride;
     if (tid < 4 * l) W[tid] = log((double)th[tid]) - log(bg[tid & 3]);
     if (tid < l) {
         int a = 0;
@@ -281,6 +281,62 @@ __global__ void __launch_bounds__(1024) finalize_kernel(
         for (int w = 0; w < (int)(blockDim.x / 32); ++w) sc += s_score[w];
         *score = sc;
     }
+}
+
+__global__ void __launch_bounds__(1024) finalize_kernel(
+    const uint32_t *__restrict__ packed, int64_t nwords, const int32_t *__restrict__ seq_off,
+    int t, int l, const double *__restrict__ bg, const float *__restrict__ theta,
+    const double *__restrict__ ll, int64_t C, int64_t *__restrict__ best_out,
+    int32_t *__restrict__ sites, uint8_t *__restrict__ consensus, int32_t *__restrict__ score) {
+    finalize_body(packed, nwords, seq_off, t, l, bg, theta, 4 * l, ll, C, best_out, sites,
+                  consensus, score);
+}
+
+// One CTA per instance of a batch.
+__global__ void __launch_bounds__(1024) finalize_batch_kernel(
+    const uint32_t *__restrict__ packed, int64_t nwords, const BatchInst *__restrict__ inst,
+    const float *__restrict__ theta, int stride, const double *__restrict__ ll,
+    int64_t *__restrict__ best_out, int32_t *__restrict__ sites, uint8_t *__restrict__ consensus,
+    int32_t *__restrict__ score) {
+    const BatchInst in = inst[blockIdx.x];
+    finalize_body(packed, nwords, in.seq_off, in.t, in.l, in.bg, theta + in.cand_begin * stride,
+                  stride, ll + in.cand_begin, in.C, best_out + blockIdx.x, sites + in.sites_off,
+                  consensus + in.cons_off, score + blockIdx.x);
+}
+
+// theta^0 for the candidates of all instances of a batch (models at `stride`).
+__global__ void theta0_batch_kernel(const uint32_t *__restrict__ packed, int64_t nwords,
+                                    const BatchInst *__restrict__ inst, int n_inst,
+                                    const int64_t *__restrict__ cand_off,
+                                    const int32_t *__restrict__ members, int64_t C, float beta,
+                                    int stride, float *__restrict__ theta0) {
+    extern __shared__ float cnt[];  // [stride][blockDim]
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t c = blockIdx.x * (int64_t)nt + tid;
+    for (int q = 0; q < stride; ++q) cnt[q * nt + tid] = 0.f;
+    if (c >= C) return;
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (inst[mid].cand_begin <= c) lo = mid; else hi = mid - 1;
+    }
+    const BatchInst in = inst[lo];
+    const int l = in.l;
+    const int64_t e0 = cand_off[c], e1 = cand_off[c + 1];
+    for (int64_t e = e0; e < e1; ++e) {
+        const int g = members[e];
+        int a = 0, b = in.t - 1;  // last sequence with lmer_off <= g
+        while (a < b) {
+            const int mid = (a + b + 1) >> 1;
+            if (__ldg(in.lmer_off + mid) <= g) a = mid; else b = mid - 1;
+        }
+        const int64_t b0 = (int64_t)__ldg(in.seq_off + a) + (g - __ldg(in.lmer_off + a));
+        const uint64_t win = window64(packed, nwords, b0);
+        for (int p = 0; p < l; ++p) cnt[(p * 4 + (int)((win >> (2 * p)) & 3u)) * nt + tid] += 1.f;
+    }
+    const float den = (float)(e1 - e0) + 4.f * beta;
+    for (int q = 0; q < stride; ++q)
+        theta0[c * stride + q] = q < 4 * l ? (cnt[q * nt + tid] + beta) / den : 0.f;
 }
 
 template <int LMAX>
@@ -369,6 +425,36 @@ int run_em(const uint32_t *packed, const Layout &L, const double *bg, const floa
     }
     PROJ_CUDA_TRY(cudaMemcpyAsync(theta_out, tmp.as<float>(), (size_t)C * L4 * sizeof(float),
                                   cudaMemcpyDeviceToDevice, st));
+    return PROJ_OK;
+}
+
+int launch_theta0_batch(const uint32_t *packed, int64_t nwords, const BatchInst *inst, int n_inst,
+                        const int64_t *cand_off, const int32_t *members, int64_t C, float beta,
+                        int stride, float *theta0, cudaStream_t st) {
+    if (C == 0) return PROJ_OK;
+    const int nt = 128;
+    const size_t smem = (size_t)stride * nt * sizeof(float);
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(theta0_batch_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+        TraceSpan ts_("theta0", st);
+        theta0_batch_kernel<<<(unsigned)((C + nt - 1) / nt), nt, smem, st>>>(
+            packed, nwords, inst, n_inst, cand_off, members, C, beta, stride, theta0);
+    }
+    PROJ_LAUNCH_CHECK("theta0_batch_kernel");
+    return PROJ_OK;
+}
+
+int launch_finalize_batch(const uint32_t *packed, int64_t nwords, const BatchInst *inst,
+                          int n_inst, const float *theta, int stride, const double *ll,
+                          int64_t *best, int32_t *sites, uint8_t *consensus, int32_t *score,
+                          cudaStream_t st) {
+    {
+        TraceSpan ts_("finalize", st);
+        finalize_batch_kernel<<<n_inst, 1024, 0, st>>>(packed, nwords, inst, theta, stride, ll, best,
+                                                       sites, consensus, score);
+    }
+    PROJ_LAUNCH_CHECK("finalize_batch_kernel");
     return PROJ_OK;
 }
 

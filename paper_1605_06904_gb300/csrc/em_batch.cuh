@@ -1,0 +1,45 @@
+// Instance and work-item descriptors of the tensor-core EM kernel, shared by
+// the single-search and batched entry points.
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace proj {
+
+// One motif-search instance as the EM kernel sees it (device copy).
+struct EmInst {
+    const int32_t *seq_off;  // [t+1] positions of its sequences in the packed input
+    const double *bg;        // [4] its background frequencies
+    int t, l;
+    int64_t cand_begin;      // index of its first candidate in the candidate arrays
+};
+
+// One unit of EM work: up to 128 candidates of one instance against one
+// contiguous range of that instance's sequences (group g of G).
+struct EmItem {
+    int64_t c0;      // first candidate (global index)
+    int nc;          // candidates in this item (<= 128)
+    int inst;        // instance index
+    int seq_lo, seq_hi;
+    int g;           // sequence group, selects the partial-result slot
+};
+
+// Host-side summary used to plan the items.
+struct EmInstHost {
+    int t = 0, l = 0;
+    int64_t C = 0, cand_begin = 0;
+};
+
+int em_tc_plan(const std::vector<EmInstHost> &insts, std::vector<EmItem> &items, int &G);
+
+// Runs iters EM iterations + a final E-step for the candidates of all
+// instances (models theta0[C][stride], stride >= 4l of each instance).
+int run_em_tc_batch(const uint32_t *packed, int64_t nwords, const std::vector<EmInstHost> &insts,
+                    const EmInst *inst_dev, const float *theta0, int64_t C, int stride, int iters,
+                    float beta, float *theta_out, double *ll, cudaStream_t st);
+
+}  // namespace proj

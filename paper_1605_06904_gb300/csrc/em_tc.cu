@@ -8,19 +8,23 @@
 // Z [C x x] with the same X.  Together they have the shape of attention with
 // one-hot keys and values: per sequence a softmax over the starts j.
 //
-// One CTA (128 threads) owns 128 candidates = the 128 lanes of tensor memory
-// and one group of sequences.  Per tile of NT l-mers of one sequence:
-//   1. the CTA writes the one-hot tile X [NT x KP] to shared memory;
-//   2. one thread issues S = W_hi X^T + W_lo X^T (M=128, N=NT, K=KP, FP32
-//      accumulation in tensor memory; W split into BF16 hi + lo parts so the
-//      product carries ~16 mantissa bits of W);
+// Work is a list of items, each = (instance, up to 128 candidates of it, a
+// range of its sequences); a CTA (128 threads = the 128 lanes of tensor
+// memory) takes items in turn from the list (persistent over the list when the
+// grid is smaller than it), so one launch serves one motif search or a batch of
+// many instances of different t, n and l.  Per tile of NT l-mers of a sequence:
+//   1. the CTA writes the one-hot tile X [NT x 4l] to shared memory (from the
+//      sequence's packed words, staged in shared memory);
+//   2. one thread issues S = W_hi X^T + W_lo X^T (M=128, N=NT, K=16*ceil(4l/16),
+//      FP32 accumulation in tensor memory; W split into BF16 hi + lo parts so
+//      the product carries ~16 mantissa bits of W);
 //   3. thread i reads row i of S, keeps a running maximum and a compensated
 //      running sum of 2^(S - max) for its candidate, rescales its row of O when
 //      the maximum grows, and writes P = 2^(S - max) as BF16 hi + lo parts;
-//   4. one thread issues O += P_hi X + P_lo X (M=128, N=KP, K=NT) with X read
-//      in MN-major form from the same shared-memory tile.
-// At the end of a sequence O / sum is added (FP64) to the candidate's counts
-// and max + log2(sum) to its log-likelihood.  Scores are kept in log2 units
+//   4. one thread issues O += P_hi X + P_lo X (M=128, N=16*ceil(4l/16), K=NT)
+//      with X read in MN-major form from the same shared-memory tile.
+// At the end of a sequence O / sum is added to the candidate's counts and
+// max + log2(sum) to its log-likelihood.  Scores are kept in log2 units
 // (W = log2 theta - log2 bg) so the exponentials are exp2.
 //
 // Every wait on an MMA completion is bounded; when a bound expires the CTA
@@ -29,8 +33,10 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
+#include "em_batch.cuh"
 #include "tc.cuh"
 
 namespace proj {
@@ -42,11 +48,12 @@ constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait on a tensor-core co
 struct EmTcParams {
     const uint32_t *packed;
     int64_t nwords;
-    const int32_t *seq_off;
-    int t, l, G;
-    const double *bg;
-    const float *theta_in;  // [C][l][4]
-    double *part_acc;       // [G][C][4l]
+    const EmInst *inst;     // [n_inst]
+    const EmItem *items;    // [n_items]
+    int n_items;
+    const float *theta_in;  // [C][stride]
+    int stride;             // floats per candidate model (>= 4l of its instance)
+    double *part_acc;       // [G][C][stride]; G == 1 when no candidate tile is split
     double *part_ll;        // [G][C]
     int64_t C;
     int mstep;
@@ -88,46 +95,16 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 template <int KP, int NT>
-__global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
+__global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 3 : 2)) em_tc_kernel(const EmTcParams P) {
     using LY = TcLayout<KP, NT>;
-    extern __shared__ __align__(1024) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int l = P.l, L4 = 4 * l;
-    const int64_t c = (int64_t)blockIdx.x * kTcThreads + tid;
-    const bool valid = c < P.C;
-    const int g = blockIdx.y;
     uint8_t *sWhi = smem + LY::OFF_WHI, *sWlo = smem + LY::OFF_WLO, *sX = smem + LY::OFF_X;
     uint8_t *sPhi = smem + LY::OFF_PHI, *sPlo = smem + LY::OFF_PLO;
+    uint32_t *sSeq = reinterpret_cast<uint32_t *>(smem + LY::OFF_SEQ);
 
-    // W_c = log2 theta_c - log2 bg in FP32 (~2^-23 relative, far below the
-    // 2^-16 of the BF16 hi + lo pair), split into BF16 hi + lo (row tid, K-major)
-    float lbg[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) lbg[a] = log2f((float)P.bg[a]);
-    for (int k8 = 0; k8 < KP; k8 += 8) {
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-            float h2[2], l2[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int k = k8 + q + u;
-                float w = 0.f;
-                if (valid && k < L4) w = log2f(__ldg(P.theta_in + c * L4 + k)) - lbg[k & 3];
-                const float h = __bfloat162float(__float2bfloat16_rn(w));
-                h2[u] = h;
-                l2[u] = w - h;
-            }
-            hi[q / 2] = pack_bf16(h2[0], h2[1]);
-            lo[q / 2] = pack_bf16(l2[0], l2[1]);
-        }
-        *reinterpret_cast<uint4 *>(sWhi + tc::kmajor_off(tid, k8, KP)) =
-            make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4 *>(sWlo + tc::kmajor_off(tid, k8, KP)) =
-            make_uint4(lo[0], lo[1], lo[2], lo[3]);
-    }
     if (tid == 0) {
         tc::mbar_init(&mbar, 1);
         tc::mbar_fence_init();
@@ -136,7 +113,6 @@ __global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
         tc::tmem_alloc(&tmem_slot, LY::TMEM_COLS);
         tc::tmem_relinquish();
     }
-    tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -146,194 +122,245 @@ __global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
     const uint32_t aWhi = tc::smem_addr(sWhi), aWlo = tc::smem_addr(sWlo);
     const uint32_t aX = tc::smem_addr(sX), aPhi = tc::smem_addr(sPhi), aPlo = tc::smem_addr(sPlo);
     constexpr uint32_t IDESC_S = tc::idesc_bf16(128, NT);
-    constexpr uint32_t IDESC_O = tc::idesc_bf16(128, KP, true);
-
-    // this group's normalised counts of candidate c, summed over its sequences
-    float tot[KP];
-#pragma unroll
-    for (int q = 0; q < KP; ++q) tot[q] = 0.f;
-    uint32_t *sSeq = reinterpret_cast<uint32_t *>(smem + LY::OFF_SEQ);
-    double ll = 0.0;
     uint32_t phase = 0;
     bool abort = false;
 
-    const int i0 = (int)((int64_t)P.t * g / P.G), i1 = (int)((int64_t)P.t * (g + 1) / P.G);
-    for (int i = i0; i < i1 && !abort; ++i) {
-        const int64_t base = P.seq_off[i];
-        const int ns = P.seq_off[i + 1] - P.seq_off[i] - l + 1;
-        float m = -INFINITY, Ssum = 0.f, Scmp = 0.f;
-        bool first = true;
-        // packed words covering this sequence (+2 for the 64-bit windows)
-        const int64_t w_first = base >> 4;
-        const int nw_seq = (int)(((base + P.seq_off[i + 1] - P.seq_off[i] + 15) >> 4) - w_first) + 2;
-        const bool staged = nw_seq <= LY::SEQ_WORDS;
-        __syncthreads();  // the previous sequence's words are no longer read
-        if (staged)
-            for (int w = tid; w < nw_seq; w += kTcThreads)
-                sSeq[w] = (w_first + w) < P.nwords ? __ldg(P.packed + w_first + w) : 0u;
-        __syncthreads();
-        for (int j0 = 0; j0 < ns; j0 += NT) {
-            const int nvalid = min(NT, ns - j0);
-            // 1. one-hot tile X[j][p*4+a] = [x_{j0+j+p} = a]
-            for (int item = tid; item < NT * (KP / 8); item += kTcThreads) {
-                const int j = item % NT, kb = item / NT;
-                // two positions per 16-byte chunk: p = 2kb (words 0-1), 2kb+1 (words 2-3);
-                // BF16 1.0 (0x3F80) in the slot of the base's code
-                uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
-                if (j < nvalid) {
-                    const uint64_t win =
-                        staged ? window64(sSeq, nw_seq, base + j0 + j - (w_first << 4))
-                               : window64(P.packed, P.nwords, base + j0 + j);
-                    const int p0 = 2 * kb, p1 = 2 * kb + 1;
-                    if (p0 < l) {
-                        const uint32_t code = (uint32_t)(win >> (2 * p0)) & 3u;
-                        const uint32_t v = 0x3F80u << (16 * (code & 1u));
-                        if (code >> 1) w1 = v; else w0 = v;
-                    }
-                    if (p1 < l) {
-                        const uint32_t code = (uint32_t)(win >> (2 * p1)) & 3u;
-                        const uint32_t v = 0x3F80u << (16 * (code & 1u));
-                        if (code >> 1) w3 = v; else w2 = v;
-                    }
+    for (int it = blockIdx.x; it < P.n_items && !abort; it += gridDim.x) {
+        const EmItem item = P.items[it];
+        const EmInst in = P.inst[item.inst];
+        const int l = in.l, L4 = 4 * l;
+        const int kq = (L4 + 15) / 16;  // K steps of the score MMA = N / 16 of the count MMA
+        const uint32_t idesc_o = tc::idesc_bf16(128, 16 * kq, true);
+        const int64_t c = item.c0 + tid;
+        const bool valid = tid < item.nc;
+
+        // W_c = log2 theta_c - log2 bg in FP32 (~2^-23 relative, far below the
+        // 2^-16 of the BF16 hi + lo pair), split into BF16 hi + lo (row tid)
+        __syncthreads();  // the previous item's MMAs and reads are complete
+        float lbg[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) lbg[a] = log2f((float)in.bg[a]);
+        for (int k8 = 0; k8 < KP; k8 += 8) {
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+                float h2[2], l2[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int k = k8 + q + u;
+                    float w = 0.f;
+                    if (valid && k < L4) w = log2f(__ldg(P.theta_in + c * P.stride + k)) - lbg[k & 3];
+                    const float h = __bfloat162float(__float2bfloat16_rn(w));
+                    h2[u] = h;
+                    l2[u] = w - h;
                 }
-                *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(j, 8 * kb, KP)) =
-                    make_uint4(w0, w1, w2, w3);
+                hi[q / 2] = pack_bf16(h2[0], h2[1]);
+                lo[q / 2] = pack_bf16(l2[0], l2[1]);
             }
-            tc::fence_async_smem();
+            *reinterpret_cast<uint4 *>(sWhi + tc::kmajor_off(tid, k8, KP)) =
+                make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4 *>(sWlo + tc::kmajor_off(tid, k8, KP)) =
+                make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+        tc::fence_async_smem();
+
+        // this item's normalised counts of candidate c, summed over its sequences
+        float tot[KP];
+#pragma unroll
+        for (int q = 0; q < KP; ++q) tot[q] = 0.f;
+        double ll = 0.0;
+
+        for (int i = item.seq_lo; i < item.seq_hi && !abort; ++i) {
+            const int64_t base = in.seq_off[i];
+            const int n_i = in.seq_off[i + 1] - in.seq_off[i];
+            const int ns = n_i - l + 1;
+            float m = -INFINITY, Ssum = 0.f, Scmp = 0.f;
+            bool first = true;
+            // packed words covering this sequence (+2 for the 64-bit windows)
+            const int64_t w_first = base >> 4;
+            const int nw_seq = (int)(((base + n_i + 15) >> 4) - w_first) + 2;
+            const bool staged = nw_seq <= LY::SEQ_WORDS;
+            __syncthreads();  // the previous sequence's words are no longer read
+            if (staged)
+                for (int w = tid; w < nw_seq; w += kTcThreads)
+                    sSeq[w] = (w_first + w) < P.nwords ? __ldg(P.packed + w_first + w) : 0u;
             __syncthreads();
-            // 2. S = W_hi X^T + W_lo X^T
-            if (tid == 0) {
-                tc::fence_after_sync();
-#pragma unroll
-                for (int s = 0; s < KP / 16; ++s)
-                    tc::mma_bf16(tS, tc::sdesc(aWhi + 256 * s, 128, KP * 16),
-                                 tc::sdesc(aX + 256 * s, 128, KP * 16), IDESC_S, s > 0);
-#pragma unroll
-                for (int s = 0; s < KP / 16; ++s)
-                    tc::mma_bf16(tS, tc::sdesc(aWlo + 256 * s, 128, KP * 16),
-                                 tc::sdesc(aX + 256 * s, 128, KP * 16), IDESC_S, 1);
-                tc::mma_commit(&mbar);
-            }
-            bool ok = tc::mbar_wait(&mbar, phase, kWaitNs);
-            phase ^= 1u;
-            abort = __syncthreads_or(!ok);
-            if (abort) break;
-            tc::fence_after_sync();
-            // 3. running max / compensated sum, P = 2^(S - max) as hi + lo
-            float tmax = -INFINITY;
-#pragma unroll
-            for (int c0 = 0; c0 < NT; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(tS + lane_base + c0, v);
-                float mx[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) mx[q] = -INFINITY;
-#pragma unroll
-                for (int q = 0; q < 32; ++q)
-                    if (nvalid == NT || c0 + q < nvalid) mx[q & 7] = fmaxf(mx[q & 7], v[q]);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) tmax = fmaxf(tmax, mx[q]);
-            }
-            // the maximum of each row may grow; the tensor-memory accesses below are
-            // .sync.aligned, so the rescale of O runs warp-uniformly (scale 1 for
-            // rows whose maximum did not grow)
-            const bool grow = tmax > m;
-            const float sc = grow ? ex2(m - tmax) : 1.f;  // 0 on the first tile (m = -inf)
-            if (grow) {
-                Ssum *= sc;
-                Scmp *= sc;
-                m = tmax;
-            }
-            if (P.mstep && !first && __any_sync(0xffffffffu, grow)) {
-#pragma unroll
-                for (int c0 = 0; c0 < KP; c0 += 16) {
-                    float v[16];
-                    tc::tmem_ld16(tO + lane_base + c0, v);
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] *= sc;
-                    tc::tmem_st16(tO + lane_base + c0, v);
-                }
-            }
-            // P = 2^(S - max): each 32-column chunk is summed as a tree (no long
-            // dependency chain) and the chunk sums are added with compensation
-            const bool full = nvalid == NT;  // only a sequence's last tile is ragged
-#pragma unroll
-            for (int c0 = 0; c0 < NT; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(tS + lane_base + c0, v);
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const float e = ex2(v[q] - m);
-                    v[q] = (full || c0 + q < nvalid) ? e : 0.f;
-                }
-                float part[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) part[q] = v[2 * q] + v[2 * q + 1];
-#pragma unroll
-                for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-                    for (int q = 0; q < w; ++q) part[q] += part[q + w];
-                kahan(Ssum, Scmp, part[0]);
-                if (P.mstep) {
-                    uint32_t hi[16], lo[16];
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const uint32_t h = pack_bf16(v[2 * q], v[2 * q + 1]);
-                        const float h0 = __uint_as_float(h << 16), h1 = __uint_as_float(h & 0xFFFF0000u);
-                        hi[q] = h;
-                        lo[q] = pack_bf16(v[2 * q] - h0, v[2 * q + 1] - h1);
+            for (int j0 = 0; j0 < ns; j0 += NT) {
+                const int nvalid = min(NT, ns - j0);
+                // 1. one-hot tile X[j][p*4+a] = [x_{j0+j+p} = a]
+                for (int item_x = tid; item_x < NT * (KP / 8); item_x += kTcThreads) {
+                    const int j = item_x % NT, kb = item_x / NT;
+                    // two positions per 16-byte chunk: p = 2kb (words 0-1), 2kb+1
+                    // (words 2-3); BF16 1.0 (0x3F80) in the slot of the base's code
+                    uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
+                    if (j < nvalid && 2 * kb < l) {
+                        const uint64_t win =
+                            staged ? window64(sSeq, nw_seq, base + j0 + j - (w_first << 4))
+                                   : window64(P.packed, P.nwords, base + j0 + j);
+                        const int p0 = 2 * kb, p1 = 2 * kb + 1;
+                        {
+                            const uint32_t code = (uint32_t)(win >> (2 * p0)) & 3u;
+                            const uint32_t v = 0x3F80u << (16 * (code & 1u));
+                            if (code >> 1) w1 = v; else w0 = v;
+                        }
+                        if (p1 < l) {
+                            const uint32_t code = (uint32_t)(win >> (2 * p1)) & 3u;
+                            const uint32_t v = 0x3F80u << (16 * (code & 1u));
+                            if (code >> 1) w3 = v; else w2 = v;
+                        }
                     }
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        *reinterpret_cast<uint4 *>(sPhi + tc::kmajor_off(tid, c0 + 8 * b, NT)) =
-                            make_uint4(hi[4 * b], hi[4 * b + 1], hi[4 * b + 2], hi[4 * b + 3]);
-                        *reinterpret_cast<uint4 *>(sPlo + tc::kmajor_off(tid, c0 + 8 * b, NT)) =
-                            make_uint4(lo[4 * b], lo[4 * b + 1], lo[4 * b + 2], lo[4 * b + 3]);
-                    }
+                    *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(j, 8 * kb, KP)) =
+                        make_uint4(w0, w1, w2, w3);
                 }
-            }
-            tc::fence_before_sync();
-            if (P.mstep) {
-                // 4. O += P_hi X + P_lo X
                 tc::fence_async_smem();
                 __syncthreads();
+                // 2. S = W_hi X^T + W_lo X^T
                 if (tid == 0) {
                     tc::fence_after_sync();
-#pragma unroll
-                    for (int s = 0; s < NT / 16; ++s)
-                        tc::mma_bf16(tO, tc::sdesc(aPhi + 256 * s, 128, NT * 16),
-                                     tc::sdesc(aX + s * 2 * KP * 16, KP * 16, 128), IDESC_O,
-                                     (s > 0 || !first) ? 1u : 0u);
-#pragma unroll
-                    for (int s = 0; s < NT / 16; ++s)
-                        tc::mma_bf16(tO, tc::sdesc(aPlo + 256 * s, 128, NT * 16),
-                                     tc::sdesc(aX + s * 2 * KP * 16, KP * 16, 128), IDESC_O, 1u);
+                    for (int s = 0; s < kq; ++s)
+                        tc::mma_bf16(tS, tc::sdesc(aWhi + 256 * s, 128, KP * 16),
+                                     tc::sdesc(aX + 256 * s, 128, KP * 16), IDESC_S, s > 0);
+                    for (int s = 0; s < kq; ++s)
+                        tc::mma_bf16(tS, tc::sdesc(aWlo + 256 * s, 128, KP * 16),
+                                     tc::sdesc(aX + 256 * s, 128, KP * 16), IDESC_S, 1);
                     tc::mma_commit(&mbar);
                 }
-                ok = tc::mbar_wait(&mbar, phase, kWaitNs);
+                bool ok = tc::mbar_wait(&mbar, phase, kWaitNs);
                 phase ^= 1u;
                 abort = __syncthreads_or(!ok);
                 if (abort) break;
                 tc::fence_after_sync();
-            } else {
-                __syncthreads();  // every row of S is read before the next tile rewrites it
+                // 3. running max / compensated sum, P = 2^(S - max) as hi + lo
+                float tmax = -INFINITY;
+#pragma unroll
+                for (int c0 = 0; c0 < NT; c0 += 32) {
+                    float v[32];
+                    tc::tmem_ld32(tS + lane_base + c0, v);
+                    float mx[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) mx[q] = -INFINITY;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        if (nvalid == NT || c0 + q < nvalid) mx[q & 7] = fmaxf(mx[q & 7], v[q]);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) tmax = fmaxf(tmax, mx[q]);
+                }
+                // the maximum of each row may grow; the tensor-memory accesses below
+                // are .sync.aligned, so the rescale of O runs warp-uniformly (scale 1
+                // for rows whose maximum did not grow)
+                const bool grow = tmax > m;
+                const float sc = grow ? ex2(m - tmax) : 1.f;  // 0 on the first tile
+                if (grow) {
+                    Ssum *= sc;
+                    Scmp *= sc;
+                    m = tmax;
+                }
+                if (P.mstep && !first && __any_sync(0xffffffffu, grow)) {
+#pragma unroll
+                    for (int c0 = 0; c0 < KP; c0 += 16) {
+                        if (c0 < 16 * kq) {
+                            float v[16];
+                            tc::tmem_ld16(tO + lane_base + c0, v);
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) v[q] *= sc;
+                            tc::tmem_st16(tO + lane_base + c0, v);
+                        }
+                    }
+                }
+                // P = 2^(S - max): each 32-column chunk is summed as a tree (no long
+                // dependency chain) and the chunk sums are added with compensation
+                const bool full = nvalid == NT;  // only a sequence's last tile is ragged
+#pragma unroll
+                for (int c0 = 0; c0 < NT; c0 += 32) {
+                    float v[32];
+                    tc::tmem_ld32(tS + lane_base + c0, v);
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const float e = ex2(v[q] - m);
+                        v[q] = (full || c0 + q < nvalid) ? e : 0.f;
+                    }
+                    float part[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) part[q] = v[2 * q] + v[2 * q + 1];
+#pragma unroll
+                    for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                        for (int q = 0; q < w; ++q) part[q] += part[q + w];
+                    kahan(Ssum, Scmp, part[0]);
+                    if (P.mstep) {
+                        uint32_t hi[16], lo[16];
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const uint32_t h = pack_bf16(v[2 * q], v[2 * q + 1]);
+                            const float h0 = __uint_as_float(h << 16);
+                            const float h1 = __uint_as_float(h & 0xFFFF0000u);
+                            hi[q] = h;
+                            lo[q] = pack_bf16(v[2 * q] - h0, v[2 * q + 1] - h1);
+                        }
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            *reinterpret_cast<uint4 *>(sPhi + tc::kmajor_off(tid, c0 + 8 * b, NT)) =
+                                make_uint4(hi[4 * b], hi[4 * b + 1], hi[4 * b + 2], hi[4 * b + 3]);
+                            *reinterpret_cast<uint4 *>(sPlo + tc::kmajor_off(tid, c0 + 8 * b, NT)) =
+                                make_uint4(lo[4 * b], lo[4 * b + 1], lo[4 * b + 2], lo[4 * b + 3]);
+                        }
+                    }
+                }
+                tc::fence_before_sync();
+                if (P.mstep) {
+                    // 4. O += P_hi X + P_lo X
+                    tc::fence_async_smem();
+                    __syncthreads();
+                    if (tid == 0) {
+                        tc::fence_after_sync();
+#pragma unroll
+                        for (int s = 0; s < NT / 16; ++s)
+                            tc::mma_bf16(tO, tc::sdesc(aPhi + 256 * s, 128, NT * 16),
+                                         tc::sdesc(aX + s * 2 * KP * 16, KP * 16, 128), idesc_o,
+                                         (s > 0 || !first) ? 1u : 0u);
+#pragma unroll
+                        for (int s = 0; s < NT / 16; ++s)
+                            tc::mma_bf16(tO, tc::sdesc(aPlo + 256 * s, 128, NT * 16),
+                                         tc::sdesc(aX + s * 2 * KP * 16, KP * 16, 128), idesc_o, 1u);
+                        tc::mma_commit(&mbar);
+                    }
+                    ok = tc::mbar_wait(&mbar, phase, kWaitNs);
+                    phase ^= 1u;
+                    abort = __syncthreads_or(!ok);
+                    if (abort) break;
+                    tc::fence_after_sync();
+                } else {
+                    __syncthreads();  // every row of S is read before the next tile rewrites it
+                }
+                first = false;
             }
-            first = false;
+            if (abort) break;
+            const float Sf = Ssum - Scmp;
+            ll += (double)((m + log2f(Sf)) * 0.69314718f - logf((float)ns));
+            if (P.mstep) {
+                const float inv = 1.f / Sf;
+#pragma unroll
+                for (int c0 = 0; c0 < KP; c0 += 16) {
+                    if (c0 < 16 * kq) {
+                        float v[16];
+                        tc::tmem_ld16(tO + lane_base + c0, v);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) tot[c0 + q] += v[q] * inv;
+                    }
+                }
+                tc::fence_before_sync();
+                __syncthreads();  // O is read before the next sequence restarts it
+            }
         }
         if (abort) break;
-        const float Sf = Ssum - Scmp;
-        ll += (double)((m + log2f(Sf)) * 0.69314718f - logf((float)ns));
-        if (P.mstep) {
-            const float inv = 1.f / Sf;
+        if (valid) {
+            P.part_ll[(int64_t)item.g * P.C + c] = ll;
+            if (P.mstep) {
+                double *dst = P.part_acc + ((int64_t)item.g * P.C + c) * P.stride;
 #pragma unroll
-            for (int c0 = 0; c0 < KP; c0 += 16) {
-                float v[16];
-                tc::tmem_ld16(tO + lane_base + c0, v);
-#pragma unroll
-                for (int q = 0; q < 16; ++q) tot[c0 + q] += v[q] * inv;
+                for (int q = 0; q < KP; ++q)
+                    if (q < L4) dst[q] = (double)tot[q];
             }
-            tc::fence_before_sync();
-            __syncthreads();  // O is read before the next sequence restarts it
         }
     }
     if (abort) {
@@ -341,14 +368,6 @@ __global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
         // let any MMA still in flight finish (bounded) before freeing its memory:
         // the phase that was being waited for has parity phase ^ 1
         tc::mbar_wait(&mbar, phase ^ 1u, kWaitNs);
-    } else if (valid) {
-        P.part_ll[(int64_t)g * P.C + c] = ll;
-        if (P.mstep) {
-            double *dst = P.part_acc + ((int64_t)g * P.C + c) * L4;
-#pragma unroll
-            for (int q = 0; q < KP; ++q)
-                if (q < L4) dst[q] = (double)tot[q];
-        }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -358,29 +377,39 @@ __global__ void __launch_bounds__(kTcThreads) em_tc_kernel(const EmTcParams P) {
     }
 }
 
+// M-step theta = (sum_g counts + pseudocount) / (t + 4 pseudocount) and the
+// log-likelihood sum over the G sequence groups, in group order.
 __global__ void em_tc_reduce_kernel(const double *__restrict__ part_acc,
-                                    const double *__restrict__ part_ll, int G, int64_t C, int L4,
-                                    int t, float beta, int mstep, float *__restrict__ theta_out,
+                                    const double *__restrict__ part_ll, int G, int64_t C,
+                                    int stride, const EmInst *__restrict__ inst, int n_inst,
+                                    float beta, int mstep, float *__restrict__ theta_out,
                                     double *__restrict__ ll_out) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (mstep && idx < C * L4) {
-        double s = 0.0;
-        for (int g = 0; g < G; ++g) s += part_acc[(int64_t)g * C * L4 + idx];
-        theta_out[idx] = (float)((s + (double)beta) / ((double)t + 4.0 * (double)beta));
+    if (idx >= C * (mstep ? stride : 1)) return;
+    const int64_t c = mstep ? idx / stride : idx;
+    const int q = mstep ? (int)(idx % stride) : 0;
+    int lo = 0, hi = n_inst - 1;  // instance of candidate c
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (inst[mid].cand_begin <= c) lo = mid; else hi = mid - 1;
     }
-    if (idx < C) {
+    if (mstep && q < 4 * inst[lo].l) {
         double s = 0.0;
-        for (int g = 0; g < G; ++g) s += part_ll[(int64_t)g * C + idx];
-        ll_out[idx] = s;
+        for (int g = 0; g < G; ++g) s += part_acc[((int64_t)g * C + c) * stride + q];
+        theta_out[idx] = (float)((s + (double)beta) / ((double)inst[lo].t + 4.0 * (double)beta));
+    }
+    if (q == 0) {
+        double s = 0.0;
+        for (int g = 0; g < G; ++g) s += part_ll[(int64_t)g * C + c];
+        ll_out[c] = s;
     }
 }
 
 template <int KP, int NT>
-int launch_tc(const EmTcParams &P, cudaStream_t st) {
+int launch_tc(const EmTcParams &P, int grid, cudaStream_t st) {
     using LY = TcLayout<KP, NT>;
     PROJ_CUDA_TRY(cudaFuncSetAttribute(em_tc_kernel<KP, NT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, LY::TOTAL));
-    dim3 grid((unsigned)((P.C + kTcThreads - 1) / kTcThreads), (unsigned)P.G);
     {
         TraceSpan ts_("em_tc", st);
         em_tc_kernel<KP, NT><<<grid, kTcThreads, LY::TOTAL, st>>>(P);
@@ -389,77 +418,120 @@ int launch_tc(const EmTcParams &P, cudaStream_t st) {
     return PROJ_OK;
 }
 
-template <int NT>
-int ctas_per_sm(int kp) {
-    int smem = 0;
-    switch (kp) {
-        case 16: smem = TcLayout<16, NT>::TOTAL; break;
-        case 32: smem = TcLayout<32, NT>::TOTAL; break;
-        case 48: smem = TcLayout<48, NT>::TOTAL; break;
-        case 64: smem = TcLayout<64, NT>::TOTAL; break;
-        case 80: smem = TcLayout<80, NT>::TOTAL; break;
-        case 96: smem = TcLayout<96, NT>::TOTAL; break;
-        case 112: smem = TcLayout<112, NT>::TOTAL; break;
-        default: smem = TcLayout<128, NT>::TOTAL; break;
-    }
-    const int cols = (NT + kp <= 128) ? 128 : 256;
-    return std::max(1, std::min(228 * 1024 / (smem + 1024), 512 / cols));
+template <int KP>
+int ctas_per_sm_kp() {
+    using LY = TcLayout<KP, 64>;
+    const int by_smem = 228 * 1024 / (LY::TOTAL + 1024 + 128);
+    const int by_tmem = 512 / (int)LY::TMEM_COLS;
+    return std::max(1, std::min(by_smem, by_tmem));
 }
 
-int dispatch(int kp, const EmTcParams &P, cudaStream_t st) {
+int ctas_per_sm(int kp) {
     switch (kp) {
-        case 16: return launch_tc<16, 64>(P, st);
-        case 32: return launch_tc<32, 64>(P, st);
-        case 48: return launch_tc<48, 64>(P, st);
-        case 64: return launch_tc<64, 64>(P, st);
-        case 80: return launch_tc<80, 64>(P, st);
-        case 96: return launch_tc<96, 64>(P, st);
-        case 112: return launch_tc<112, 64>(P, st);
-        default: return launch_tc<128, 64>(P, st);
+        case 16: return ctas_per_sm_kp<16>();
+        case 32: return ctas_per_sm_kp<32>();
+        case 48: return ctas_per_sm_kp<48>();
+        case 64: return ctas_per_sm_kp<64>();
+        case 80: return ctas_per_sm_kp<80>();
+        case 96: return ctas_per_sm_kp<96>();
+        case 112: return ctas_per_sm_kp<112>();
+        default: return ctas_per_sm_kp<128>();
+    }
+}
+
+int dispatch(int kp, const EmTcParams &P, int grid, cudaStream_t st) {
+    switch (kp) {
+        case 16: return launch_tc<16, 64>(P, grid, st);
+        case 32: return launch_tc<32, 64>(P, grid, st);
+        case 48: return launch_tc<48, 64>(P, grid, st);
+        case 64: return launch_tc<64, 64>(P, grid, st);
+        case 80: return launch_tc<80, 64>(P, grid, st);
+        case 96: return launch_tc<96, 64>(P, grid, st);
+        case 112: return launch_tc<112, 64>(P, grid, st);
+        default: return launch_tc<128, 64>(P, grid, st);
     }
 }
 
 }  // namespace
 
-int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const float *theta0,
-              int64_t C, int iters, float beta, float *theta_out, double *ll, cudaStream_t st) {
-    const int L4 = 4 * L.l;
-    const int kp = 16 * ((L4 + 15) / 16);
-    const int64_t tiles = (C + kTcThreads - 1) / kTcThreads;
-    const int64_t want = (int64_t)sm_count() * ctas_per_sm<64>(kp) * 2;
-    const int G = (int)std::min<int64_t>(L.t, std::max<int64_t>(1, (want + tiles - 1) / tiles));
-    DevBuf part, tmp, flag;
-    PROJ_TRY(part.alloc((size_t)G * C * (L4 + 1) * sizeof(double), st));
-    PROJ_TRY(tmp.alloc((size_t)C * L4 * sizeof(float), st));
+int em_tc_plan(const std::vector<EmInstHost> &insts, std::vector<EmItem> &items, int &G) {
+    // split each instance's candidates into tiles of 128; when there are too
+    // few tiles to fill every SM a few times, split the sequences into G groups
+    int kp = 16;
+    int64_t tiles = 0;
+    for (const EmInstHost &h : insts) {
+        kp = std::max(kp, 16 * ((4 * h.l + 15) / 16));
+        tiles += (h.C + kTcThreads - 1) / kTcThreads;
+    }
+    const int64_t slots = (int64_t)sm_count() * ctas_per_sm(kp);
+    int tmin = 1 << 30;
+    for (const EmInstHost &h : insts) tmin = std::min(tmin, h.t);
+    G = 1;
+    if (tiles > 0 && tiles < 2 * slots)
+        G = (int)std::min<int64_t>(std::max(1, tmin), (2 * slots + tiles - 1) / tiles);
+    items.clear();
+    for (size_t ii = 0; ii < insts.size(); ++ii) {
+        const EmInstHost &h = insts[ii];
+        for (int64_t c0 = 0; c0 < h.C; c0 += kTcThreads)
+            for (int g = 0; g < G; ++g) {
+                EmItem it;
+                it.c0 = h.cand_begin + c0;
+                it.nc = (int)std::min<int64_t>(kTcThreads, h.C - c0);
+                it.inst = (int)ii;
+                it.seq_lo = (int)((int64_t)h.t * g / G);
+                it.seq_hi = (int)((int64_t)h.t * (g + 1) / G);
+                it.g = g;
+                items.push_back(it);
+            }
+    }
+    return kp;
+}
+
+int run_em_tc_batch(const uint32_t *packed, int64_t nwords, const std::vector<EmInstHost> &insts,
+                    const EmInst *inst_dev, const float *theta0, int64_t C, int stride, int iters,
+                    float beta, float *theta_out, double *ll, cudaStream_t st) {
+    if (C == 0) return PROJ_OK;
+    std::vector<EmItem> items;
+    int G = 1;
+    const int kp = em_tc_plan(insts, items, G);
+    PROJ_REQUIRE(kp <= 128, "l above 32 is not supported");
+    DevBuf part, tmp, flag, itemb;
+    PROJ_TRY(part.alloc((size_t)G * C * (stride + 1) * sizeof(double), st));
+    PROJ_TRY(tmp.alloc((size_t)C * stride * sizeof(float), st));
     PROJ_TRY(flag.alloc(sizeof(int), st));
+    PROJ_TRY(itemb.alloc(items.size() * sizeof(EmItem), st));
+    PROJ_CUDA_TRY(cudaMemcpyAsync(itemb.as<EmItem>(), items.data(), items.size() * sizeof(EmItem),
+                                  cudaMemcpyHostToDevice, st));
     PROJ_CUDA_TRY(cudaMemsetAsync(flag.as<int>(), 0, sizeof(int), st));
-    PROJ_CUDA_TRY(cudaMemcpyAsync(tmp.as<float>(), theta0, (size_t)C * L4 * sizeof(float),
+    PROJ_CUDA_TRY(cudaMemcpyAsync(tmp.as<float>(), theta0, (size_t)C * stride * sizeof(float),
                                   cudaMemcpyDeviceToDevice, st));
     EmTcParams P{};
     P.packed = packed;
-    P.nwords = L.nwords;
-    P.seq_off = L.seq_off_dev();
-    P.t = L.t;
-    P.l = L.l;
-    P.G = G;
-    P.bg = bg;
+    P.nwords = nwords;
+    P.inst = inst_dev;
+    P.items = itemb.as<EmItem>();
+    P.n_items = (int)items.size();
     P.theta_in = tmp.as<float>();
+    P.stride = stride;
     P.part_ll = part.as<double>();
     P.part_acc = part.as<double>() + (size_t)G * C;
     P.C = C;
     P.err = flag.as<int>();
+    const int grid = (int)std::min<int64_t>((int64_t)items.size(),
+                                            (int64_t)sm_count() * ctas_per_sm(kp));
     for (int it = 0; it <= iters; ++it) {
         P.mstep = it < iters;
-        PROJ_TRY(dispatch(kp, P, st));
-        const int64_t n = P.mstep ? C * L4 : C;
+        PROJ_TRY(dispatch(kp, P, grid, st));
+        const int64_t n = P.mstep ? C * stride : C;
         {
             TraceSpan ts_("em_reduce", st);
             em_tc_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-                P.part_acc, P.part_ll, G, C, L4, L.t, beta, P.mstep, tmp.as<float>(), ll);
+                P.part_acc, P.part_ll, G, C, stride, inst_dev, (int)insts.size(), beta, P.mstep,
+                tmp.as<float>(), ll);
         }
         PROJ_LAUNCH_CHECK("em_tc_reduce_kernel");
     }
-    PROJ_CUDA_TRY(cudaMemcpyAsync(theta_out, tmp.as<float>(), (size_t)C * L4 * sizeof(float),
+    PROJ_CUDA_TRY(cudaMemcpyAsync(theta_out, tmp.as<float>(), (size_t)C * stride * sizeof(float),
                                   cudaMemcpyDeviceToDevice, st));
     int err = 0;
     PROJ_CUDA_TRY(cudaMemcpyAsync(&err, flag.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -469,6 +541,26 @@ int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const f
         return PROJ_ETIMEOUT;
     }
     return PROJ_OK;
+}
+
+int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const float *theta0,
+              int64_t C, int iters, float beta, float *theta_out, double *ll, cudaStream_t st) {
+    std::vector<EmInstHost> insts(1);
+    insts[0].t = L.t;
+    insts[0].l = L.l;
+    insts[0].C = C;
+    insts[0].cand_begin = 0;
+    EmInst in{};
+    in.seq_off = L.seq_off_dev();
+    in.t = L.t;
+    in.l = L.l;
+    in.bg = bg;
+    in.cand_begin = 0;
+    DevBuf ib;
+    PROJ_TRY(ib.alloc(sizeof(EmInst), st));
+    PROJ_CUDA_TRY(cudaMemcpyAsync(ib.as<EmInst>(), &in, sizeof(EmInst), cudaMemcpyHostToDevice, st));
+    return run_em_tc_batch(packed, L.nwords, insts, ib.as<EmInst>(), theta0, C, 4 * L.l, iters,
+                           beta, theta_out, ll, st);
 }
 
 }  // namespace proj

@@ -120,12 +120,11 @@ __device__ inline void block_scan2(int a, int b, int &pa, int &pb, int &ta, int 
     __syncthreads();
 }
 
+// One (trial, key-range part) unit of the bucket kernels; `unit` indexes the
+// per-unit arrays of P (part_nb, part_nm, cand_base, mem_base).
 template <bool FILL>
-__global__ void __launch_bounds__(kThreads, 1) hash_kernel(const HashParams P) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ int s_pos[16];
-    __shared__ int2 s_warp[kWarps + 1];
-    __shared__ int s_round[kWarps + 1];
+__device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, uint8_t *smem,
+                                          int *s_pos, int2 *s_warp, int *s_round) {
 
     const SmemLayout S = smem_layout(P, FILL);
     uint32_t *hist32 = reinterpret_cast<uint32_t *>(smem);
@@ -137,8 +136,8 @@ __global__ void __launch_bounds__(kThreads, 1) hash_kernel(const HashParams P) {
         reinterpret_cast<uint32_t *>(smem + S.hist_bytes + S.bitmap_bytes + S.off_bytes);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int trial_local = blockIdx.x / P.parts;
-    const int part = blockIdx.x % P.parts;
+    const int trial_local = unit / P.parts;
+    const int part = unit % P.parts;
     const uint64_t trial = (uint64_t)(P.trial_begin + trial_local);
     const uint32_t lo_key = (uint32_t)part * (uint32_t)P.hb;
     const uint32_t hb = (uint32_t)P.hb;
@@ -216,15 +215,15 @@ __global__ void __launch_bounds__(kThreads, 1) hash_kernel(const HashParams P) {
 
     if (!FILL) {
         if (tid == 0) {
-            P.part_nb[blockIdx.x] = NB;
-            P.part_nm[blockIdx.x] = NM;
+            P.part_nb[unit] = NB;
+            P.part_nm[unit] = NM;
         }
         return;
     }
 
     // pass 2: candidate table in key order, bucket cursors, enriched bitmap
-    const int64_t cbase = P.cand_base[blockIdx.x];
-    const int64_t mbase = P.mem_base[blockIdx.x];
+    const int64_t cbase = P.cand_base[unit];
+    const int64_t mbase = P.mem_base[unit];
     for (int b = b_begin; b < b_end; ++b) {
         const int c = P.hist16 ? hist16[b] : (int)hist32[b];
         if (c >= P.s) {
@@ -311,6 +310,35 @@ __global__ void __launch_bounds__(kThreads, 1) hash_kernel(const HashParams P) {
             __syncwarp();
         }
     }
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(kThreads, 1) hash_kernel(const HashParams P) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ int s_pos[16];
+    __shared__ int2 s_warp[kWarps + 1];
+    __shared__ int s_round[kWarps + 1];
+    hash_unit<FILL>(P, (int)blockIdx.x, smem, s_pos, s_warp, s_round);
+}
+
+// Many instances in one launch: block u runs unit u - unit_begin[i] of the
+// instance i with unit_begin[i] <= u < unit_begin[i+1].  Each instance's
+// parameter block already points at its own slices of the per-unit arrays.
+template <bool FILL>
+__global__ void __launch_bounds__(kThreads, 1) hash_batch_kernel(const HashParams *__restrict__ insts,
+                                                                 const int64_t *__restrict__ unit_begin,
+                                                                 int n_inst) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ int s_pos[16];
+    __shared__ int2 s_warp[kWarps + 1];
+    __shared__ int s_round[kWarps + 1];
+    const int64_t u = blockIdx.x;
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (unit_begin[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    hash_unit<FILL>(insts[lo], (int)(u - unit_begin[lo]), smem, s_pos, s_warp, s_round);
 }
 
 // Exclusive scan over the (trial, part) counts in launch order, which is
@@ -457,6 +485,151 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
         hash_kernel<true><<<(unsigned)n_units, kThreads, S2.total, st>>>(P);
     }
     PROJ_LAUNCH_CHECK("hash_kernel<fill>");
+    return PROJ_OK;
+}
+
+namespace {
+
+// per-instance candidate and member offsets: the scanned bases at each
+// instance's first unit, and the totals at the end
+__global__ void batch_begins_kernel(const int64_t *__restrict__ cbase,
+                                    const int64_t *__restrict__ mbase,
+                                    const int64_t *__restrict__ unit_begin, int n_inst,
+                                    const int64_t *__restrict__ totals, int64_t *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_inst) {
+        out[2 * i] = cbase[unit_begin[i]];
+        out[2 * i + 1] = mbase[unit_begin[i]];
+    } else if (i == n_inst) {
+        out[2 * i] = totals[0];
+        out[2 * i + 1] = totals[1];
+    }
+}
+
+}  // namespace
+
+int run_hash_batch(const std::vector<HashInstSpec> &spec, HashBatchOut &out, cudaStream_t st) {
+    const int n = (int)spec.size();
+    PROJ_REQUIRE(n >= 1, "empty batch");
+    std::vector<HashParams> hp(n);
+    std::vector<int64_t> unit_begin(n + 1, 0);
+    int dyn1 = 0, dyn2 = 0;
+    for (int i = 0; i < n; ++i) {
+        const HashInstSpec &q = spec[i];
+        PROJ_REQUIRE(q.k >= 1 && q.k <= 10 && q.k <= q.l, "instance %d: need 1 <= k <= min(l, 10)", i);
+        PROJ_REQUIRE(q.s >= 1 && q.m >= 1, "instance %d: need s >= 1 and m >= 1", i);
+        HashParams &P = hp[i];
+        P = HashParams{};
+        P.packed = q.packed;
+        P.nwords = q.nwords;
+        P.seq_off = q.seq_off_rel;
+        P.lmer_off = q.lmer_off;
+        P.t = q.t; P.l = q.l; P.k = q.k; P.s = q.s; P.x = q.x;
+        P.seed = q.seed;
+        P.trial_begin = 0;
+        const int64_t nbuck = (int64_t)1 << (2 * q.k);
+        if (nbuck * 4 <= kHistBytes) {
+            P.hist16 = 0; P.hb = (int)nbuck; P.parts = 1;
+        } else if (q.x <= 65535) {
+            P.hist16 = 1; P.hb = (int)std::min<int64_t>(nbuck, kHistBytes / 2); P.parts = (int)(nbuck / P.hb);
+        } else {
+            P.hist16 = 0; P.hb = kHistBytes / 4; P.parts = (int)(nbuck / P.hb);
+        }
+        HashParams Q = P;
+        Q.stage_words = (int)q.nwords;
+        if (smem_layout(Q, true).total <= kSmemLimit) P.stage_words = (int)q.nwords;
+        PROJ_REQUIRE(smem_layout(P, true).total <= kSmemLimit, "instance %d: too many sequences", i);
+        dyn1 = std::max(dyn1, smem_layout(P, false).total);
+        dyn2 = std::max(dyn2, smem_layout(P, true).total);
+        unit_begin[i + 1] = unit_begin[i] + (int64_t)q.m * P.parts;
+    }
+    const int64_t U = unit_begin[n];
+    PROJ_REQUIRE(U < ((int64_t)1 << 31), "too many (trial, part) units in the batch");
+
+    DevBuf meta, ub, hpb, begins;
+    PROJ_TRY(meta.alloc((size_t)U * (4 + 4 + 8 + 8), st));
+    PROJ_TRY(ub.alloc((size_t)(n + 1) * sizeof(int64_t), st));
+    PROJ_TRY(hpb.alloc((size_t)n * sizeof(HashParams), st));
+    PROJ_TRY(begins.alloc((size_t)(n + 1) * 2 * sizeof(int64_t), st));
+    int32_t *part_nb = meta.as<int32_t>();
+    int32_t *part_nm = part_nb + U;
+    int64_t *cbase = reinterpret_cast<int64_t *>(part_nm + U);
+    int64_t *mbase = cbase + U;
+    for (int i = 0; i < n; ++i) {
+        HashParams &P = hp[i];
+        P.part_nb = part_nb + unit_begin[i];
+        P.part_nm = part_nm + unit_begin[i];
+        P.cand_base = cbase + unit_begin[i];
+        P.mem_base = mbase + unit_begin[i];
+    }
+    PROJ_CUDA_TRY(cudaMemcpyAsync(ub.as<int64_t>(), unit_begin.data(), (n + 1) * sizeof(int64_t),
+                                  cudaMemcpyHostToDevice, st));
+    PROJ_CUDA_TRY(cudaMemcpyAsync(hpb.as<HashParams>(), hp.data(), n * sizeof(HashParams),
+                                  cudaMemcpyHostToDevice, st));
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_batch_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_batch_kernel<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+    {
+        TraceSpan ts_("hash_count", st);
+        hash_batch_kernel<false><<<(unsigned)U, kThreads, dyn1, st>>>(hpb.as<HashParams>(),
+                                                                     ub.as<int64_t>(), n);
+    }
+    PROJ_LAUNCH_CHECK("hash_batch_kernel<count>");
+    DevBuf tot;
+    PROJ_TRY(tot.alloc(3 * sizeof(int64_t), st));
+    int64_t *totals = tot.as<int64_t>();
+    int64_t *off0 = totals + 2;  // sentinel slot (capacity 0 here)
+    {
+        TraceSpan ts_("hash_scan", st);
+        hash_scan_kernel<<<1, 1024, 0, st>>>(part_nb, part_nm, (int)U, cbase, mbase, totals, 0, off0);
+    }
+    PROJ_LAUNCH_CHECK("hash_scan_kernel");
+    batch_begins_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(cbase, mbase, ub.as<int64_t>(), n,
+                                                              totals, begins.as<int64_t>());
+    PROJ_LAUNCH_CHECK("batch_begins_kernel");
+    std::vector<int64_t> bh(2 * (n + 1));
+    PROJ_CUDA_TRY(cudaMemcpyAsync(bh.data(), begins.as<int64_t>(), bh.size() * sizeof(int64_t),
+                                  cudaMemcpyDeviceToHost, st));
+    PROJ_CUDA_TRY(cudaStreamSynchronize(st));
+    out.C = bh[2 * n];
+    out.M = bh[2 * n + 1];
+    out.cand_begin.resize(n);
+    out.n_cand.resize(n);
+    out.mem_begin.resize(n);
+    out.n_mem.resize(n);
+    for (int i = 0; i < n; ++i) {
+        out.cand_begin[i] = bh[2 * i];
+        out.mem_begin[i] = bh[2 * i + 1];
+        out.n_cand[i] = bh[2 * (i + 1)] - bh[2 * i];
+        out.n_mem[i] = bh[2 * (i + 1) + 1] - bh[2 * i + 1];
+    }
+    const int64_t C = out.C, M = out.M;
+    PROJ_TRY(out.cand.alloc((size_t)(C + 1) * 8 + (size_t)C * 12 + (size_t)M * 4 + 64, st));
+    PROJ_CUDA_TRY(cudaMemcpyAsync(out.cand_off() + C, totals + 1, sizeof(int64_t),
+                                  cudaMemcpyDeviceToDevice, st));
+    DevBuf scratch;
+    if (M > 0) PROJ_TRY(scratch.alloc((size_t)M * 8, st));
+    for (int i = 0; i < n; ++i) {
+        HashParams &P = hp[i];
+        P.cap_cand = C;
+        P.cap_members = M;
+        P.cand_trial = out.cand_trial();
+        P.cand_key = out.cand_key();
+        P.cand_cnt = out.cand_cnt();
+        P.cand_off = out.cand_off();
+        P.members = out.members();
+        P.scratch_key = scratch.as<uint32_t>();
+        P.scratch_gid = reinterpret_cast<int32_t *>(P.scratch_key + M);
+    }
+    PROJ_CUDA_TRY(cudaMemcpyAsync(hpb.as<HashParams>(), hp.data(), n * sizeof(HashParams),
+                                  cudaMemcpyHostToDevice, st));
+    {
+        TraceSpan ts_("hash_fill", st);
+        hash_batch_kernel<true><<<(unsigned)U, kThreads, dyn2, st>>>(hpb.as<HashParams>(),
+                                                                    ub.as<int64_t>(), n);
+    }
+    PROJ_LAUNCH_CHECK("hash_batch_kernel<fill>");
     return PROJ_OK;
 }
 

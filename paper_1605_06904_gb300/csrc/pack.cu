@@ -75,6 +75,42 @@ __global__ void background_kernel(const uint32_t *__restrict__ packed, int64_t t
     }
 }
 
+// Background of each instance of a batch: base counts over its base range
+// [base_range[2i], base_range[2i+1]) of the packed input (one CTA each).
+__global__ void background_batch_kernel(const uint32_t *__restrict__ packed,
+                                        const int64_t *__restrict__ base_range,
+                                        double *__restrict__ bg) {
+    __shared__ unsigned long long cnt[4];
+    if (threadIdx.x < 4) cnt[threadIdx.x] = 0ull;
+    __syncthreads();
+    const int64_t b0 = base_range[2 * blockIdx.x], b1 = base_range[2 * blockIdx.x + 1];
+    unsigned long long c1 = 0, c2 = 0, c3 = 0;
+    for (int64_t w = (b0 >> 4) + threadIdx.x; w <= ((b1 - 1) >> 4); w += blockDim.x) {
+        const int64_t lo = w << 4;
+        const int first = (int)(b0 > lo ? b0 - lo : 0);            // first valid base in the word
+        const int last = (int)(b1 - lo < 16 ? b1 - lo : 16);         // one past the last
+        uint32_t valid = 0u;
+        for (int q = first; q < last; ++q) valid |= 1u << (2 * q);
+        const uint32_t v = packed[w];
+        const uint32_t lo2 = v & valid, hi2 = (v >> 1) & valid;
+        c1 += __popc(lo2 & ~hi2);
+        c2 += __popc(hi2 & ~lo2);
+        c3 += __popc(lo2 & hi2);
+    }
+    atomicAdd(&cnt[1], c1);
+    atomicAdd(&cnt[2], c2);
+    atomicAdd(&cnt[3], c3);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long c[4];
+        c[1] = cnt[1]; c[2] = cnt[2]; c[3] = cnt[3];
+        c[0] = (unsigned long long)(b1 - b0) - c[1] - c[2] - c[3];
+        unsigned long long tot = 0;
+        for (int a = 0; a < 4; ++a) { if (c[a] == 0) c[a] = 1; tot += c[a]; }
+        for (int a = 0; a < 4; ++a) bg[4 * blockIdx.x + a] = (double)c[a] / (double)tot;
+    }
+}
+
 __global__ void positions_kernel(uint64_t seed, int64_t trial_begin, int64_t n_trials, int l,
                                  int k, uint8_t *__restrict__ pos) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -108,6 +144,16 @@ int launch_background(const uint32_t *packed, int64_t total, double *bg, cudaStr
         background_kernel<<<1, 1024, 0, st>>>(packed, total, bg);
     }
     PROJ_LAUNCH_CHECK("background_kernel");
+    return PROJ_OK;
+}
+
+int launch_background_batch(const uint32_t *packed, const int64_t *base_range, int n_inst,
+                            double *bg, cudaStream_t st) {
+    {
+        TraceSpan ts_("background", st);
+        background_batch_kernel<<<n_inst, 256, 0, st>>>(packed, base_range, bg);
+    }
+    PROJ_LAUNCH_CHECK("background_batch_kernel");
     return PROJ_OK;
 }
 

@@ -1,0 +1,97 @@
+"""Batched searches (projection_find_batch): every instance of a batch of
+uneven t, n and l must give what it gives alone (projection_find, same
+tensor-core EM): identical candidate lists (hashing is integer work), identical
+consensus and sites, and log-likelihoods equal to BF16-split tolerance; and it
+must agree with the FP64 oracle on a few instances."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from synth import mix_instances, planted_instance
+from tests.conftest import ll_tol
+
+pytestmark = pytest.mark.gpu
+
+LL_REL_BF16 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def P(native_lib):
+    import paper_1605_06904_gb300 as P
+    torch.cuda.set_device(0)
+    return P
+
+
+def _small_mix():
+    """Uneven instances with small trial counts (fast for the oracle)."""
+    out = []
+    specs = [(12, 330, 11, 2, 6, 4, 12), (25, 700, 13, 3, 7, 4, 20), (10, 1100, 15, 4, 7, 3, 15),
+             (31, 400, 17, 5, 7, 4, 9), (17, 950, 19, 6, 8, 3, 25), (8, 300, 9, 1, 5, 3, 7),
+             (40, 520, 12, 2, 7, 4, 11)]
+    for q, (t, n, l, d, k, s, m) in enumerate(specs):
+        inst = planted_instance(500 + q, 0, t, n, l, d)
+        inst.params = dict(k=k, s=s, m=m)
+        out.append(inst)
+    return out
+
+
+def test_batch_equals_single_searches(P):
+    insts = _small_mix()
+    seeds = [7 + 3 * q for q in range(len(insts))]
+    got = P.projection_find_batch([i.seqs for i in insts], [i.l for i in insts],
+                                  [i.d for i in insts], [i.params["k"] for i in insts],
+                                  [i.params["s"] for i in insts], [i.params["m"] for i in insts],
+                                  seeds, em_iters=5, pseudocount=0.25)
+    for inst, sd, g in zip(insts, seeds, got):
+        p = inst.params
+        one = P.projection_find(inst.ascii, inst.seq_off, inst.l, inst.d, p["k"], p["s"], p["m"],
+                                seed=sd, em_iters=5, pseudocount=0.25,
+                                precision=P.PROJ_EM_BF16_SPLIT)
+        assert g["n_candidates"] == one["n_candidates"] and g["n_members"] == one["n_members"]
+        assert (g["k"], g["s"], g["m"]) == (one["k"], one["s"], one["m"])
+        assert g["consensus"] == one["consensus"]
+        assert np.array_equal(g["sites"], one["sites"])
+        assert g["score"] == one["score"]
+        assert abs(g["loglik"] - one["loglik"]) <= ll_tol(one["loglik"], inst.t, 1e-5)
+        assert np.max(np.abs(g["pwm"] - one["pwm"])) <= 1e-5
+
+
+def test_batch_matches_oracle(P):
+    insts = _small_mix()[:4]
+    seeds = [11, 12, 13, 14]
+    got = P.projection_find_batch([i.seqs for i in insts], [i.l for i in insts],
+                                  [i.d for i in insts], [i.params["k"] for i in insts],
+                                  [i.params["s"] for i in insts], [i.params["m"] for i in insts],
+                                  seeds, em_iters=5, pseudocount=0.25)
+    for inst, sd, g in zip(insts, seeds, got):
+        p = inst.params
+        want = O.find([q.decode() for q in inst.seqs], inst.l, inst.d, p["k"], p["s"], p["m"],
+                      seed=sd, em_iters=5, beta=0.25, nthreads=16)
+        assert g["n_candidates"] == want["n_candidates"]
+        assert g["consensus"] == want["consensus"]
+        assert np.array_equal(g["sites"], want["sites"])
+        assert abs(g["loglik"] - want["loglik"]) <= ll_tol(want["loglik"], inst.t, LL_REL_BF16)
+
+
+def test_batch_of_config4_instances_runs(P):
+    insts = mix_instances(24)
+    for inst in insts:  # keep the trial counts small for a quick check
+        inst.params["m"] = 20
+    got = P.projection_find_batch([i.seqs for i in insts], [i.l for i in insts],
+                                  [i.d for i in insts], [i.params["k"] for i in insts],
+                                  [i.params["s"] for i in insts], [20] * len(insts),
+                                  list(range(len(insts))), em_iters=5, pseudocount=0.25)
+    assert len(got) == len(insts)
+    for inst, g in zip(insts, got):
+        assert g["status"] == 0 and g["t"] == inst.t and g["l"] == inst.l
+        if g["n_candidates"]:
+            assert len(g["consensus"]) == inst.l and g["sites"].shape == (inst.t,)
+
+
+def test_batch_rejects_fp32(P):
+    inst = _small_mix()[0]
+    with pytest.raises(P.ProjectionError) as e:
+        P.projection_find_batch([inst.seqs], [inst.l], [inst.d], [6], [4], [5], [1],
+                                precision=P.PROJ_EM_FP32)
+    assert e.value.status == -7
