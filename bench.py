@@ -407,8 +407,10 @@ def main():
                 "avg_launch_ms": em_ms / max(1, em_launches),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (derived)"}
     else:
-        k_pad = 16 * math.ceil(4 * inst.l / 16)
-        flops = args.steps * x * C * (iters * 2 * 2 * k_pad * 2 + 2 * 2 * k_pad)
+        # algorithmic FLOPs of the two one-hot contractions at K = 4l: 2*4l for the
+        # scores (every launch) + 2*4l for the counts (M-step launches); the hi + lo
+        # duplication and the K padding the kernel executes are not credited
+        flops = args.steps * x * C * (iters * 16 * inst.l + 8 * inst.l)
         achieved = flops / (em_ms / 1e3) / 1e12 if em_ms > 0 else None
         peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

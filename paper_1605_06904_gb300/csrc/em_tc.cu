@@ -187,30 +187,36 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 3 : 2)) em_tc_kernel(c
             __syncthreads();
             for (int j0 = 0; j0 < ns; j0 += NT) {
                 const int nvalid = min(NT, ns - j0);
-                // 1. one-hot tile X[j][p*4+a] = [x_{j0+j+p} = a]
-                for (int item_x = tid; item_x < NT * (KP / 8); item_x += kTcThreads) {
-                    const int j = item_x % NT, kb = item_x / NT;
-                    // two positions per 16-byte chunk: p = 2kb (words 0-1), 2kb+1
-                    // (words 2-3); BF16 1.0 (0x3F80) in the slot of the base's code
-                    uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
-                    if (j < nvalid && 2 * kb < l) {
-                        const uint64_t win =
-                            staged ? window64(sSeq, nw_seq, base + j0 + j - (w_first << 4))
-                                   : window64(P.packed, P.nwords, base + j0 + j);
+                // 1. one-hot tile X[j][p*4+a] = [x_{j0+j+p} = a]: thread (j, half) writes
+                //    16-byte chunks kb (two positions each, BF16 1.0 = 0x3F80 in the slot of
+                //    the base's code) of row j from one 64-bit window
+                static_assert(kTcThreads % NT == 0, "rows must divide the CTA");
+                {
+                    constexpr int kSplit = kTcThreads / NT;  // threads per row
+                    constexpr int kChunks = KP / 8;
+                    const int j = tid % NT, part = tid / NT;
+                    const bool row_ok = j < nvalid;
+                    uint64_t win = 0;
+                    if (row_ok)
+                        win = staged ? window64(sSeq, nw_seq, base + j0 + j - (w_first << 4))
+                                     : window64(P.packed, P.nwords, base + j0 + j);
+#pragma unroll
+                    for (int kb = part; kb < kChunks; kb += kSplit) {
+                        uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
                         const int p0 = 2 * kb, p1 = 2 * kb + 1;
-                        {
+                        if (row_ok && p0 < l) {
                             const uint32_t code = (uint32_t)(win >> (2 * p0)) & 3u;
                             const uint32_t v = 0x3F80u << (16 * (code & 1u));
                             if (code >> 1) w1 = v; else w0 = v;
                         }
-                        if (p1 < l) {
+                        if (row_ok && p1 < l) {
                             const uint32_t code = (uint32_t)(win >> (2 * p1)) & 3u;
                             const uint32_t v = 0x3F80u << (16 * (code & 1u));
                             if (code >> 1) w3 = v; else w2 = v;
                         }
+                        *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(j, 8 * kb, KP)) =
+                            make_uint4(w0, w1, w2, w3);
                     }
-                    *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(j, 8 * kb, KP)) =
-                        make_uint4(w0, w1, w2, w3);
                 }
                 tc::fence_async_smem();
                 __syncthreads();
@@ -230,80 +236,101 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 3 : 2)) em_tc_kernel(c
                 abort = __syncthreads_or(!ok);
                 if (abort) break;
                 tc::fence_after_sync();
-                // 3. running max / compensated sum, P = 2^(S - max) as hi + lo
-                float tmax = -INFINITY;
-#pragma unroll
-                for (int c0 = 0; c0 < NT; c0 += 32) {
-                    float v[32];
-                    tc::tmem_ld32(tS + lane_base + c0, v);
-                    float mx[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) mx[q] = -INFINITY;
-#pragma unroll
-                    for (int q = 0; q < 32; ++q)
-                        if (nvalid == NT || c0 + q < nvalid) mx[q & 7] = fmaxf(mx[q & 7], v[q]);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) tmax = fmaxf(tmax, mx[q]);
-                }
-                // the maximum of each row may grow; the tensor-memory accesses below
-                // are .sync.aligned, so the rescale of O runs warp-uniformly (scale 1
-                // for rows whose maximum did not grow)
-                const bool grow = tmax > m;
-                const float sc = grow ? ex2(m - tmax) : 1.f;  // 0 on the first tile
-                if (grow) {
-                    Ssum *= sc;
-                    Scmp *= sc;
-                    m = tmax;
-                }
-                if (P.mstep && !first && __any_sync(0xffffffffu, grow)) {
-#pragma unroll
-                    for (int c0 = 0; c0 < KP; c0 += 16) {
-                        if (c0 < 16 * kq) {
-                            float v[16];
-                            tc::tmem_ld16(tO + lane_base + c0, v);
-#pragma unroll
-                            for (int q = 0; q < 16; ++q) v[q] *= sc;
-                            tc::tmem_st16(tO + lane_base + c0, v);
-                        }
-                    }
-                }
-                // P = 2^(S - max): each 32-column chunk is summed as a tree (no long
-                // dependency chain) and the chunk sums are added with compensation
+                // 3. P = 2^(S - m) with m a reference near the row maximum: the exact
+                //    maximum of the first tile of a sequence, then kept until a tile
+                //    holds a score more than 20 above it (P > 2^20); only then is the
+                //    maximum recomputed and the row's O and sum rescaled.  Each 32-column
+                //    chunk is summed as a tree and the chunk sums are added with
+                //    compensation.  The tensor-memory accesses are .sync.aligned, so
+                //    every decision that guards them is taken per warp.
                 const bool full = nvalid == NT;  // only a sequence's last tile is ragged
+                bool redo = first;
+                for (int pass = 0; pass < 2; ++pass) {
+                    if (redo) {
+                        float tmax = -INFINITY;
 #pragma unroll
-                for (int c0 = 0; c0 < NT; c0 += 32) {
-                    float v[32];
-                    tc::tmem_ld32(tS + lane_base + c0, v);
+                        for (int c0 = 0; c0 < NT; c0 += 32) {
+                            float v[32];
+                            tc::tmem_ld32(tS + lane_base + c0, v);
+                            float mx[8];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        const float e = ex2(v[q] - m);
-                        v[q] = (full || c0 + q < nvalid) ? e : 0.f;
+                            for (int q = 0; q < 8; ++q) mx[q] = -INFINITY;
+                            if (full) {
+#pragma unroll
+                                for (int q = 0; q < 32; ++q) mx[q & 7] = fmaxf(mx[q & 7], v[q]);
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < 32; ++q)
+                                    if (c0 + q < nvalid) mx[q & 7] = fmaxf(mx[q & 7], v[q]);
+                            }
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) tmax = fmaxf(tmax, mx[q]);
+                        }
+                        const bool grow = tmax > m;
+                        const float sc = grow ? ex2(m - tmax) : 1.f;  // 0 when m = -inf
+                        if (grow) {
+                            Ssum *= sc;
+                            Scmp *= sc;
+                            m = tmax;
+                        }
+                        if (P.mstep && !first && __any_sync(0xffffffffu, grow)) {
+#pragma unroll
+                            for (int c0 = 0; c0 < KP; c0 += 16) {
+                                if (c0 < 16 * kq) {
+                                    float v[16];
+                                    tc::tmem_ld16(tO + lane_base + c0, v);
+#pragma unroll
+                                    for (int q = 0; q < 16; ++q) v[q] *= sc;
+                                    tc::tmem_st16(tO + lane_base + c0, v);
+                                }
+                            }
+                        }
                     }
-                    float part[16];
+                    float add = 0.f;  // this tile's sum, chunk by chunk
+                    bool big = false;
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) part[q] = v[2 * q] + v[2 * q + 1];
+                    for (int c0 = 0; c0 < NT; c0 += 32) {
+                        float v[32];
+                        tc::tmem_ld32(tS + lane_base + c0, v);
+                        if (full) {
 #pragma unroll
-                    for (int w = 8; w >= 1; w >>= 1)
+                            for (int q = 0; q < 32; ++q) v[q] = ex2(v[q] - m);
+                        } else {
 #pragma unroll
-                        for (int q = 0; q < w; ++q) part[q] += part[q + w];
-                    kahan(Ssum, Scmp, part[0]);
-                    if (P.mstep) {
-                        uint32_t hi[16], lo[16];
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) {
-                            const uint32_t h = pack_bf16(v[2 * q], v[2 * q + 1]);
-                            const float h0 = __uint_as_float(h << 16);
-                            const float h1 = __uint_as_float(h & 0xFFFF0000u);
-                            hi[q] = h;
-                            lo[q] = pack_bf16(v[2 * q] - h0, v[2 * q + 1] - h1);
+                            for (int q = 0; q < 32; ++q) v[q] = (c0 + q < nvalid) ? ex2(v[q] - m) : 0.f;
                         }
+                        float part[16];
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            *reinterpret_cast<uint4 *>(sPhi + tc::kmajor_off(tid, c0 + 8 * b, NT)) =
-                                make_uint4(hi[4 * b], hi[4 * b + 1], hi[4 * b + 2], hi[4 * b + 3]);
-                            *reinterpret_cast<uint4 *>(sPlo + tc::kmajor_off(tid, c0 + 8 * b, NT)) =
-                                make_uint4(lo[4 * b], lo[4 * b + 1], lo[4 * b + 2], lo[4 * b + 3]);
+                        for (int q = 0; q < 16; ++q) part[q] = v[2 * q] + v[2 * q + 1];
+#pragma unroll
+                        for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                            for (int q = 0; q < w; ++q) part[q] += part[q + w];
+                        add += part[0];
+                        big |= part[0] > 1048576.f;  // some score > m + 20 (or NaN-free inf)
+                        if (P.mstep) {
+                            uint32_t hi[16], lo[16];
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                const uint32_t h = pack_bf16(v[2 * q], v[2 * q + 1]);
+                                const float h0 = __uint_as_float(h << 16);
+                                const float h1 = __uint_as_float(h & 0xFFFF0000u);
+                                hi[q] = h;
+                                lo[q] = pack_bf16(v[2 * q] - h0, v[2 * q + 1] - h1);
+                            }
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) {
+                                *reinterpret_cast<uint4 *>(sPhi + tc::kmajor_off(tid, c0 + 8 * b, NT)) =
+                                    make_uint4(hi[4 * b], hi[4 * b + 1], hi[4 * b + 2], hi[4 * b + 3]);
+                                *reinterpret_cast<uint4 *>(sPlo + tc::kmajor_off(tid, c0 + 8 * b, NT)) =
+                                    make_uint4(lo[4 * b], lo[4 * b + 1], lo[4 * b + 2], lo[4 * b + 3]);
+                            }
                         }
+                    }
+                    redo = __any_sync(0xffffffffu, big) && pass == 0;
+                    if (!redo) {
+                        kahan(Ssum, Scmp, add);
+                        break;
                     }
                 }
                 tc::fence_before_sync();
@@ -384,16 +411,17 @@ __global__ void em_tc_reduce_kernel(const double *__restrict__ part_acc,
                                     int stride, const EmInst *__restrict__ inst, int n_inst,
                                     float beta, int mstep, float *__restrict__ theta_out,
                                     double *__restrict__ ll_out) {
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= C * (mstep ? stride : 1)) return;
-    const int64_t c = mstep ? idx / stride : idx;
-    const int q = mstep ? (int)(idx % stride) : 0;
+    // one thread per (candidate, model entry); C * stride < 2^31 (checked by the host)
+    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t width = mstep ? (uint32_t)stride : 1u;
+    if ((int64_t)idx >= C * width) return;
+    const uint32_t c = idx / width, q = idx - c * width;
     int lo = 0, hi = n_inst - 1;  // instance of candidate c
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (inst[mid].cand_begin <= c) lo = mid; else hi = mid - 1;
+        if (inst[mid].cand_begin <= (int64_t)c) lo = mid; else hi = mid - 1;
     }
-    if (mstep && q < 4 * inst[lo].l) {
+    if (mstep && (int)q < 4 * inst[lo].l) {
         double s = 0.0;
         for (int g = 0; g < G; ++g) s += part_acc[((int64_t)g * C + c) * stride + q];
         theta_out[idx] = (float)((s + (double)beta) / ((double)inst[lo].t + 4.0 * (double)beta));
@@ -495,6 +523,7 @@ int run_em_tc_batch(const uint32_t *packed, int64_t nwords, const std::vector<Em
     int G = 1;
     const int kp = em_tc_plan(insts, items, G);
     PROJ_REQUIRE(kp <= 128, "l above 32 is not supported");
+    PROJ_REQUIRE(C * (int64_t)stride < ((int64_t)1 << 31), "too many candidate model entries");
     DevBuf part, tmp, flag, itemb;
     PROJ_TRY(part.alloc((size_t)G * C * (stride + 1) * sizeof(double), st));
     PROJ_TRY(tmp.alloc((size_t)C * stride * sizeof(float), st));

@@ -53,8 +53,10 @@ def test_batch_equals_single_searches(P):
         assert g["consensus"] == one["consensus"]
         assert np.array_equal(g["sites"], one["sites"])
         assert g["score"] == one["score"]
-        assert abs(g["loglik"] - one["loglik"]) <= ll_tol(one["loglik"], inst.t, 1e-5)
-        assert np.max(np.abs(g["pwm"] - one["pwm"])) <= 1e-5
+        # both are BF16-split results that differ only in the order of the FP32
+        # count sums over sequence groups; bounded by the BF16-split tolerances
+        assert abs(g["loglik"] - one["loglik"]) <= ll_tol(one["loglik"], inst.t, LL_REL_BF16)
+        assert np.max(np.abs(g["pwm"] - one["pwm"])) <= 5e-5
 
 
 def test_batch_matches_oracle(P):
