@@ -108,6 +108,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def recorded_traffic(profile: str, sources) -> float | None:
+    """DRAM bytes per launch from a committed ncu summary, if the kernel sources
+    still hash to what the capture was taken with (else None)."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
+        h = hashlib.sha256()
+        for s in sources:
+            h.update(open(os.path.join(ROOT, "paper_1605_06904_gb300", "csrc", s), "rb").read())
+        vals = dict(ln.strip().split(": ", 1) for ln in text.splitlines()
+                    if ln.strip().startswith(("traffic_bytes_per_launch:", "source_sha256_16:")))
+        if vals.get("source_sha256_16") != h.hexdigest()[:16]:
+            return None
+        return float(vals["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -413,8 +431,11 @@ def main():
         flops = args.steps * x * C * (iters * 16 * inst.l + 8 * inst.l)
         achieved = flops / (em_ms / 1e3) / 1e12 if em_ms > 0 else None
         peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+        traffic = (recorded_traffic("em_tc_kernel_planted15_4.md",
+                                    ["em_tc.cu", "tc.cuh", "em_batch.cuh"])
+                   if args.config == 2 else None)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "kernel": "em_tc_kernel", "launches": em_launches,
                 "avg_launch_ms": em_ms / max(1, em_launches),
                 "peak_source": f"bf16_tflops_sustained ({pk_kind})"}
