@@ -211,6 +211,7 @@ typedef struct {
     float *pwm;            /* [l][4], allocated by the library */
     char *consensus;       /* l letters + NUL, allocated by the library */
     int32_t *sites;        /* [t] 0-based starts, allocated by the library */
+    int64_t n_refined;     /* candidates refined by EM (n_candidates, or `top`) */
 } projection_result;
 
 /* The paper's problem statement (Algorithm 2: INPUT t sequences, l, n, d;
@@ -229,6 +230,20 @@ int projection_find_packed(const uint32_t *packed_dev, const int64_t *seq_off, i
                            int d, int k, int s, int m, uint64_t seed, int em_iters,
                            float pseudocount, int precision, projection_result *out,
                            void *stream);
+
+/* As projection_find / projection_find_packed, refining only the `top`
+ * enriched buckets with the most member l-mers (ties keep (trial, key) order;
+ * top = 0 refines all).  The paper ranks buckets only by the threshold s; the
+ * cap bounds EM work on serving-scale inputs with 10^6..10^7 enriched buckets.
+ * out->n_candidates counts all enriched buckets, out->n_refined the refined
+ * ones, out->win_index indexes the full (trial, key)-ordered list. */
+int projection_find_top(const uint8_t *ascii, const int64_t *seq_off, int t, int l, int d, int k,
+                        int s, int m, uint64_t seed, int em_iters, float pseudocount,
+                        int precision, int64_t top, projection_result *out, void *stream);
+int projection_find_packed_top(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
+                               int d, int k, int s, int m, uint64_t seed, int em_iters,
+                               float pseudocount, int precision, int64_t top,
+                               projection_result *out, void *stream);
 
 /* Batched serving: n_inst independent searches in one call.  Instance i owns
  * sequences inst_seq[i] .. inst_seq[i+1]-1 of the linear input (ascii,

@@ -289,6 +289,17 @@ def score(codes, seq_off, l, sites_) -> int:
     return int(_L().orc_score(_p(codes), _p(seq_off), seq_off.size - 1, l, _p(sites_)))
 
 
+def top_candidates(cand_cnt, top: int) -> np.ndarray:
+    """The `top` candidates with the most member l-mers, in that order; equal
+    counts keep the (trial, key) order of the candidate list.  Reading of the
+    "top 1024 enriched buckets" of the serving-scale workload: the paper ranks
+    buckets only by the threshold s (Algorithm 2 step 3), so a cap on their
+    number keeps the largest buckets."""
+    cnt = np.asarray(cand_cnt, np.int64)
+    order = np.lexsort((np.arange(cnt.size), -cnt))
+    return order[:top].astype(np.int64)
+
+
 def rank(ll: np.ndarray) -> int:
     """Best candidate: the highest log-likelihood ratio; a tie goes to the
     candidate that comes first in (trial, key) order."""
@@ -297,7 +308,7 @@ def rank(ll: np.ndarray) -> int:
 
 
 def find(ascii_seqs, l, d, k=0, s=0, m=0, seed=0, em_iters=5, beta=0.25, nthreads=1,
-         subset=None, with_hash=False):
+         subset=None, with_hash=False, top=0):
     """Whole pipeline (Algorithm 2 + Section 5.1) on a list of ASCII sequences.
 
     ``subset``: optional candidate indices; EM then runs on those candidates
@@ -310,7 +321,10 @@ def find(ascii_seqs, l, d, k=0, s=0, m=0, seed=0, em_iters=5, beta=0.25, nthread
     k, s, m = default_params(lens, l, d, k, s, m)
     h = hash_trials(codes, seq_off, l, k, s, seed, 0, m)
     C = h["cand_key"].size
-    idx = np.arange(C) if subset is None else np.asarray(subset, np.int64)
+    if top and C > top:
+        idx = top_candidates(h["cand_cnt"], top)
+    else:
+        idx = np.arange(C) if subset is None else np.asarray(subset, np.int64)
     bg = background(codes)
     th0 = np.empty((idx.size, l, 4))
     for n, c in enumerate(idx):

@@ -19,7 +19,7 @@ __all__ = ["projection_packed_words", "projection_default_params", "projection_p
            "projection_background", "projection_positions", "trial_hash",
            "trial_hash_noalloc", "theta0_build",
            "em_refine", "projection_finalize", "projection_find", "projection_find_packed",
-           "projection_find_batch",
+           "projection_find_batch", "projection_find_top", "projection_find_packed_top",
            "projection_trace_enable", "projection_trace_read", "ProjectionError",
            "PROJ_EM_FP32", "PROJ_EM_BF16_SPLIT", "seq_offsets"]
 
@@ -216,7 +216,7 @@ def _result_dict(r: ProjectionResult) -> dict:
     out = {"status": r.status, "t": t, "l": l, "k": r.k, "s": r.s, "m": r.m,
            "n_candidates": r.n_candidates, "n_members": r.n_members, "win_index": r.win_index,
            "win_trial": r.win_trial, "win_key": r.win_key, "loglik": r.loglik,
-           "score": r.score}
+           "score": r.score, "n_refined": r.n_refined}
     if r.pwm:
         out["pwm"] = np.ctypeslib.as_array(r.pwm, shape=(l * 4,)).reshape(l, 4).copy()
         out["sites"] = np.ctypeslib.as_array(r.sites, shape=(t,)).copy()
@@ -239,6 +239,37 @@ def projection_find(ascii, seq_off, l, d, k=0, s=0, m=0, seed=0, em_iters=5, pse
     rc = lib().projection_find(aptr, _ptr(off), off.size - 1, l, d, k, s, m, seed & (2**64 - 1),
                                em_iters, float(pseudocount), precision, ctypes.byref(r),
                                _stream(stream))
+    try:
+        check(rc)
+        return _result_dict(r)
+    finally:
+        lib().projection_result_free(ctypes.byref(r))
+
+
+def projection_find_top(ascii, seq_off, l, d, k=0, s=0, m=0, seed=0, em_iters=5,
+                        pseudocount=0.25, precision=PROJ_EM_FP32, top=0, stream=None) -> dict:
+    """projection_find refining only the `top` largest enriched buckets."""
+    off = _off(seq_off)
+    ascii = np.ascontiguousarray(np.asarray(ascii, np.uint8))
+    r = ProjectionResult()
+    rc = lib().projection_find_top(_ptr(ascii), _ptr(off), off.size - 1, l, d, k, s, m,
+                                   seed & (2**64 - 1), em_iters, float(pseudocount), precision,
+                                   int(top), ctypes.byref(r), _stream(stream))
+    try:
+        check(rc)
+        return _result_dict(r)
+    finally:
+        lib().projection_result_free(ctypes.byref(r))
+
+
+def projection_find_packed_top(packed, seq_off, l, d, k=0, s=0, m=0, seed=0, em_iters=5,
+                               pseudocount=0.25, precision=PROJ_EM_FP32, top=0,
+                               stream=None) -> dict:
+    off = _off(seq_off)
+    r = ProjectionResult()
+    rc = lib().projection_find_packed_top(_ptr(packed), _ptr(off), off.size - 1, l, d, k, s, m,
+                                          seed & (2**64 - 1), em_iters, float(pseudocount),
+                                          precision, int(top), ctypes.byref(r), _stream(stream))
     try:
         check(rc)
         return _result_dict(r)

@@ -32,7 +32,8 @@ class ProjectionResult(ctypes.Structure):
                 ("n_candidates", i64), ("n_members", i64), ("win_index", i64),
                 ("win_trial", i32), ("win_key", ctypes.c_uint32), ("loglik", ctypes.c_double),
                 ("score", i32), ("pwm", ctypes.POINTER(ctypes.c_float)),
-                ("consensus", ctypes.c_char_p), ("sites", ctypes.POINTER(ctypes.c_int32))]
+                ("consensus", ctypes.c_char_p), ("sites", ctypes.POINTER(ctypes.c_int32)),
+                ("n_refined", i64)]
 
 
 SIGNATURES = {
@@ -53,6 +54,10 @@ SIGNATURES = {
                          ctypes.POINTER(ProjectionResult), P], i32),
     "projection_find_packed": ([P, P, i32, i32, i32, i32, i32, i32, u64, i32, f32, i32,
                                 ctypes.POINTER(ProjectionResult), P], i32),
+    "projection_find_top": ([P, P, i32, i32, i32, i32, i32, i32, u64, i32, f32, i32, i64,
+                             ctypes.POINTER(ProjectionResult), P], i32),
+    "projection_find_packed_top": ([P, P, i32, i32, i32, i32, i32, i32, u64, i32, f32, i32, i64,
+                                    ctypes.POINTER(ProjectionResult), P], i32),
     "projection_find_batch": ([P, P, P, i32, P, P, P, P, P, P, i32, f32, i32,
                                ctypes.POINTER(ProjectionResult), P], i32),
     "projection_result_free": ([ctypes.POINTER(ProjectionResult)], None),

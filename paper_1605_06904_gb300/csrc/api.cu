@@ -265,7 +265,7 @@ int projection_finalize(const uint32_t *packed_dev, const int64_t *seq_off, int 
 
 static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int l, int d, int k,
                      int s, int m, uint64_t seed, int em_iters, float pseudocount, int precision,
-                     projection_result *out, cudaStream_t st) {
+                     int64_t top, projection_result *out, cudaStream_t st) {
     PROJ_REQUIRE(packed != nullptr, "packed input must not be NULL");
     PROJ_REQUIRE(d >= 0 && d < l, "need 0 <= d < l");
     Layout L;
@@ -319,18 +319,37 @@ static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int 
     ho.totals = totals;
     PROJ_TRY(run_trial_hash(packed, L, k, s, seed, 0, m, nullptr, ho, st));
 
+    // keep only the `top` largest buckets when asked (serving-scale inputs)
+    std::vector<int64_t> sel;
+    std::vector<int32_t> sel_cnt;
+    const int64_t *r_off = ho.cand_off;
+    const int32_t *r_members = ho.members;
+    int64_t R = C;
+    DevBuf compact;
+    if (top > 0 && C > top) {
+        PROJ_TRY(select_top(ho.cand_cnt, C, top, sel, sel_cnt, st));
+        int64_t *no = nullptr;
+        int32_t *nm = nullptr;
+        PROJ_TRY(gather_selected(sel, sel_cnt, ho.cand_off, ho.members, compact, &no, &nm, st));
+        r_off = no;
+        r_members = nm;
+        R = (int64_t)sel.size();
+    }
+    out->n_refined = R;
+
     DevBuf model;
-    PROJ_TRY(model.alloc((size_t)C * 4 * l * sizeof(float) + (size_t)C * sizeof(double) + 16, st));
+    PROJ_TRY(model.alloc((size_t)R * 4 * l * sizeof(float) + (size_t)R * sizeof(double) + 16, st));
     double *ll = model.as<double>();
-    float *theta = reinterpret_cast<float *>(ll + C);
-    PROJ_TRY(launch_theta0(packed, L, ho.cand_off, ho.members, C, pseudocount, theta, st));
-    PROJ_TRY(run_em(packed, L, bg, theta, C, em_iters, pseudocount, precision, theta, ll, st));
-    PROJ_TRY(launch_finalize(packed, L, bg, theta, ll, C, best, sites, cons, score, st));
+    float *theta = reinterpret_cast<float *>(ll + R);
+    PROJ_TRY(launch_theta0(packed, L, r_off, r_members, R, pseudocount, theta, st));
+    PROJ_TRY(run_em(packed, L, bg, theta, R, em_iters, pseudocount, precision, theta, ll, st));
+    PROJ_TRY(launch_finalize(packed, L, bg, theta, ll, R, best, sites, cons, score, st));
 
     int64_t b = -1;
     PROJ_CUDA_TRY(cudaMemcpyAsync(&b, best, sizeof b, cudaMemcpyDeviceToHost, st));
     PROJ_CUDA_TRY(cudaStreamSynchronize(st));
-    out->win_index = b;
+    const int64_t b_orig = (b >= 0 && !sel.empty()) ? sel[b] : b;  // index in the full list
+    out->win_index = b_orig;
     out->pwm = (float *)calloc((size_t)4 * l, sizeof(float));
     out->consensus = (char *)calloc((size_t)l + 1, 1);
     out->sites = (int32_t *)calloc((size_t)t, sizeof(int32_t));
@@ -345,8 +364,8 @@ static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int 
         PROJ_CUDA_TRY(cudaMemcpyAsync(out->pwm, theta + b * 4 * l, (size_t)4 * l * sizeof(float),
                                       cudaMemcpyDeviceToHost, st));
         PROJ_CUDA_TRY(cudaMemcpyAsync(&out->loglik, ll + b, 8, cudaMemcpyDeviceToHost, st));
-        PROJ_CUDA_TRY(cudaMemcpyAsync(&out->win_trial, ho.cand_trial + b, 4, cudaMemcpyDeviceToHost, st));
-        PROJ_CUDA_TRY(cudaMemcpyAsync(&out->win_key, ho.cand_key + b, 4, cudaMemcpyDeviceToHost, st));
+        PROJ_CUDA_TRY(cudaMemcpyAsync(&out->win_trial, ho.cand_trial + b_orig, 4, cudaMemcpyDeviceToHost, st));
+        PROJ_CUDA_TRY(cudaMemcpyAsync(&out->win_key, ho.cand_key + b_orig, 4, cudaMemcpyDeviceToHost, st));
     }
     PROJ_CUDA_TRY(cudaStreamSynchronize(st));
     out->consensus[l] = 0;
@@ -357,6 +376,7 @@ static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int 
     }
     return PROJ_OK;
 }
+
 
 static void result_init(projection_result *out) {
     memset(out, 0, sizeof *out);
@@ -372,14 +392,29 @@ int projection_find_packed(const uint32_t *packed_dev, const int64_t *seq_off, i
     if (!out) { set_error("out must not be NULL"); return PROJ_EINVAL; }
     result_init(out);
     const int rc = find_impl(packed_dev, seq_off, t, l, d, k, s, m, seed, em_iters, pseudocount,
-                             precision, out, (cudaStream_t)stream);
+                             precision, 0, out, (cudaStream_t)stream);
     out->status = rc;
     return rc;
 }
 
-int projection_find(const uint8_t *ascii, const int64_t *seq_off, int t, int l, int d, int k,
-                    int s, int m, uint64_t seed, int em_iters, float pseudocount, int precision,
-                    projection_result *out, void *stream) {
+int projection_find_packed_top(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
+                               int d, int k, int s, int m, uint64_t seed, int em_iters,
+                               float pseudocount, int precision, int64_t top,
+                               projection_result *out, void *stream) {
+    clear_error();
+    if (!out) { set_error("out must not be NULL"); return PROJ_EINVAL; }
+    result_init(out);
+    if (top < 0) { set_error("top must be >= 0"); out->status = PROJ_EINVAL; return PROJ_EINVAL; }
+    const int rc = find_impl(packed_dev, seq_off, t, l, d, k, s, m, seed, em_iters, pseudocount,
+                             precision, top, out, (cudaStream_t)stream);
+    out->status = rc;
+    return rc;
+}
+
+
+static int find_host(const uint8_t *ascii, const int64_t *seq_off, int t, int l, int d, int k,
+                     int s, int m, uint64_t seed, int em_iters, float pseudocount, int precision,
+                     int64_t top, projection_result *out, void *stream) {
     clear_error();
     if (!out) { set_error("out must not be NULL"); return PROJ_EINVAL; }
     result_init(out);
@@ -406,9 +441,29 @@ int projection_find(const uint8_t *ascii, const int64_t *seq_off, int t, int l, 
         set_error("character %d at index %lld is not A/C/G/T", (int)ascii[bad_h], (long long)bad_h);
         return fail(PROJ_EBADCHAR);
     }
-    rc = find_impl(packed, seq_off, t, l, d, k, s, m, seed, em_iters, pseudocount, precision, out, st);
+    rc = find_impl(packed, seq_off, t, l, d, k, s, m, seed, em_iters, pseudocount, precision, top,
+                   out, st);
     out->status = rc;
     return rc;
+}
+
+int projection_find(const uint8_t *ascii, const int64_t *seq_off, int t, int l, int d, int k,
+                    int s, int m, uint64_t seed, int em_iters, float pseudocount, int precision,
+                    projection_result *out, void *stream) {
+    return find_host(ascii, seq_off, t, l, d, k, s, m, seed, em_iters, pseudocount, precision, 0,
+                     out, stream);
+}
+
+int projection_find_top(const uint8_t *ascii, const int64_t *seq_off, int t, int l, int d, int k,
+                        int s, int m, uint64_t seed, int em_iters, float pseudocount,
+                        int precision, int64_t top, projection_result *out, void *stream) {
+    if (top < 0) {
+        set_error("top must be >= 0");
+        if (out) { result_init(out); out->status = PROJ_EINVAL; }
+        return PROJ_EINVAL;
+    }
+    return find_host(ascii, seq_off, t, l, d, k, s, m, seed, em_iters, pseudocount, precision, top,
+                     out, stream);
 }
 
 int projection_find_batch(const uint8_t *ascii, const int64_t *seq_off, const int *inst_seq,

@@ -175,6 +175,15 @@ int launch_finalize(const uint32_t *packed, const Layout &L, const double *bg,
 
 int sm_count();
 
+// The `top` largest candidates (size desc, index asc) and their sizes; empty
+// when top <= 0.  Synchronises `st`.
+int select_top(const int32_t *cnt_dev, int64_t C, int64_t top, std::vector<int64_t> &sel,
+               std::vector<int32_t> &sel_cnt, cudaStream_t st);
+// Compact CSR list (offsets, members) of the selected candidates in out_buf.
+int gather_selected(const std::vector<int64_t> &sel, const std::vector<int32_t> &sel_cnt,
+                    const int64_t *cand_off, const int32_t *members, DevBuf &out_buf,
+                    int64_t **new_off, int32_t **new_members, cudaStream_t st);
+
 // Event pair around one kernel launch while tracing is enabled
 // (projection_trace_enable); a no-op otherwise.
 class TraceSpan {

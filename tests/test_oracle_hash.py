@@ -131,3 +131,20 @@ def test_planted_bucket_appears_in_some_trial():
     # every trial: counts sum to x, cand list sorted by (trial, key)
     order = list(zip(h["cand_trial"].tolist(), h["cand_key"].tolist()))
     assert order == sorted(order) and len(set(order)) == len(order)
+
+
+def test_top_candidates_order_and_ties():
+    cnt = np.array([5, 9, 5, 12, 9, 4, 12, 5])
+    assert O.top_candidates(cnt, 5).tolist() == [3, 6, 1, 4, 0]
+    assert O.top_candidates(cnt, 100).tolist() == [3, 6, 1, 4, 0, 2, 7, 5]
+    # brute force over random lists: same multiset of counts as a full sort,
+    # non-increasing counts, ties in index order
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        c = rng.integers(3, 9, rng.integers(1, 300))
+        k = int(rng.integers(1, 320))
+        sel = O.top_candidates(c, k)
+        assert sel.size == min(k, c.size) and len(set(sel.tolist())) == sel.size
+        assert sorted(c[sel].tolist(), reverse=True) == sorted(c.tolist(), reverse=True)[:sel.size]
+        for a, b in zip(sel[:-1], sel[1:]):
+            assert c[a] > c[b] or (c[a] == c[b] and a < b)
