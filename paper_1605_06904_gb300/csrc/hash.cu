@@ -62,6 +62,13 @@ struct HashParams {
     int32_t *members;
     uint32_t *scratch_key;    // [cap_members]
     int32_t *scratch_gid;     // [cap_members]
+    // partitioned mode (large inputs split into many key-range parts): the
+    // (key - part * hb, l-mer id) pairs of (trial, part) are
+    // pairs[seg_off[(trial*parts + part)*n_chunks] .. seg_off[(trial*parts + part + 1)*n_chunks]),
+    // in l-mer id order
+    const uint2 *pairs;
+    const int64_t *seg_off;
+    int n_chunks;
 };
 
 struct SmemLayout {
@@ -183,7 +190,16 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     for (int q = 0; q < 16; ++q) pos[q] = q < P.k ? s_pos[q] : 0;
 
     // Algorithm 2 steps 2b-2c: project every l-mer and count its bucket.
-    {
+    int64_t seg_b = 0, seg_e = 0;
+    if (P.pairs) {
+        seg_b = P.seg_off[((int64_t)trial_local * P.parts + part) * P.n_chunks];
+        seg_e = P.seg_off[((int64_t)trial_local * P.parts + part + 1) * P.n_chunks];
+        for (int64_t e = seg_b + tid; e < seg_e; e += kThreads) {
+            const uint32_t rel = P.pairs[e].x;
+            if (P.hist16) atomicAdd(&hist32[rel >> 1], 1u << (16 * (rel & 1u)));
+            else atomicAdd(&hist32[rel], 1u);
+        }
+    } else {
         int i = 0;
         for (int gid = tid; gid < P.x; gid += kThreads) {
             while (s_lmer[i + 1] <= gid) ++i;
@@ -246,14 +262,23 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     // enriched l-mers in id order -> scratch[mbase .. mbase+NM)
     {
         int i = 0, running = 0;
-        for (int base = 0; base < P.x; base += kThreads) {
-            const int gid = base + tid;
+        const int64_t n_iter = P.pairs ? seg_e - seg_b : (int64_t)P.x;
+        for (int64_t base = 0; base < n_iter; base += kThreads) {
+            const int64_t it = base + tid;
             bool e = false;
             uint32_t rel = 0u;
-            if (gid < P.x) {
-                while (s_lmer[i + 1] <= gid) ++i;
-                const int64_t b0 = (int64_t)s_seq[i] + (gid - s_lmer[i]);
-                rel = lmer_key(window64(words, nwords, b0), pos, P.k) - lo_key;
+            int gid = 0;
+            if (it < n_iter) {
+                if (P.pairs) {
+                    const uint2 pr = P.pairs[seg_b + it];
+                    rel = pr.x;
+                    gid = (int)pr.y;
+                } else {
+                    gid = (int)it;
+                    while (s_lmer[i + 1] <= gid) ++i;
+                    const int64_t b0 = (int64_t)s_seq[i] + (gid - s_lmer[i]);
+                    rel = lmer_key(window64(words, nwords, b0), pos, P.k) - lo_key;
+                }
                 e = rel < hb && ((bitmap[rel >> 5] >> (rel & 31u)) & 1u);
             }
             const uint32_t bal = __ballot_sync(0xffffffffu, e);
@@ -341,6 +366,141 @@ __global__ void __launch_bounds__(kThreads, 1) hash_batch_kernel(const HashParam
     hash_unit<FILL>(insts[lo], (int)(u - unit_begin[lo]), smem, s_pos, s_warp, s_round);
 }
 
+// ---------------------------------------------------------------------------
+// Partitioned mode for large inputs: when 4^k counters need several key-range
+// parts and x is large, every part's CTA would otherwise rebuild all x keys.
+// Instead the keys are built twice per trial in total: (1) each (trial, chunk)
+// counts its l-mers per part, (2) a scan lays the parts out contiguously
+// (chunks in order inside each part), (3) a stable scatter writes
+// (key - part * hb, l-mer id) pairs, so each part's segment is in l-mer id
+// order and the bucket kernels read only their own segment.
+// ---------------------------------------------------------------------------
+constexpr int kPartThreads = 256;
+constexpr int kPartWarps = kPartThreads / 32;
+constexpr int kChunk = 8192;  // l-mers per (trial, chunk)
+constexpr int kMaxParts = 32;
+
+__device__ __forceinline__ void part_setup(const HashParams &P, int trial_local, int *s_pos) {
+    if (threadIdx.x == 0) {
+        if (P.fixed_pos) {
+            for (int q = 0; q < P.k; ++q) s_pos[q] = P.pos_in[q];
+        } else {
+            draw_positions(P.seed, (uint64_t)(P.trial_begin + trial_local), P.l, P.k, s_pos);
+        }
+    }
+    __syncthreads();
+}
+
+// sequence holding global l-mer id g (last i with lmer_off[i] <= g)
+__device__ __forceinline__ int seq_of(const int32_t *lmer_off, int t, int g) {
+    int lo = 0, hi = t - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(lmer_off + mid) <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kPartThreads) part_count_kernel(const HashParams P,
+                                                                  int64_t *__restrict__ counts) {
+    __shared__ int s_pos[16];
+    __shared__ unsigned s_cnt[kMaxParts];
+    const int trial_local = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+    if (tid < kMaxParts) s_cnt[tid] = 0u;
+    part_setup(P, trial_local, s_pos);
+    int pos[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) pos[q] = q < P.k ? s_pos[q] : 0;
+    const int g0 = chunk * kChunk, g1 = min(P.x, g0 + kChunk);
+    int i = g0 + tid < g1 ? seq_of(P.lmer_off, P.t, g0 + tid) : 0;
+    for (int g = g0 + tid; g < g1; g += kPartThreads) {
+        while (__ldg(P.lmer_off + i + 1) <= g) ++i;
+        const int64_t b0 = (int64_t)__ldg(P.seq_off + i) + (g - __ldg(P.lmer_off + i));
+        const uint32_t key = lmer_key(window64(P.packed, P.nwords, b0), pos, P.k);
+        atomicAdd(&s_cnt[key / (uint32_t)P.hb], 1u);
+    }
+    __syncthreads();
+    if (tid < P.parts)
+        counts[((int64_t)trial_local * P.parts + tid) * P.n_chunks + chunk] = s_cnt[tid];
+}
+
+// exclusive scan of n int64 values in one CTA, out[n] = total
+__global__ void __launch_bounds__(1024) scan_i64_kernel(const int64_t *__restrict__ in, int64_t n,
+                                                        int64_t *__restrict__ out) {
+    __shared__ long long s[1024];
+    const int tid = threadIdx.x;
+    const int64_t chunk = (n + 1023) / 1024;
+    const int64_t lo = min((int64_t)tid * chunk, n), hi = min(lo + chunk, n);
+    long long a = 0;
+    for (int64_t e = lo; e < hi; ++e) a += in[e];
+    s[tid] = a;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const long long v = tid >= o ? s[tid - o] : 0;
+        __syncthreads();
+        s[tid] += v;
+        __syncthreads();
+    }
+    long long p = s[tid] - a;
+    for (int64_t e = lo; e < hi; ++e) {
+        out[e] = p;
+        p += in[e];
+    }
+    if (tid == 1023) out[n] = s[1023];
+}
+
+__global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const HashParams P,
+                                                                    const int64_t *__restrict__ offs,
+                                                                    uint2 *__restrict__ pairs) {
+    __shared__ int s_pos[16];
+    __shared__ long long s_base[kMaxParts];
+    __shared__ int s_w[kPartWarps][kMaxParts];
+    const int trial_local = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    if (tid < kMaxParts)
+        s_base[tid] = tid < P.parts ? offs[((int64_t)trial_local * P.parts + tid) * P.n_chunks + chunk] : 0;
+    part_setup(P, trial_local, s_pos);
+    int pos[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) pos[q] = q < P.k ? s_pos[q] : 0;
+    const int g0 = chunk * kChunk, g1 = min(P.x, g0 + kChunk);
+    for (int r0 = g0; r0 < g1; r0 += kPartThreads) {
+        for (int q = tid; q < kPartWarps * kMaxParts; q += kPartThreads) (&s_w[0][0])[q] = 0;
+        __syncthreads();
+        const int g = r0 + tid;
+        const bool ok = g < g1;
+        uint32_t key = 0u, part = 0u;
+        if (ok) {
+            const int i = seq_of(P.lmer_off, P.t, g);
+            const int64_t b0 = (int64_t)__ldg(P.seq_off + i) + (g - __ldg(P.lmer_off + i));
+            key = lmer_key(window64(P.packed, P.nwords, b0), pos, P.k);
+            part = key / (uint32_t)P.hb;
+        }
+        const unsigned act = __ballot_sync(0xffffffffu, ok);
+        unsigned grp = 0u;
+        int rank = 0;
+        if (ok) {
+            grp = __match_any_sync(act, part);
+            rank = __popc(grp & ((1u << lane) - 1u));
+            if (rank == 0) s_w[warp][part] = __popc(grp);
+        }
+        __syncthreads();
+        if (ok) {
+            int before = 0;
+            for (int w = 0; w < warp; ++w) before += s_w[w][part];
+            const long long at = s_base[part] + before + rank;
+            pairs[at] = make_uint2(key - part * (uint32_t)P.hb, (uint32_t)g);
+        }
+        __syncthreads();
+        if (tid < P.parts) {
+            int add = 0;
+            for (int w = 0; w < kPartWarps; ++w) add += s_w[w][tid];
+            s_base[tid] += add;
+        }
+        __syncthreads();
+    }
+}
+
 // Exclusive scan over the (trial, part) counts in launch order, which is
 // (trial, key) order: candidate and member offsets plus the totals.
 __global__ void __launch_bounds__(1024) hash_scan_kernel(const int32_t *__restrict__ nb,
@@ -424,8 +584,10 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
     }
     P.pos_out = out.positions;
     P.counts_out = out.counts;
-    // stage the packed input when it fits next to the histogram
-    {
+    // stage the packed input when it fits next to the histogram (the
+    // partitioned mode reads precomputed keys instead)
+    const bool partitioned = P.parts > 1 && L.x > 65535;
+    if (!partitioned) {
         HashParams Q = P;
         Q.stage_words = (int)L.nwords;
         if (smem_layout(Q, true).total <= kSmemLimit) P.stage_words = (int)L.nwords;
@@ -450,6 +612,36 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
     P.cand_base = cbase;
     P.mem_base = mbase;
 
+    // large inputs over several key-range parts: partition (key, id) pairs first
+    DevBuf part_buf;
+    if (partitioned) {
+        PROJ_REQUIRE(P.parts <= kMaxParts, "too many key-range parts");
+        P.n_chunks = (int)((L.x + kChunk - 1) / kChunk);
+        const int64_t n_cnt = n_trials * P.parts * P.n_chunks;
+        PROJ_REQUIRE(n_trials * L.x < ((int64_t)1 << 40), "partition too large");
+        PROJ_TRY(part_buf.alloc((size_t)(2 * n_cnt + 1) * 8 + (size_t)n_trials * L.x * 8, st));
+        int64_t *cnt = part_buf.as<int64_t>();
+        int64_t *seg = cnt + n_cnt;
+        uint2 *pairs = reinterpret_cast<uint2 *>(seg + n_cnt + 1);
+        const dim3 grid((unsigned)P.n_chunks, (unsigned)n_trials);
+        {
+            TraceSpan ts_("hash_partition", st);
+            part_count_kernel<<<grid, kPartThreads, 0, st>>>(P, cnt);
+        }
+        PROJ_LAUNCH_CHECK("part_count_kernel");
+        {
+            TraceSpan ts_("hash_partition", st);
+            scan_i64_kernel<<<1, 1024, 0, st>>>(cnt, n_cnt, seg);
+        }
+        PROJ_LAUNCH_CHECK("scan_i64_kernel");
+        {
+            TraceSpan ts_("hash_partition", st);
+            part_scatter_kernel<<<grid, kPartThreads, 0, st>>>(P, seg, pairs);
+        }
+        PROJ_LAUNCH_CHECK("part_scatter_kernel");
+        P.pairs = pairs;
+        P.seg_off = seg;
+    }
     PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
     PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<true>,
