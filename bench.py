@@ -108,6 +108,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_over_ranks(work, seconds, device, world):
+    """Whole-job totals of a weak-scaling run: per-rank work summed, wall time
+    the slowest rank's (one all-reduce each; no data-path collective)."""
+    import torch
+    import torch.distributed as dist
+    w = torch.tensor([float(v) for v in work], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in w.tolist()], float(t.item())
+
+
+def rank_instance(cfg: int, rank: int):
+    """Weak scaling: rank r searches instance r of the workload."""
+    return instance_for_config(cfg, rank)
+
+
 def recorded_traffic(profile: str, sources) -> float | None:
     """DRAM bytes per launch from a committed ncu summary, if the kernel sources
     still hash to what the capture was taken with (else None)."""
@@ -454,7 +472,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
 
-    inst = instance_for_config(args.config, rank)  # weak scaling: one instance per GPU
+    inst = rank_instance(args.config, rank)  # weak scaling: one instance per GPU
     p = dict(inst.params)
     k, s, m = resolve(inst, p)
     iters, beta, seed = p["em_iters"], p["beta"], 1000 + args.config
@@ -511,16 +529,11 @@ def main():
     em_ms, em_launches = P.projection_trace_read(em_name)
     _, all_launches = P.projection_trace_read("")
 
-    tot = torch.tensor([scores_step * args.steps, m * x * args.steps, args.steps, 0.0],
-                       dtype=torch.float64, device=dev)
-    tmax = torch.tensor([T], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    T_job = float(tmax.item())
-    value = float(tot[0].item()) / T_job
-    hashes = float(tot[1].item()) / T_job
-    inst_rate = float(tot[2].item()) / T_job
+    (job_scores, job_hashes, job_steps), T_job = reduce_over_ranks(
+        [scores_step * args.steps, m * x * args.steps, args.steps], T, dev, world)
+    value = job_scores / T_job
+    hashes = job_hashes / T_job
+    inst_rate = job_steps / T_job
 
     # ---- roofline of the dominant kernel (EM)
     pk, pk_kind = peaks()

@@ -262,6 +262,16 @@ int projection_find_batch(const uint8_t *ascii, const int64_t *seq_off, const in
 
 void projection_result_free(projection_result *r);
 
+/* ---- failure detection --------------------------------------------------- */
+
+/* Self-test of the bounded waits used by the tensor-core kernels: launches a
+ * kernel that waits on an mbarrier nothing arrives on, with a limit of
+ * timeout_ns (<= 2 s) measured on the GPU's global timer.  Returns
+ * PROJ_ETIMEOUT when the wait expired and the kernel returned (the expected
+ * outcome; the CUDA context stays usable), PROJ_ECUDA otherwise.
+ * Synchronises `stream`. */
+int projection_selftest_wait(int64_t timeout_ns, void *stream);
+
 /* ---- tracing (CUDA-event timers per kernel) ----------------------------- */
 
 /* on != 0: start recording a CUDA event pair around every kernel the library

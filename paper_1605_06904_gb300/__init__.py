@@ -20,7 +20,8 @@ __all__ = ["projection_packed_words", "projection_default_params", "projection_p
            "trial_hash_noalloc", "theta0_build",
            "em_refine", "projection_finalize", "projection_find", "projection_find_packed",
            "projection_find_batch", "projection_find_top", "projection_find_packed_top",
-           "projection_trace_enable", "projection_trace_read", "ProjectionError",
+           "projection_trace_enable", "projection_trace_read", "projection_selftest_wait",
+           "ProjectionError",
            "PROJ_EM_FP32", "PROJ_EM_BF16_SPLIT", "seq_offsets"]
 
 
@@ -317,6 +318,12 @@ def projection_find_batch(instances, l, d, k=None, s=None, m=None, seeds=None, e
     finally:
         for i in range(n):
             lib().projection_result_free(ctypes.byref(res[i]))
+
+
+def projection_selftest_wait(timeout_ns: int = 50_000_000, stream=None) -> int:
+    """Runs the bounded-wait self-test; returns the status (PROJ_ETIMEOUT = -5
+    is the expected one)."""
+    return int(lib().projection_selftest_wait(int(timeout_ns), _stream(stream)))
 
 
 # ---- tracing -----------------------------------------------------------------

@@ -61,6 +61,7 @@ SIGNATURES = {
     "projection_find_batch": ([P, P, P, i32, P, P, P, P, P, P, i32, f32, i32,
                                ctypes.POINTER(ProjectionResult), P], i32),
     "projection_result_free": ([ctypes.POINTER(ProjectionResult)], None),
+    "projection_selftest_wait": ([i64, P], i32),
     "projection_trace_enable": ([i32], i32),
     "projection_trace_read": ([ctypes.c_char_p, P, P], i32),
 }

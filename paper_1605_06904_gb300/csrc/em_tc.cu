@@ -593,3 +593,46 @@ int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const f
 }
 
 }  // namespace proj
+
+// ---------------------------------------------------------------------------
+// projection_selftest_wait: exercises the bounded wait of the tensor-core
+// kernels on an mbarrier that nothing arrives on.
+// ---------------------------------------------------------------------------
+namespace proj {
+namespace {
+
+__global__ void selftest_wait_kernel(uint64_t timeout_ns, int *flag) {
+    __shared__ __align__(8) uint64_t mbar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&mbar, 1);
+        tc::mbar_fence_init();
+    }
+    __syncthreads();
+    const bool ok = tc::mbar_wait(&mbar, 0u, timeout_ns);  // phase 0 never completes
+    if (!__syncthreads_or(!ok) && threadIdx.x == 0) *flag = 2;  // unexpected completion
+    if (!ok && threadIdx.x == 0) *flag = 1;
+}
+
+}  // namespace
+}  // namespace proj
+
+extern "C" int projection_selftest_wait(int64_t timeout_ns, void *stream) {
+    using namespace proj;
+    clear_error();
+    cudaStream_t st = (cudaStream_t)stream;
+    PROJ_REQUIRE(timeout_ns > 0 && timeout_ns <= 2000000000LL, "timeout must be in (0, 2 s]");
+    DevBuf flag;
+    PROJ_TRY(flag.alloc(sizeof(int), st));
+    PROJ_CUDA_TRY(cudaMemsetAsync(flag.as<int>(), 0, sizeof(int), st));
+    selftest_wait_kernel<<<1, 64, 0, st>>>((uint64_t)timeout_ns, flag.as<int>());
+    PROJ_LAUNCH_CHECK("selftest_wait_kernel");
+    int h = 0;
+    PROJ_CUDA_TRY(cudaMemcpyAsync(&h, flag.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    PROJ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h == 1) {
+        set_error("bounded wait expired after %lld ns, as requested", (long long)timeout_ns);
+        return PROJ_ETIMEOUT;
+    }
+    set_error("the wait did not expire (flag %d)", h);
+    return PROJ_ECUDA;
+}
