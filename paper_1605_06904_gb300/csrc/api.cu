@@ -608,6 +608,7 @@ int projection_find_batch(const uint8_t *ascii, const int64_t *seq_off, const in
         sites_off += t;
         cons_off += l[i];
         eh[i].t = t; eh[i].l = l[i]; eh[i].C = H.n_cand[i]; eh[i].cand_begin = H.cand_begin[i];
+        eh[i].lmers = xs[i];
         ei[i].seq_off = bi[i].seq_off; ei[i].bg = bi[i].bg; ei[i].t = t; ei[i].l = l[i];
         ei[i].cand_begin = H.cand_begin[i];
         out[i].n_candidates = H.n_cand[i];
@@ -625,16 +626,21 @@ int projection_find_batch(const uint8_t *ascii, const int64_t *seq_off, const in
     float *theta = reinterpret_cast<float *>(ll + C);
     BATCH_TRY(launch_theta0_batch(packed, nwords, bib.as<BatchInst>(), n_inst, H.cand_off(),
                                   H.members(), C, pseudocount, stride, theta, st));
-    BATCH_TRY(run_em_tc_batch(packed, nwords, eh, eib.as<EmInst>(), theta, C, stride, em_iters,
-                              pseudocount, theta, ll, st));
     const size_t res_bytes = (size_t)n_inst * (8 + 4) + (size_t)t_sum * 4 + (size_t)l_sum + 64;
     BATCH_TRY(res.alloc(res_bytes, st));
     int64_t *best = res.as<int64_t>();
     int32_t *score = reinterpret_cast<int32_t *>(best + n_inst);
     int32_t *sites = score + n_inst;
     uint8_t *cons = reinterpret_cast<uint8_t *>(sites + t_sum);
-    BATCH_TRY(launch_finalize_batch(packed, nwords, bib.as<BatchInst>(), n_inst, theta, stride, ll,
-                                    best, sites, cons, score, st));
+    // EM iterations and the per-instance finalisation replay as one graph
+    EmTcRun run;
+    BATCH_TRY(em_tc_prepare(packed, nwords, eh, eib.as<EmInst>(), theta, C, stride, run, st));
+    BATCH_TRY(run_as_graph(kGraphBatchTail, st, [&](cudaStream_t cs) {
+        PROJ_TRY(em_tc_enqueue(run, em_iters, pseudocount, theta, ll, cs));
+        return launch_finalize_batch(packed, nwords, bib.as<BatchInst>(), n_inst, theta, stride, ll,
+                                     best, sites, cons, score, cs);
+    }));
+    BATCH_TRY(em_tc_finish(run, st));
     std::vector<unsigned char> hres(res_bytes);
     BATCH_CUDA(cudaMemcpyAsync(hres.data(), res.as<unsigned char>(), res_bytes,
                                cudaMemcpyDeviceToHost, st));

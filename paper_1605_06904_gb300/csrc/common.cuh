@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <vector>
 
 #include "../../include/projection.h"
@@ -196,6 +197,14 @@ class TraceSpan {
     int slot_ = -1;
     cudaStream_t st_;
 };
+bool trace_active();
+
+// Runs `body` (launches only: no allocation, no synchronisation) as a CUDA
+// graph on `st`: captured on a private stream, its executable graph kept per
+// (host thread, device, slot) and updated in place on the next call.
+// PROJ_GRAPHS=0 in the environment runs `body` directly on `st` instead.
+int run_as_graph(int slot, cudaStream_t st, const std::function<int(cudaStream_t)> &body);
+enum GraphSlot { kGraphEm = 0, kGraphBatchTail = 1 };
 
 // ---------------------------------------------------------------------------
 // Device helpers

@@ -32,9 +32,30 @@ struct EmItem {
 struct EmInstHost {
     int t = 0, l = 0;
     int64_t C = 0, cand_begin = 0;
+    int64_t lmers = 0;
 };
 
-int em_tc_plan(const std::vector<EmInstHost> &insts, std::vector<EmItem> &items, int &G);
+int em_tc_plan(const std::vector<EmInstHost> &insts, std::vector<EmItem> &items, int &G,
+               int ctas, int g_target);
+
+// One tensor-core EM run split into allocation/planning (em_tc_prepare, may
+// synchronise to autotune), launches only (em_tc_enqueue, capturable in a
+// CUDA graph) and the error check (em_tc_finish, synchronises).
+struct EmTcRun {
+    const uint32_t *packed = nullptr;
+    int64_t nwords = 0;
+    const EmInst *inst_dev = nullptr;
+    const float *theta0 = nullptr;
+    int64_t C = 0;
+    int stride = 0, n_inst = 0, kp = 16, G = 1, ctas = 3, n_items = 0;
+    DevBuf part, tmp, flag, items;
+};
+int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmInstHost> &insts,
+                  const EmInst *inst_dev, const float *theta0, int64_t C, int stride,
+                  EmTcRun &run, cudaStream_t st);
+int em_tc_enqueue(EmTcRun &run, int iters, float beta, float *theta_out, double *ll,
+                  cudaStream_t st);
+int em_tc_finish(EmTcRun &run, cudaStream_t st);
 
 // Runs iters EM iterations + a final E-step for the candidates of all
 // instances (models theta0[C][stride], stride >= 4l of each instance).

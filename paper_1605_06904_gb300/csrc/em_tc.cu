@@ -32,7 +32,12 @@
 // frees its tensor memory.
 #include <math.h>
 
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -482,21 +487,49 @@ int dispatch(int kp, const EmTcParams &P, int grid, cudaStream_t st) {
 
 }  // namespace
 
-int em_tc_plan(const std::vector<EmInstHost> &insts, std::vector<EmItem> &items, int &G) {
+// ---------------------------------------------------------------------------
+// Work plan and autotuning.  A schedule is (ctas, g_target): CTAs per SM of
+// the persistent grid (<= what shared memory and registers allow) and how
+// many work items per CTA slot the sequence-group split aims for when there
+// are few candidate tiles.  The first search of each shape class times one
+// E-step launch of every candidate schedule on its own data and keeps the
+// fastest (per process); PROJ_AUTOTUNE=0 turns this off (default schedule).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Sched { int ctas, g_target; };
+const Sched kScheds[] = {{3, 2}, {3, 1}, {3, 4}, {2, 2}, {2, 4}, {1, 4}};
+constexpr Sched kDefaultSched = {3, 2};
+
+std::mutex g_tune_mu;
+std::map<uint64_t, Sched> g_tuned;
+
+uint64_t shape_key(int kp, int64_t C, int tmin, int64_t lmers) {
+    int cb = 0, xb = 0;
+    while (((int64_t)1 << cb) < C) ++cb;
+    while (((int64_t)1 << xb) < lmers) ++xb;
+    return ((uint64_t)kp << 48) | ((uint64_t)cb << 40) | ((uint64_t)std::min(tmin, 65535) << 16) |
+           (uint64_t)xb;
+}
+
+}  // namespace
+
+int em_tc_plan(const std::vector<EmInstHost> &insts, std::vector<EmItem> &items, int &G,
+               int ctas, int g_target) {
     // split each instance's candidates into tiles of 128; when there are too
-    // few tiles to fill every SM a few times, split the sequences into G groups
+    // few tiles for g_target items per CTA slot, split the sequences into G groups
     int kp = 16;
     int64_t tiles = 0;
     for (const EmInstHost &h : insts) {
         kp = std::max(kp, 16 * ((4 * h.l + 15) / 16));
         tiles += (h.C + kTcThreads - 1) / kTcThreads;
     }
-    const int64_t slots = (int64_t)sm_count() * ctas_per_sm(kp);
+    const int64_t slots = (int64_t)sm_count() * std::min(ctas, ctas_per_sm(kp));
     int tmin = 1 << 30;
     for (const EmInstHost &h : insts) tmin = std::min(tmin, h.t);
     G = 1;
-    if (tiles > 0 && tiles < 2 * slots)
-        G = (int)std::min<int64_t>(std::max(1, tmin), (2 * slots + tiles - 1) / tiles);
+    if (tiles > 0 && tiles < g_target * slots)
+        G = (int)std::min<int64_t>(std::max(1, tmin), (g_target * slots + tiles - 1) / tiles);
     items.clear();
     for (size_t ii = 0; ii < insts.size(); ++ii) {
         const EmInstHost &h = insts[ii];
@@ -515,61 +548,163 @@ int em_tc_plan(const std::vector<EmInstHost> &insts, std::vector<EmItem> &items,
     return kp;
 }
 
-int run_em_tc_batch(const uint32_t *packed, int64_t nwords, const std::vector<EmInstHost> &insts,
-                    const EmInst *inst_dev, const float *theta0, int64_t C, int stride, int iters,
-                    float beta, float *theta_out, double *ll, cudaStream_t st) {
+int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmInstHost> &insts,
+                  const EmInst *inst_dev, const float *theta0, int64_t C, int stride,
+                  EmTcRun &run, cudaStream_t st) {
+    run.C = C;
+    run.stride = stride;
+    run.n_inst = (int)insts.size();
+    run.inst_dev = inst_dev;
+    run.packed = packed;
+    run.nwords = nwords;
+    run.theta0 = theta0;
     if (C == 0) return PROJ_OK;
-    std::vector<EmItem> items;
-    int G = 1;
-    const int kp = em_tc_plan(insts, items, G);
-    PROJ_REQUIRE(kp <= 128, "l above 32 is not supported");
     PROJ_REQUIRE(C * (int64_t)stride < ((int64_t)1 << 31), "too many candidate model entries");
-    DevBuf part, tmp, flag, itemb;
-    PROJ_TRY(part.alloc((size_t)G * C * (stride + 1) * sizeof(double), st));
-    PROJ_TRY(tmp.alloc((size_t)C * stride * sizeof(float), st));
-    PROJ_TRY(flag.alloc(sizeof(int), st));
-    PROJ_TRY(itemb.alloc(items.size() * sizeof(EmItem), st));
-    PROJ_CUDA_TRY(cudaMemcpyAsync(itemb.as<EmItem>(), items.data(), items.size() * sizeof(EmItem),
+    int tmin = 1 << 30;
+    int64_t lmers = 0;
+    int kp = 16;
+    for (const EmInstHost &h : insts) {
+        tmin = std::min(tmin, h.t);
+        lmers += h.lmers;
+        kp = std::max(kp, 16 * ((4 * h.l + 15) / 16));
+    }
+    PROJ_REQUIRE(kp <= 128, "l above 32 is not supported");
+    const uint64_t key = shape_key(kp, C, tmin, lmers);
+    Sched sched = kDefaultSched;
+    bool known = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) { sched = it->second; known = true; }
+    }
+    const char *env = getenv("PROJ_AUTOTUNE");
+    bool tune = !known && !(env && env[0] == '0');
+    // PROJ_EM_SCHED="ctas,g_target" forces one schedule (no tuning, no cache)
+    if (const char *fs = getenv("PROJ_EM_SCHED")) {
+        int c = 0, g = 0;
+        if (sscanf(fs, "%d,%d", &c, &g) == 2 && c >= 1 && c <= 3 && g >= 1 && g <= 8) {
+            sched = {c, g};
+            tune = false;
+        }
+    }
+
+    // buffers sized for the largest G any candidate schedule may pick
+    int Gmax = 1;
+    std::vector<EmItem> items;
+    for (const Sched &sc : kScheds) {
+        int G = 1;
+        em_tc_plan(insts, items, G, sc.ctas, sc.g_target);
+        Gmax = std::max(Gmax, G);
+    }
+    PROJ_TRY(run.part.alloc((size_t)Gmax * C * (stride + 1) * sizeof(double), st));
+    PROJ_TRY(run.tmp.alloc((size_t)C * stride * sizeof(float), st));
+    PROJ_TRY(run.flag.alloc(sizeof(int), st));
+    PROJ_CUDA_TRY(cudaMemsetAsync(run.flag.as<int>(), 0, sizeof(int), st));
+
+    if (tune) {
+        // time one E-step launch per schedule on this data
+        PROJ_CUDA_TRY(cudaMemcpyAsync(run.tmp.as<float>(), theta0, (size_t)C * stride * sizeof(float),
+                                      cudaMemcpyDeviceToDevice, st));
+        cudaEvent_t e0, e1;
+        PROJ_CUDA_TRY(cudaEventCreate(&e0));
+        PROJ_CUDA_TRY(cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        for (const Sched &sc : kScheds) {
+            int G = 1;
+            const int kpp = em_tc_plan(insts, items, G, sc.ctas, sc.g_target);
+            DevBuf ib;
+            PROJ_TRY(ib.alloc(items.size() * sizeof(EmItem), st));
+            PROJ_CUDA_TRY(cudaMemcpyAsync(ib.as<EmItem>(), items.data(), items.size() * sizeof(EmItem),
+                                          cudaMemcpyHostToDevice, st));
+            EmTcParams P{};
+            P.packed = packed; P.nwords = nwords; P.inst = inst_dev; P.items = ib.as<EmItem>();
+            P.n_items = (int)items.size(); P.theta_in = run.tmp.as<float>(); P.stride = stride;
+            P.part_ll = run.part.as<double>(); P.part_acc = run.part.as<double>() + (size_t)G * C;
+            P.C = C; P.err = run.flag.as<int>(); P.mstep = 0;
+            const int grid = (int)std::min<int64_t>((int64_t)items.size(),
+                                                    (int64_t)sm_count() * std::min(sc.ctas, ctas_per_sm(kpp)));
+            PROJ_CUDA_TRY(cudaEventRecord(e0, st));
+            PROJ_TRY(dispatch(kpp, P, grid, st));
+            PROJ_CUDA_TRY(cudaEventRecord(e1, st));
+            PROJ_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            PROJ_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) { best_ms = ms; sched = sc; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = sched;
+    }
+    run.kp = em_tc_plan(insts, items, run.G, sched.ctas, sched.g_target);
+    run.ctas = sched.ctas;
+    PROJ_TRY(run.items.alloc(items.size() * sizeof(EmItem), st));
+    PROJ_CUDA_TRY(cudaMemcpyAsync(run.items.as<EmItem>(), items.data(), items.size() * sizeof(EmItem),
                                   cudaMemcpyHostToDevice, st));
-    PROJ_CUDA_TRY(cudaMemsetAsync(flag.as<int>(), 0, sizeof(int), st));
-    PROJ_CUDA_TRY(cudaMemcpyAsync(tmp.as<float>(), theta0, (size_t)C * stride * sizeof(float),
+    run.n_items = (int)items.size();
+    return PROJ_OK;
+}
+
+int em_tc_enqueue(EmTcRun &run, int iters, float beta, float *theta_out, double *ll,
+                  cudaStream_t st) {
+    const int64_t C = run.C;
+    if (C == 0) return PROJ_OK;
+    const int stride = run.stride, G = run.G;
+    PROJ_CUDA_TRY(cudaMemcpyAsync(run.tmp.as<float>(), run.theta0, (size_t)C * stride * sizeof(float),
                                   cudaMemcpyDeviceToDevice, st));
     EmTcParams P{};
-    P.packed = packed;
-    P.nwords = nwords;
-    P.inst = inst_dev;
-    P.items = itemb.as<EmItem>();
-    P.n_items = (int)items.size();
-    P.theta_in = tmp.as<float>();
+    P.packed = run.packed;
+    P.nwords = run.nwords;
+    P.inst = run.inst_dev;
+    P.items = run.items.as<EmItem>();
+    P.n_items = run.n_items;
+    P.theta_in = run.tmp.as<float>();
     P.stride = stride;
-    P.part_ll = part.as<double>();
-    P.part_acc = part.as<double>() + (size_t)G * C;
+    P.part_ll = run.part.as<double>();
+    P.part_acc = run.part.as<double>() + (size_t)G * C;
     P.C = C;
-    P.err = flag.as<int>();
-    const int grid = (int)std::min<int64_t>((int64_t)items.size(),
-                                            (int64_t)sm_count() * ctas_per_sm(kp));
+    P.err = run.flag.as<int>();
+    const int grid = (int)std::min<int64_t>((int64_t)run.n_items,
+                                            (int64_t)sm_count() * std::min(run.ctas, ctas_per_sm(run.kp)));
     for (int it = 0; it <= iters; ++it) {
         P.mstep = it < iters;
-        PROJ_TRY(dispatch(kp, P, grid, st));
+        PROJ_TRY(dispatch(run.kp, P, grid, st));
         const int64_t n = P.mstep ? C * stride : C;
         {
             TraceSpan ts_("em_reduce", st);
             em_tc_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-                P.part_acc, P.part_ll, G, C, stride, inst_dev, (int)insts.size(), beta, P.mstep,
-                tmp.as<float>(), ll);
+                P.part_acc, P.part_ll, G, C, stride, run.inst_dev, run.n_inst, beta, P.mstep,
+                run.tmp.as<float>(), ll);
         }
         PROJ_LAUNCH_CHECK("em_tc_reduce_kernel");
     }
-    PROJ_CUDA_TRY(cudaMemcpyAsync(theta_out, tmp.as<float>(), (size_t)C * stride * sizeof(float),
+    PROJ_CUDA_TRY(cudaMemcpyAsync(theta_out, run.tmp.as<float>(), (size_t)C * stride * sizeof(float),
                                   cudaMemcpyDeviceToDevice, st));
+    return PROJ_OK;
+}
+
+int em_tc_finish(EmTcRun &run, cudaStream_t st) {
+    if (run.C == 0) return PROJ_OK;
     int err = 0;
-    PROJ_CUDA_TRY(cudaMemcpyAsync(&err, flag.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    PROJ_CUDA_TRY(cudaMemcpyAsync(&err, run.flag.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
     PROJ_CUDA_TRY(cudaStreamSynchronize(st));
     if (err) {
         set_error("a bounded wait for tensor-core completion expired in em_tc_kernel");
         return PROJ_ETIMEOUT;
     }
     return PROJ_OK;
+}
+
+int run_em_tc_batch(const uint32_t *packed, int64_t nwords, const std::vector<EmInstHost> &insts,
+                    const EmInst *inst_dev, const float *theta0, int64_t C, int stride, int iters,
+                    float beta, float *theta_out, double *ll, cudaStream_t st) {
+    EmTcRun run;
+    if (C == 0) return PROJ_OK;
+    PROJ_TRY(em_tc_prepare(packed, nwords, insts, inst_dev, theta0, C, stride, run, st));
+    PROJ_TRY(run_as_graph(kGraphEm, st, [&](cudaStream_t cs) {
+        return em_tc_enqueue(run, iters, beta, theta_out, ll, cs);
+    }));
+    return em_tc_finish(run, st);
 }
 
 int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const float *theta0,
@@ -579,6 +714,7 @@ int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const f
     insts[0].l = L.l;
     insts[0].C = C;
     insts[0].cand_begin = 0;
+    insts[0].lmers = L.x;
     EmInst in{};
     in.seq_off = L.seq_off_dev();
     in.t = L.t;

@@ -19,6 +19,16 @@ bool g_on = false;
 std::vector<Record> g_rec;   // events are reused across enable() calls
 size_t g_used = 0;
 
+// inside a stream capture the record becomes an event-record node of the
+// graph, so the pair still times the kernel when the graph runs
+void record(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, st);
+}
+
 }  // namespace
 
 TraceSpan::TraceSpan(const char *name, cudaStream_t st) : st_(st) {
@@ -32,14 +42,19 @@ TraceSpan::TraceSpan(const char *name, cudaStream_t st) : st_(st) {
     }
     slot_ = (int)g_used++;
     g_rec[slot_].name = name;
-    cudaEventRecord(g_rec[slot_].ev[0], st_);
+    record(g_rec[slot_].ev[0], st_);
 }
 
 void TraceSpan::end() {
     if (slot_ < 0) return;
     std::lock_guard<std::mutex> lk(g_mu);
-    cudaEventRecord(g_rec[slot_].ev[1], st_);
+    record(g_rec[slot_].ev[1], st_);
     slot_ = -1;
+}
+
+bool trace_active() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_on;
 }
 
 }  // namespace proj

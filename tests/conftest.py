@@ -1,6 +1,7 @@
 import os
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -40,3 +41,17 @@ def ll_tol(want, t, rel=1e-6):
     each rounded at FP32 precision)."""
     import numpy as np
     return rel * np.maximum(np.abs(want), t)
+
+
+def oracle_theta0_sample(inst, k, s, seed, n, trials, beta=0.25):
+    """theta^0 of up to n evenly spaced candidates of `trials` trials, built by
+    the oracle alone (hash, enrichment and Section 5.1's starting model) and
+    rounded to float32: the shared input of EM parity tests."""
+    import oracle as O
+    codes = O.encode(inst.ascii)
+    h = O.hash_trials(codes, inst.seq_off, inst.l, k, s, seed, 0, trials)
+    C = h["cand_key"].size
+    idx = np.unique(np.linspace(0, C - 1, min(n, C)).astype(np.int64))
+    th = np.stack([O.theta0(codes, inst.seq_off, inst.l,
+                            h["members"][h["cand_off"][c]:h["cand_off"][c + 1]], beta) for c in idx])
+    return th.astype(np.float32)

@@ -15,7 +15,7 @@ import torch
 
 import oracle as O
 from synth import instance_for_config, planted_instance
-from tests.conftest import ll_tol
+from tests.conftest import ll_tol, oracle_theta0_sample
 
 pytestmark = pytest.mark.gpu
 
@@ -36,11 +36,7 @@ def upload(P, ascii_bytes):
 
 
 def _theta0(P, inst, packed, k, s, seed, n, trials=20):
-    h = P.trial_hash(packed, inst.seq_off, inst.l, k, s, seed, 0, trials)
-    C = h["n_candidates"]
-    th = P.theta0_build(packed, inst.seq_off, inst.l, h["cand_off"], h["members"], C, 0.25)
-    idx = np.unique(np.linspace(0, C - 1, min(n, C)).astype(np.int64))
-    return th.cpu().numpy()[idx]
+    return oracle_theta0_sample(inst, k, s, seed, n, trials)
 
 
 CASES = {

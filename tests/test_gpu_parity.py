@@ -11,7 +11,7 @@ import torch
 
 import oracle as O
 from synth import instance_for_config, planted_instance
-from tests.conftest import ll_tol
+from tests.conftest import ll_tol, oracle_theta0_sample
 
 pytestmark = pytest.mark.gpu
 
@@ -231,12 +231,14 @@ def _candidates(P, inst, cfg_seed, trials=None):
 @pytest.mark.parametrize("cfg", [1, 2])
 def test_theta0_matches_oracle(P, cfg):
     inst = instance_for_config(cfg)
-    packed, h = _candidates(P, inst, 1000 + cfg, trials=40)
-    C = h["n_candidates"]
-    th = P.theta0_build(packed, inst.seq_off, inst.l, h["cand_off"], h["members"], C, 0.25)
     codes = O.encode(inst.ascii)
-    mem, co = h["members"].cpu().numpy(), h["cand_off"].cpu().numpy()
-    want = O.theta0_all(codes, inst.seq_off, inst.l, co, mem, 0.25)
+    prm = inst.params
+    oh = O.hash_trials(codes, inst.seq_off, inst.l, prm["k"], prm["s"], 1000 + cfg, 0, 40)
+    want = O.theta0_all(codes, inst.seq_off, inst.l, oh["cand_off"], oh["members"], 0.25)
+    packed = upload(P, inst.ascii)
+    co = torch.from_numpy(oh["cand_off"].astype(np.int64)).cuda()
+    mem = torch.from_numpy(oh["members"].astype(np.int32)).cuda()
+    th = P.theta0_build(packed, inst.seq_off, inst.l, co, mem, oh["cand_key"].size, 0.25)
     assert np.max(np.abs(th.cpu().numpy() - want)) <= 1e-6
 
 
@@ -252,11 +254,7 @@ def _em_case(P, inst, theta0_f32, iters, beta, precision):
 
 
 def _sample_theta0(P, inst, seed, n, trials=30):
-    packed, h = _candidates(P, inst, seed, trials=trials)
-    C = h["n_candidates"]
-    th = P.theta0_build(packed, inst.seq_off, inst.l, h["cand_off"], h["members"], C, 0.25)
-    idx = np.unique(np.linspace(0, C - 1, min(n, C)).astype(np.int64))
-    return th.cpu().numpy()[idx]
+    return oracle_theta0_sample(inst, inst.params["k"], inst.params["s"], seed, n, trials)
 
 
 @pytest.mark.parametrize("cfg,n,iters", [(1, 300, 5), (1, 9, 5), (2, 200, 5), (3, 64, 8),
