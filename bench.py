@@ -7,7 +7,10 @@ Philox positions, projection, hashing and bucket counts for all m trials ->
 enriched-bucket lists -> theta^0 -> EM for every enriched bucket -> FP64
 ranking, consensus, sites.  Default workload: planted (15,4), t = 20 x n = 600,
 k = 7, s = 4, m = 172 (the Section 5 bound at q = 0.95), 5 EM iterations,
-pseudocount 0.25.
+pseudocount 0.25.  EM runs on the tensor cores with the BF16 hi + lo split
+(--precision fp32 selects the plain FP32 SIMT path); the line also gives one
+step of the other precision through the same call and, for both, the errors
+against the FP64 oracle from identical starting models.
 
 Prints one JSON line.  `value` is EM l-mer x PWM scores per second over the
 whole step (scores per step = x * C * (em_iters + 1), C = enriched buckets);
@@ -151,6 +154,37 @@ def peaks():
         return d, "measured"
     except (OSError, ValueError):
         return {"hbm_gbs": FALLBACK_HBM_GBS, "bf16_tflops": FALLBACK_BF16_TFLOPS}, "fallback"
+
+
+def em_error_report(P, inst, packed, k, s, seed, iters, beta, dev, n_sample=16, trials=2):
+    """Errors of both EM precisions against the FP64 oracle from identical
+    starting models: theta^0 of the n_sample largest buckets of the first
+    `trials` trials, hashed and built by the oracle (inputs of the GPU leg are
+    the float32 rounding of the oracle's theta^0)."""
+    import torch
+
+    import oracle as O
+    codes = O.encode(inst.ascii)
+    off = inst.seq_off
+    h = O.hash_trials(codes, off, inst.l, k, s, seed, 0, trials)
+    sel = O.top_candidates(h["cand_cnt"], n_sample)
+    th0 = np.stack([O.theta0(codes, off, inst.l, h["members"][h["cand_off"][c]:h["cand_off"][c + 1]],
+                             beta) for c in sel]).astype(np.float32)
+    w_pwm, w_ll = O.em(codes, off, inst.l, O.background(codes), th0.astype(np.float64), iters,
+                       beta, nthreads=os.cpu_count() or 1)
+    bg = P.projection_background(packed, off[-1])
+    out = {}
+    for name, prec in (("bf16_split", P.PROJ_EM_BF16_SPLIT), ("fp32", P.PROJ_EM_FP32)):
+        g_pwm, g_ll = P.em_refine(packed, off, inst.l, bg, torch.from_numpy(th0).to(dev), iters,
+                                  beta, prec)
+        g_pwm, g_ll = g_pwm.cpu().numpy(), g_ll.cpu().numpy()
+        out[name] = {"pwm_max_abs": float(np.abs(g_pwm - w_pwm).max()),
+                     "ll_max_rel": float((np.abs(g_ll - w_ll) /
+                                          np.maximum(np.abs(w_ll), inst.t)).max()),
+                     "consensus_equal_frac": float(np.mean(
+                         [O.consensus(g_pwm[q]) == O.consensus(w_pwm[q])
+                          for q in range(len(sel))]))}
+    return out, int(len(sel))
 
 
 # ---------------------------------------------------------------------------
@@ -383,29 +417,8 @@ def run_top(args):
     R = res["n_refined"]
     scores = x * R * (iters + 1)
 
-    # errors against the FP64 oracle on a sample of the refined models
-    h = P.trial_hash(packed, off, inst.l, k, s, seed, 0, m)
-    cnt = h["cand_cnt"].cpu().numpy()
-    sel = O.top_candidates(cnt, top)
-    co = h["cand_off"].cpu().numpy()
-    mem = h["members"].cpu().numpy()
-    sub = sel[:: max(1, sel.size // args.err_sample)][: args.err_sample]
-    codes = O.encode(inst.ascii)
-    th0 = np.stack([O.theta0(codes, off, inst.l, mem[co[c]:co[c + 1]], beta) for c in sub])
-    bg = P.projection_background(packed, off[-1])
-    errs = {}
-    w_pwm, w_ll = O.em(codes, off, inst.l, O.background(codes), th0.astype(np.float32)
-                       .astype(np.float64), iters, beta, nthreads=os.cpu_count() or 1)
-    for name, prec in (("bf16_split", P.PROJ_EM_BF16_SPLIT), ("fp32", P.PROJ_EM_FP32)):
-        g_pwm, g_ll = P.em_refine(packed, off, inst.l, bg,
-                                  torch.from_numpy(th0.astype(np.float32)).to(dev), iters, beta,
-                                  prec)
-        g_pwm, g_ll = g_pwm.cpu().numpy(), g_ll.cpu().numpy()
-        errs[name] = {"pwm_max_abs": float(np.abs(g_pwm - w_pwm).max()),
-                      "ll_max_rel": float((np.abs(g_ll - w_ll) /
-                                           np.maximum(np.abs(w_ll), inst.t)).max()),
-                      "consensus_equal_frac": float(np.mean(
-                          [O.consensus(g_pwm[q]) == O.consensus(w_pwm[q]) for q in range(len(sub))]))}
+    errs, n_err = em_error_report(P, inst, packed, k, s, seed, iters, beta, dev,
+                                  n_sample=args.err_sample, trials=1)
     pk, pk_kind = peaks()
     flops = args.steps * x * R * (iters * 16 * inst.l + 8 * inst.l)
     achieved = flops / (em_ms / 1e3) / 1e12 if em_ms > 0 else None
@@ -421,7 +434,8 @@ def run_top(args):
         "n_candidates": res["n_candidates"], "n_refined": R,
         "fp32_ms_per_step": T32 * 1e3, "motif_found": res["consensus"],
         "motif_found_fp32": res32["consensus"], "motif_planted": inst.motif,
-        "errors_vs_fp64_oracle": errs, "error_sample": int(len(sub)),
+        "errors_vs_fp64_oracle": errs,
+        "error_sample": f"{n_err} largest buckets of trial 0 (oracle hash + theta0), {iters} EM iters",
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if achieved else None, "traffic": None,
                      "kernel": "em_tc_kernel", "launches": em_launches,
@@ -444,7 +458,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--config", type=int, default=2)
-    ap.add_argument("--precision", choices=["fp32", "bf16split"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16split"], default="bf16split")
     ap.add_argument("--ref-sample", type=int, default=6000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-inst", type=int, default=256)
@@ -580,6 +594,22 @@ def main():
     e2e = {"value": scores_step / e2e_T, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_T * 1e3}
 
+    # the other precision through the same call (one step, after the timed region)
+    other = P.PROJ_EM_FP32 if prec == P.PROJ_EM_BF16_SPLIT else P.PROJ_EM_BF16_SPLIT
+    flush.fill_(0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r_other = P.projection_find_packed(packed, off, inst.l, inst.d, k, s, m, seed=seed,
+                                       em_iters=iters, pseudocount=beta, precision=other)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    other_ms = e0.elapsed_time(e1)
+    errs = None
+    if rank == 0 and not args.no_cpu_baseline:
+        errs, n_err = em_error_report(P, inst, packed, k, s, seed, iters, beta, dev,
+                                      n_sample=args.err_sample)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": T_job * 1e3 / args.steps,
@@ -589,6 +619,12 @@ def main():
         "hashes_per_s": hashes, "instances_per_s": inst_rate,
         "n_candidates": C, "scores_per_step": scores_step,
         "motif_found": res["consensus"], "motif_planted": inst.motif,
+        ("fp32" if other == P.PROJ_EM_FP32 else "bf16_split") + "_ms_per_step": other_ms,
+        ("motif_found_fp32" if other == P.PROJ_EM_FP32 else "motif_found_bf16_split"):
+            r_other["consensus"],
+        "errors_vs_fp64_oracle": errs,
+        "error_sample": (f"{args.err_sample} largest buckets of trials 0-1 (oracle hash + "
+                         f"theta0), {iters} EM iters") if errs else None,
         "wall_ms_per_step": wall * 1e3 / args.steps,
         "flush_ms_per_step": float(np.mean(flush_ms)),
         "roofline": roof, "clocks": clk, "e2e": e2e,

@@ -12,17 +12,20 @@
 // range of its sequences); a CTA (128 threads = the 128 lanes of tensor
 // memory) takes items in turn from the list (persistent over the list when the
 // grid is smaller than it), so one launch serves one motif search or a batch of
-// many instances of different t, n and l.  Per tile of NT l-mers of a sequence:
-//   1. the CTA writes the one-hot tile X [NT x 4l] to shared memory (from the
-//      sequence's packed words, staged in shared memory);
-//   2. one thread issues S = W_hi X^T + W_lo X^T (M=128, N=NT, K=16*ceil(4l/16),
+// many instances of different t, n and l.  Per tile of 64 l-mers of a sequence:
+//   1. the CTA writes the one-hot tile X [64 x 4l] to shared memory (from the
+//      item's packed words, staged in shared memory);
+//   2. one thread issues S = W_hi X^T + W_lo X^T (M=128, N=64, K=16*ceil(4l/16),
 //      FP32 accumulation in tensor memory; W split into BF16 hi + lo parts so
 //      the product carries ~16 mantissa bits of W);
 //   3. thread i reads row i of S, keeps a running maximum and a compensated
 //      running sum of 2^(S - max) for its candidate, rescales its row of O when
 //      the maximum grows, and writes P = 2^(S - max) as BF16 hi + lo parts;
-//   4. one thread issues O += P_hi X + P_lo X (M=128, N=16*ceil(4l/16), K=NT)
+//   4. one thread issues O += P_hi X + P_lo X (M=128, N=16*ceil(4l/16), K=64)
 //      with X read in MN-major form from the same shared-memory tile.
+// The steps of consecutive tiles overlap (two score buffers in tensor memory,
+// a ring of three one-hot tiles): the score MMA of tile i+1 and the count MMA
+// of tile i-1 run on the tensor core while the CUDA cores work on tile i.
 // At the end of a sequence O / sum is added to the candidate's counts and
 // max + log2(sum) to its log-likelihood.  Scores are kept in log2 units
 // (W = log2 theta - log2 bg) so the exponentials are exp2.
@@ -65,20 +68,25 @@ struct EmTcParams {
     int *err;
 };
 
-template <int KP, int NT>
+constexpr int kNT = 64;  // l-mers per tile (N of the score MMA, K of the count MMA)
+
+template <int KP>
 struct TcLayout {
-    static constexpr int W_BYTES = 128 * KP * 2;  // each of W_hi, W_lo
-    static constexpr int X_BYTES = NT * KP * 2;
-    static constexpr int P_BYTES = 128 * NT * 2;  // each of P_hi, P_lo
+    static constexpr int W_BYTES = 128 * KP * 2;   // each of W_hi, W_lo
+    static constexpr int X_BYTES = kNT * KP * 2;   // one one-hot tile
+    static constexpr int NX = 3;                   // ring of one-hot tiles
+    static constexpr int P_BYTES = 128 * kNT * 2;  // each of P_hi, P_lo
     static constexpr int OFF_WHI = 0;
     static constexpr int OFF_WLO = OFF_WHI + W_BYTES;
     static constexpr int OFF_X = OFF_WLO + W_BYTES;
-    static constexpr int OFF_PHI = OFF_X + X_BYTES;
+    static constexpr int OFF_PHI = OFF_X + NX * X_BYTES;
     static constexpr int OFF_PLO = OFF_PHI + P_BYTES;
-    static constexpr int SEQ_WORDS = 512;  // staged packed words of one sequence (8K bases)
+    static constexpr int SEQ_WORDS = 1024;  // staged packed words of an item (16K bases)
     static constexpr int OFF_SEQ = OFF_PLO + P_BYTES;
     static constexpr int TOTAL = OFF_SEQ + SEQ_WORDS * 4;
-    static constexpr uint32_t TMEM_COLS = (NT + KP <= 128) ? 128u : 256u;
+    // two score buffers S[2] (kNT columns each) and the count accumulator O (KP)
+    static constexpr uint32_t TMEM_COLS = 256;
+    static_assert(2 * kNT + KP <= 256, "tensor-memory budget");
 };
 
 __device__ __forceinline__ float ex2(float x) {
@@ -99,11 +107,85 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-template <int KP, int NT>
-__global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 3 : 2)) em_tc_kernel(const EmTcParams P) {
-    using LY = TcLayout<KP, NT>;
+// Walks the l-mer tiles of an item's sequences in order: sequence seq, first
+// start j0 of the tile, ns = number of starts of the sequence, base = its
+// first base in the packed input.
+struct TileIt {
+    int seq, j0, ns;
+    int64_t base;
+    __device__ __forceinline__ void load(const EmInst &in) {
+        base = in.seq_off[seq];
+        ns = (int)(in.seq_off[seq + 1] - base) - in.l + 1;
+    }
+    __device__ __forceinline__ void start(const EmInst &in, int s0) {
+        seq = s0;
+        j0 = 0;
+        load(in);
+    }
+    __device__ __forceinline__ bool last() const { return j0 + kNT >= ns; }
+    __device__ __forceinline__ void advance(const EmInst &in, int seq_hi) {
+        j0 += kNT;
+        if (j0 >= ns) {
+            ++seq;
+            j0 = 0;
+            if (seq < seq_hi) load(in);
+        }
+    }
+};
+
+// One-hot tile X[j][p*4+a] = [x_{j0+j+p} = a] of the l-mers of tile `t`:
+// thread (row j, half) writes the 16-byte chunks (two positions each, BF16
+// 1.0 = 0x3F80 in the slot of the base's code) of its half of row j, from one
+// 64-bit window of the packed sequence (staged words when `staged`).
+template <int KP>
+__device__ __forceinline__ void build_x(uint8_t *sX, const TileIt &t, int l, const uint32_t *sSeq,
+                                        int nw_st, int64_t w_first, bool staged,
+                                        const uint32_t *packed, int64_t nwords, int tid) {
+    static_assert(kTcThreads == 2 * kNT, "two threads per row");
+    constexpr int kChunks = KP / 8;
+    const int j = tid % kNT, part = tid / kNT;
+    const bool row_ok = j < t.ns - t.j0;
+    uint64_t win = 0;
+    if (row_ok) {
+        const int64_t b0 = t.base + t.j0 + j;
+        win = staged ? window64(sSeq, nw_st, b0 - (w_first << 4)) : window64(packed, nwords, b0);
+    }
+#pragma unroll
+    for (int kb = part; kb < kChunks; kb += 2) {
+        uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
+        const int p0 = 2 * kb, p1 = 2 * kb + 1;
+        if (row_ok && p0 < l) {
+            const uint32_t code = (uint32_t)(win >> (2 * p0)) & 3u;
+            const uint32_t v = 0x3F80u << (16 * (code & 1u));
+            if (code >> 1) w1 = v; else w0 = v;
+        }
+        if (row_ok && p1 < l) {
+            const uint32_t code = (uint32_t)(win >> (2 * p1)) & 3u;
+            const uint32_t v = 0x3F80u << (16 * (code & 1u));
+            if (code >> 1) w3 = v; else w2 = v;
+        }
+        *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(j, 8 * kb, KP)) = make_uint4(w0, w1, w2, w3);
+    }
+}
+
+// Software pipeline over the tiles i = 0 .. n-1 of an item (one __syncthreads
+// per tile):
+//   - the score MMA of tile i+1 is issued before the softmax of tile i, into
+//     the other score buffer, so the tensor core works while the CUDA cores
+//     compute exponentials;
+//   - the count MMA of tile i is issued after its P is written and runs
+//     during the softmax of tile i+1;
+//   - the one-hot tile of i+2 is built during tile i, into a ring of three
+//     (tiles i and i+1 are still read by issued MMAs).
+// Waits: S(i) before its softmax; the count MMA of i-1 before P(i) overwrites
+// P and before slot (i+2) % 3 = (i-1) % 3 is rebuilt; the count MMA of a
+// sequence's last tile before its O is read.
+template <int KP>
+__global__ void __launch_bounds__(kTcThreads, 2) em_tc_kernel(const EmTcParams P) {
+    using LY = TcLayout<KP>;
+    constexpr int NT = kNT;
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbS[2], mbO, mbEnd;
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5;
     uint8_t *sWhi = smem + LY::OFF_WHI, *sWlo = smem + LY::OFF_WLO, *sX = smem + LY::OFF_X;
@@ -111,7 +193,10 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 3 : 2)) em_tc_kernel(c
     uint32_t *sSeq = reinterpret_cast<uint32_t *>(smem + LY::OFF_SEQ);
 
     if (tid == 0) {
-        tc::mbar_init(&mbar, 1);
+        tc::mbar_init(&mbS[0], 1);
+        tc::mbar_init(&mbS[1], 1);
+        tc::mbar_init(&mbO, 1);
+        tc::mbar_init(&mbEnd, 1);
         tc::mbar_fence_init();
     }
     if (warp == 0) {
@@ -122,13 +207,24 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 3 : 2)) em_tc_kernel(c
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tm = tmem_slot;
-    const uint32_t tS = tm, tO = tm + NT;
+    const uint32_t tO = tm + 2 * NT;
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     const uint32_t aWhi = tc::smem_addr(sWhi), aWlo = tc::smem_addr(sWlo);
     const uint32_t aX = tc::smem_addr(sX), aPhi = tc::smem_addr(sPhi), aPlo = tc::smem_addr(sPlo);
     constexpr uint32_t IDESC_S = tc::idesc_bf16(128, NT);
-    uint32_t phase = 0;
-    bool abort = false;
+    uint32_t phS = 0u;            // bit b: parity of the next completion of score buffer b
+    uint32_t o_waited = 0;        // count MMAs of this CTA known complete (in issue order)
+    uint32_t o_base = 0;          // count MMAs issued before the current item
+    bool ok = true, abort = false;
+
+    // waits until the first `target` count MMAs of the current item have
+    // completed; completion j (0-based, over the CTA's life) has parity j & 1
+    auto wait_o = [&](uint32_t target) {
+        while (ok && o_waited < o_base + target) {
+            ok = tc::mbar_wait(&mbO, o_waited & 1u, kWaitNs);
+            ++o_waited;
+        }
+    };
 
     for (int it = blockIdx.x; it < P.n_items && !abort; it += gridDim.x) {
         const EmItem item = P.items[it];
@@ -139,9 +235,8 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 3 : 2)) em_tc_kernel(c
         const int64_t c = item.c0 + tid;
         const bool valid = tid < item.nc;
 
-        // W_c = log2 theta_c - log2 bg in FP32 (~2^-23 relative, far below the
-        // 2^-16 of the BF16 hi + lo pair), split into BF16 hi + lo (row tid)
         __syncthreads();  // the previous item's MMAs and reads are complete
+        // W_c = log2 theta_c - log2 bg in FP32, split into BF16 hi + lo (row tid)
         float lbg[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) lbg[a] = log2f((float)in.bg[a]);
@@ -167,223 +262,222 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 3 : 2)) em_tc_kernel(c
             *reinterpret_cast<uint4 *>(sWlo + tc::kmajor_off(tid, k8, KP)) =
                 make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
-        tc::fence_async_smem();
+        // the packed words of the item's sequences (+2 for the 64-bit windows)
+        const int64_t b_lo = in.seq_off[item.seq_lo], b_hi = in.seq_off[item.seq_hi];
+        const int64_t w_first = b_lo >> 4;
+        const int nw_st = (int)(((b_hi + 15) >> 4) - w_first) + 2;
+        const bool staged = nw_st <= LY::SEQ_WORDS;
+        if (staged)
+            for (int w = tid; w < nw_st; w += kTcThreads)
+                sSeq[w] = (w_first + w) < P.nwords ? __ldg(P.packed + w_first + w) : 0u;
+        // number of tiles of the item
+        int n = 0;
+        for (int s = item.seq_lo; s < item.seq_hi; ++s)
+            n += ((int)(in.seq_off[s + 1] - in.seq_off[s]) - l + 1 + NT - 1) / NT;
+        __syncthreads();  // staged words visible to build_x
 
-        // this item's normalised counts of candidate c, summed over its sequences
-        float tot[KP];
+        TileIt tb, tcur;
+        tb.start(in, item.seq_lo);
+        tcur.start(in, item.seq_lo);
+        build_x<KP>(sX, tb, l, sSeq, nw_st, w_first, staged, P.packed, P.nwords, tid);
+        tb.advance(in, item.seq_hi);
+        if (n > 1) {
+            build_x<KP>(sX + LY::X_BYTES, tb, l, sSeq, nw_st, w_first, staged, P.packed, P.nwords, tid);
+            tb.advance(in, item.seq_hi);
+        }
+        tc::fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            for (int s = 0; s < kq; ++s)
+                tc::mma_bf16(tm, tc::sdesc(aWhi + 256 * s, 128, KP * 16),
+                             tc::sdesc(aX + 256 * s, 128, KP * 16), IDESC_S, s > 0);
+            for (int s = 0; s < kq; ++s)
+                tc::mma_bf16(tm, tc::sdesc(aWlo + 256 * s, 128, KP * 16),
+                             tc::sdesc(aX + 256 * s, 128, KP * 16), IDESC_S, 1);
+            tc::mma_commit(&mbS[0]);
+        }
+
+        float tot[KP];  // this item's normalised counts of candidate c
 #pragma unroll
         for (int q = 0; q < KP; ++q) tot[q] = 0.f;
         double ll = 0.0;
+        float m = -INFINITY, Ssum = 0.f, Scmp = 0.f;
+        bool first = true;
+        o_base = o_waited;  // every count MMA of earlier items was waited for
 
-        for (int i = item.seq_lo; i < item.seq_hi && !abort; ++i) {
-            const int64_t base = in.seq_off[i];
-            const int n_i = in.seq_off[i + 1] - in.seq_off[i];
-            const int ns = n_i - l + 1;
-            float m = -INFINITY, Ssum = 0.f, Scmp = 0.f;
-            bool first = true;
-            // packed words covering this sequence (+2 for the 64-bit windows)
-            const int64_t w_first = base >> 4;
-            const int nw_seq = (int)(((base + n_i + 15) >> 4) - w_first) + 2;
-            const bool staged = nw_seq <= LY::SEQ_WORDS;
-            __syncthreads();  // the previous sequence's words are no longer read
-            if (staged)
-                for (int w = tid; w < nw_seq; w += kTcThreads)
-                    sSeq[w] = (w_first + w) < P.nwords ? __ldg(P.packed + w_first + w) : 0u;
-            __syncthreads();
-            for (int j0 = 0; j0 < ns; j0 += NT) {
-                const int nvalid = min(NT, ns - j0);
-                // 1. one-hot tile X[j][p*4+a] = [x_{j0+j+p} = a]: thread (j, half) writes
-                //    16-byte chunks kb (two positions each, BF16 1.0 = 0x3F80 in the slot of
-                //    the base's code) of row j from one 64-bit window
-                static_assert(kTcThreads % NT == 0, "rows must divide the CTA");
-                {
-                    constexpr int kSplit = kTcThreads / NT;  // threads per row
-                    constexpr int kChunks = KP / 8;
-                    const int j = tid % NT, part = tid / NT;
-                    const bool row_ok = j < nvalid;
-                    uint64_t win = 0;
-                    if (row_ok)
-                        win = staged ? window64(sSeq, nw_seq, base + j0 + j - (w_first << 4))
-                                     : window64(P.packed, P.nwords, base + j0 + j);
+        for (int i = 0; i < n; ++i) {
+            const int b = i & 1;
+            const uint32_t tS = tm + NT * b;
+            // score MMA of tile i+1 (its one-hot tile and score buffer are free)
+            if (tid == 0 && i + 1 < n) {
+                tc::fence_after_sync();
+                const uint32_t xn = aX + ((i + 1) % 3) * LY::X_BYTES;
+                const uint32_t tSn = tm + NT * (b ^ 1);
+                for (int s = 0; s < kq; ++s)
+                    tc::mma_bf16(tSn, tc::sdesc(aWhi + 256 * s, 128, KP * 16),
+                                 tc::sdesc(xn + 256 * s, 128, KP * 16), IDESC_S, s > 0);
+                for (int s = 0; s < kq; ++s)
+                    tc::mma_bf16(tSn, tc::sdesc(aWlo + 256 * s, 128, KP * 16),
+                                 tc::sdesc(xn + 256 * s, 128, KP * 16), IDESC_S, 1);
+                tc::mma_commit(&mbS[b ^ 1]);
+            }
+            if (ok) ok = tc::mbar_wait(&mbS[b], (phS >> b) & 1u, kWaitNs);
+            phS ^= 1u << b;
+            tc::fence_after_sync();
+
+            // P = 2^(S - m) with m a reference near the row maximum: the exact
+            // maximum of the first tile of a sequence, then kept until a tile
+            // holds a score more than 20 above it (P > 2^20); only then is the
+            // maximum recomputed, the row's O and sum rescaled and the tile's P
+            // recomputed.  The tile is summed as a tree and added to the running
+            // sum with compensation.  Tensor-memory accesses are .sync.aligned,
+            // so every decision that guards them is taken per warp.
+            const int nvalid = min(NT, tcur.ns - tcur.j0);
+            const bool full = nvalid == NT;  // only a sequence's last tile is ragged
+            float v[NT];
+            tc::tmem_ld64(tS + lane_base, v);
+            if (first) {
+                float mx[8];
 #pragma unroll
-                    for (int kb = part; kb < kChunks; kb += kSplit) {
-                        uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
-                        const int p0 = 2 * kb, p1 = 2 * kb + 1;
-                        if (row_ok && p0 < l) {
-                            const uint32_t code = (uint32_t)(win >> (2 * p0)) & 3u;
-                            const uint32_t v = 0x3F80u << (16 * (code & 1u));
-                            if (code >> 1) w1 = v; else w0 = v;
+                for (int q = 0; q < 8; ++q) mx[q] = -INFINITY;
+#pragma unroll
+                for (int q = 0; q < NT; ++q)
+                    if (full || q < nvalid) mx[q & 7] = fmaxf(mx[q & 7], v[q]);
+#pragma unroll
+                for (int q = 1; q < 8; ++q) mx[0] = fmaxf(mx[0], mx[q]);
+                m = mx[0];
+            }
+            float add;
+            bool big;
+            {
+#pragma unroll
+                for (int q = 0; q < NT; ++q) v[q] = (full || q < nvalid) ? ex2(v[q] - m) : 0.f;
+                float part[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) part[q] = (v[q] + v[q + 16]) + (v[q + 32] + v[q + 48]);
+#pragma unroll
+                for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                    for (int q = 0; q < w; ++q) part[q] += part[q + w];
+                add = part[0];
+                big = !(add <= 1048576.f);  // some score > m + 20 (or a non-finite sum)
+            }
+            if (__any_sync(0xffffffffu, big)) {
+                // rare: re-read the scores, move the reference to the exact maximum
+                tc::tmem_ld64(tS + lane_base, v);
+                float tmax = -INFINITY;
+#pragma unroll
+                for (int q = 0; q < NT; ++q)
+                    if (full || q < nvalid) tmax = fmaxf(tmax, v[q]);
+                const bool grow = tmax > m;
+                const float sc = grow ? ex2(m - tmax) : 1.f;
+                if (grow) {
+                    Ssum *= sc;
+                    Scmp *= sc;
+                    m = tmax;
+                }
+                if (P.mstep && !first && __any_sync(0xffffffffu, grow)) {
+                    wait_o((uint32_t)i);  // O holds every count MMA issued so far
+                    tc::fence_after_sync();
+#pragma unroll
+                    for (int c0 = 0; c0 < KP; c0 += 16) {
+                        if (c0 < 16 * kq) {
+                            float o[16];
+                            tc::tmem_ld16(tO + lane_base + c0, o);
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) o[q] *= sc;
+                            tc::tmem_st16(tO + lane_base + c0, o);
                         }
-                        if (row_ok && p1 < l) {
-                            const uint32_t code = (uint32_t)(win >> (2 * p1)) & 3u;
-                            const uint32_t v = 0x3F80u << (16 * (code & 1u));
-                            if (code >> 1) w3 = v; else w2 = v;
-                        }
-                        *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(j, 8 * kb, KP)) =
-                            make_uint4(w0, w1, w2, w3);
                     }
                 }
-                tc::fence_async_smem();
-                __syncthreads();
-                // 2. S = W_hi X^T + W_lo X^T
+#pragma unroll
+                for (int q = 0; q < NT; ++q) v[q] = (full || q < nvalid) ? ex2(v[q] - m) : 0.f;
+                float part[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) part[q] = (v[q] + v[q + 16]) + (v[q + 32] + v[q + 48]);
+#pragma unroll
+                for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+                    for (int q = 0; q < w; ++q) part[q] += part[q + w];
+                add = part[0];
+            }
+            kahan(Ssum, Scmp, add);
+
+            if (P.mstep) {
+                wait_o((uint32_t)i);  // the count MMA of tile i-1 has read P and X(i-1)
+#pragma unroll
+                for (int g = 0; g < NT / 8; ++g) {
+                    uint32_t hi[4], lo[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float a0 = v[8 * g + 2 * q], a1 = v[8 * g + 2 * q + 1];
+                        const uint32_t h = pack_bf16(a0, a1);
+                        hi[q] = h;
+                        lo[q] = pack_bf16(a0 - __uint_as_float(h << 16),
+                                          a1 - __uint_as_float(h & 0xFFFF0000u));
+                    }
+                    *reinterpret_cast<uint4 *>(sPhi + tc::kmajor_off(tid, 8 * g, NT)) =
+                        make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    *reinterpret_cast<uint4 *>(sPlo + tc::kmajor_off(tid, 8 * g, NT)) =
+                        make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                }
+            }
+            // one-hot tile of i+2 into the slot of tile i-1
+            if (i + 2 < n) {
+                build_x<KP>(sX + ((i + 2) % 3) * LY::X_BYTES, tb, l, sSeq, nw_st, w_first, staged,
+                            P.packed, P.nwords, tid);
+                tb.advance(in, item.seq_hi);
+            }
+            tc::fence_before_sync();
+            tc::fence_async_smem();
+            abort = __syncthreads_or(!ok);
+            if (abort) break;
+            const bool seq_end = tcur.last();
+            if (P.mstep) {
+                // O (+)= P_hi X + P_lo X, X read in MN-major form
                 if (tid == 0) {
                     tc::fence_after_sync();
-                    for (int s = 0; s < kq; ++s)
-                        tc::mma_bf16(tS, tc::sdesc(aWhi + 256 * s, 128, KP * 16),
-                                     tc::sdesc(aX + 256 * s, 128, KP * 16), IDESC_S, s > 0);
-                    for (int s = 0; s < kq; ++s)
-                        tc::mma_bf16(tS, tc::sdesc(aWlo + 256 * s, 128, KP * 16),
-                                     tc::sdesc(aX + 256 * s, 128, KP * 16), IDESC_S, 1);
-                    tc::mma_commit(&mbar);
+                    const uint32_t xc = aX + (i % 3) * LY::X_BYTES;
+#pragma unroll
+                    for (int s = 0; s < NT / 16; ++s)
+                        tc::mma_bf16(tO, tc::sdesc(aPhi + 256 * s, 128, NT * 16),
+                                     tc::sdesc(xc + s * 2 * KP * 16, KP * 16, 128), idesc_o,
+                                     (s > 0 || !first) ? 1u : 0u);
+#pragma unroll
+                    for (int s = 0; s < NT / 16; ++s)
+                        tc::mma_bf16(tO, tc::sdesc(aPlo + 256 * s, 128, NT * 16),
+                                     tc::sdesc(xc + s * 2 * KP * 16, KP * 16, 128), idesc_o, 1u);
+                    tc::mma_commit(&mbO);
                 }
-                bool ok = tc::mbar_wait(&mbar, phase, kWaitNs);
-                phase ^= 1u;
-                abort = __syncthreads_or(!ok);
-                if (abort) break;
-                tc::fence_after_sync();
-                // 3. P = 2^(S - m) with m a reference near the row maximum: the exact
-                //    maximum of the first tile of a sequence, then kept until a tile
-                //    holds a score more than 20 above it (P > 2^20); only then is the
-                //    maximum recomputed and the row's O and sum rescaled.  Each 32-column
-                //    chunk is summed as a tree and the chunk sums are added with
-                //    compensation.  The tensor-memory accesses are .sync.aligned, so
-                //    every decision that guards them is taken per warp.
-                const bool full = nvalid == NT;  // only a sequence's last tile is ragged
-                bool redo = first;
-                for (int pass = 0; pass < 2; ++pass) {
-                    if (redo) {
-                        float tmax = -INFINITY;
-#pragma unroll
-                        for (int c0 = 0; c0 < NT; c0 += 32) {
-                            float v[32];
-                            tc::tmem_ld32(tS + lane_base + c0, v);
-                            float mx[8];
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) mx[q] = -INFINITY;
-                            if (full) {
-#pragma unroll
-                                for (int q = 0; q < 32; ++q) mx[q & 7] = fmaxf(mx[q & 7], v[q]);
-                            } else {
-#pragma unroll
-                                for (int q = 0; q < 32; ++q)
-                                    if (c0 + q < nvalid) mx[q & 7] = fmaxf(mx[q & 7], v[q]);
-                            }
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) tmax = fmaxf(tmax, mx[q]);
-                        }
-                        const bool grow = tmax > m;
-                        const float sc = grow ? ex2(m - tmax) : 1.f;  // 0 when m = -inf
-                        if (grow) {
-                            Ssum *= sc;
-                            Scmp *= sc;
-                            m = tmax;
-                        }
-                        if (P.mstep && !first && __any_sync(0xffffffffu, grow)) {
-#pragma unroll
-                            for (int c0 = 0; c0 < KP; c0 += 16) {
-                                if (c0 < 16 * kq) {
-                                    float v[16];
-                                    tc::tmem_ld16(tO + lane_base + c0, v);
-#pragma unroll
-                                    for (int q = 0; q < 16; ++q) v[q] *= sc;
-                                    tc::tmem_st16(tO + lane_base + c0, v);
-                                }
-                            }
-                        }
-                    }
-                    float add = 0.f;  // this tile's sum, chunk by chunk
-                    bool big = false;
-#pragma unroll
-                    for (int c0 = 0; c0 < NT; c0 += 32) {
-                        float v[32];
-                        tc::tmem_ld32(tS + lane_base + c0, v);
-                        if (full) {
-#pragma unroll
-                            for (int q = 0; q < 32; ++q) v[q] = ex2(v[q] - m);
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < 32; ++q) v[q] = (c0 + q < nvalid) ? ex2(v[q] - m) : 0.f;
-                        }
-                        float part[16];
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) part[q] = v[2 * q] + v[2 * q + 1];
-#pragma unroll
-                        for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-                            for (int q = 0; q < w; ++q) part[q] += part[q + w];
-                        add += part[0];
-                        big |= part[0] > 1048576.f;  // some score > m + 20 (or NaN-free inf)
-                        if (P.mstep) {
-                            uint32_t hi[16], lo[16];
-#pragma unroll
-                            for (int q = 0; q < 16; ++q) {
-                                const uint32_t h = pack_bf16(v[2 * q], v[2 * q + 1]);
-                                const float h0 = __uint_as_float(h << 16);
-                                const float h1 = __uint_as_float(h & 0xFFFF0000u);
-                                hi[q] = h;
-                                lo[q] = pack_bf16(v[2 * q] - h0, v[2 * q + 1] - h1);
-                            }
-#pragma unroll
-                            for (int b = 0; b < 4; ++b) {
-                                *reinterpret_cast<uint4 *>(sPhi + tc::kmajor_off(tid, c0 + 8 * b, NT)) =
-                                    make_uint4(hi[4 * b], hi[4 * b + 1], hi[4 * b + 2], hi[4 * b + 3]);
-                                *reinterpret_cast<uint4 *>(sPlo + tc::kmajor_off(tid, c0 + 8 * b, NT)) =
-                                    make_uint4(lo[4 * b], lo[4 * b + 1], lo[4 * b + 2], lo[4 * b + 3]);
-                            }
-                        }
-                    }
-                    redo = __any_sync(0xffffffffu, big) && pass == 0;
-                    if (!redo) {
-                        kahan(Ssum, Scmp, add);
-                        break;
-                    }
-                }
-                tc::fence_before_sync();
+            }
+            first = false;
+            if (seq_end) {
+                const float Sf = Ssum - Scmp;
+                ll += (double)((m + log2f(Sf)) * 0.69314718f - logf((float)tcur.ns));
                 if (P.mstep) {
-                    // 4. O += P_hi X + P_lo X
-                    tc::fence_async_smem();
-                    __syncthreads();
-                    if (tid == 0) {
-                        tc::fence_after_sync();
-#pragma unroll
-                        for (int s = 0; s < NT / 16; ++s)
-                            tc::mma_bf16(tO, tc::sdesc(aPhi + 256 * s, 128, NT * 16),
-                                         tc::sdesc(aX + s * 2 * KP * 16, KP * 16, 128), idesc_o,
-                                         (s > 0 || !first) ? 1u : 0u);
-#pragma unroll
-                        for (int s = 0; s < NT / 16; ++s)
-                            tc::mma_bf16(tO, tc::sdesc(aPlo + 256 * s, 128, NT * 16),
-                                         tc::sdesc(aX + s * 2 * KP * 16, KP * 16, 128), idesc_o, 1u);
-                        tc::mma_commit(&mbar);
-                    }
-                    ok = tc::mbar_wait(&mbar, phase, kWaitNs);
-                    phase ^= 1u;
-                    abort = __syncthreads_or(!ok);
-                    if (abort) break;
+                    wait_o((uint32_t)i + 1);
                     tc::fence_after_sync();
-                } else {
-                    __syncthreads();  // every row of S is read before the next tile rewrites it
-                }
-                first = false;
-            }
-            if (abort) break;
-            const float Sf = Ssum - Scmp;
-            ll += (double)((m + log2f(Sf)) * 0.69314718f - logf((float)ns));
-            if (P.mstep) {
-                const float inv = 1.f / Sf;
+                    const float inv = 1.f / Sf;
 #pragma unroll
-                for (int c0 = 0; c0 < KP; c0 += 16) {
-                    if (c0 < 16 * kq) {
-                        float v[16];
-                        tc::tmem_ld16(tO + lane_base + c0, v);
+                    for (int c0 = 0; c0 < KP; c0 += 16) {
+                        if (c0 < 16 * kq) {
+                            float o[16];
+                            tc::tmem_ld16(tO + lane_base + c0, o);
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) tot[c0 + q] += v[q] * inv;
+                            for (int q = 0; q < 16; ++q) tot[c0 + q] += o[q] * inv;
+                        }
                     }
+                    tc::fence_before_sync();  // O is read before the next count MMA restarts it
                 }
-                tc::fence_before_sync();
-                __syncthreads();  // O is read before the next sequence restarts it
+                m = -INFINITY;
+                Ssum = 0.f;
+                Scmp = 0.f;
+                first = true;
             }
+            tcur.advance(in, item.seq_hi);
         }
+        abort = __syncthreads_or(!ok || abort);
         if (abort) break;
         if (valid) {
             P.part_ll[(int64_t)item.g * P.C + c] = ll;
@@ -395,12 +489,10 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 3 : 2)) em_tc_kernel(c
             }
         }
     }
-    if (abort) {
-        if (tid == 0) atomicExch(P.err, 1);
-        // let any MMA still in flight finish (bounded) before freeing its memory:
-        // the phase that was being waited for has parity phase ^ 1
-        tc::mbar_wait(&mbar, phase ^ 1u, kWaitNs);
-    }
+    if (abort && tid == 0) atomicExch(P.err, 1);
+    // every MMA this CTA issued has completed (bounded) before its memory is freed
+    if (tid == 0) tc::mma_commit(&mbEnd);
+    tc::mbar_wait(&mbEnd, 0u, kWaitNs);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -438,14 +530,14 @@ __global__ void em_tc_reduce_kernel(const double *__restrict__ part_acc,
     }
 }
 
-template <int KP, int NT>
+template <int KP>
 int launch_tc(const EmTcParams &P, int grid, cudaStream_t st) {
-    using LY = TcLayout<KP, NT>;
-    PROJ_CUDA_TRY(cudaFuncSetAttribute(em_tc_kernel<KP, NT>,
+    using LY = TcLayout<KP>;
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(em_tc_kernel<KP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, LY::TOTAL));
     {
         TraceSpan ts_("em_tc", st);
-        em_tc_kernel<KP, NT><<<grid, kTcThreads, LY::TOTAL, st>>>(P);
+        em_tc_kernel<KP><<<grid, kTcThreads, LY::TOTAL, st>>>(P);
     }
     PROJ_LAUNCH_CHECK("em_tc_kernel");
     return PROJ_OK;
@@ -453,7 +545,7 @@ int launch_tc(const EmTcParams &P, int grid, cudaStream_t st) {
 
 template <int KP>
 int ctas_per_sm_kp() {
-    using LY = TcLayout<KP, 64>;
+    using LY = TcLayout<KP>;
     const int by_smem = 228 * 1024 / (LY::TOTAL + 1024 + 128);
     const int by_tmem = 512 / (int)LY::TMEM_COLS;
     return std::max(1, std::min(by_smem, by_tmem));
@@ -474,14 +566,14 @@ int ctas_per_sm(int kp) {
 
 int dispatch(int kp, const EmTcParams &P, int grid, cudaStream_t st) {
     switch (kp) {
-        case 16: return launch_tc<16, 64>(P, grid, st);
-        case 32: return launch_tc<32, 64>(P, grid, st);
-        case 48: return launch_tc<48, 64>(P, grid, st);
-        case 64: return launch_tc<64, 64>(P, grid, st);
-        case 80: return launch_tc<80, 64>(P, grid, st);
-        case 96: return launch_tc<96, 64>(P, grid, st);
-        case 112: return launch_tc<112, 64>(P, grid, st);
-        default: return launch_tc<128, 64>(P, grid, st);
+        case 16: return launch_tc<16>(P, grid, st);
+        case 32: return launch_tc<32>(P, grid, st);
+        case 48: return launch_tc<48>(P, grid, st);
+        case 64: return launch_tc<64>(P, grid, st);
+        case 80: return launch_tc<80>(P, grid, st);
+        case 96: return launch_tc<96>(P, grid, st);
+        case 112: return launch_tc<112>(P, grid, st);
+        default: return launch_tc<128>(P, grid, st);
     }
 }
 
@@ -498,8 +590,8 @@ int dispatch(int kp, const EmTcParams &P, int grid, cudaStream_t st) {
 namespace {
 
 struct Sched { int ctas, g_target; };
-const Sched kScheds[] = {{3, 2}, {3, 1}, {3, 4}, {2, 2}, {2, 4}, {1, 4}};
-constexpr Sched kDefaultSched = {3, 2};
+const Sched kScheds[] = {{2, 2}, {2, 1}, {2, 4}, {1, 2}, {1, 4}, {2, 8}};
+constexpr Sched kDefaultSched = {2, 2};
 
 std::mutex g_tune_mu;
 std::map<uint64_t, Sched> g_tuned;
