@@ -609,6 +609,7 @@ int projection_find_batch(const uint8_t *ascii, const int64_t *seq_off, const in
         cons_off += l[i];
         eh[i].t = t; eh[i].l = l[i]; eh[i].C = H.n_cand[i]; eh[i].cand_begin = H.cand_begin[i];
         eh[i].lmers = xs[i];
+        eh[i].seq_off = offs.data() + off_pos[i] + 2 * (t + 1);  // global positions
         ei[i].seq_off = bi[i].seq_off; ei[i].bg = bi[i].bg; ei[i].t = t; ei[i].l = l[i];
         ei[i].cand_begin = H.cand_begin[i];
         out[i].n_candidates = H.n_cand[i];

@@ -26,6 +26,7 @@ struct EmItem {
     int inst;        // instance index
     int seq_lo, seq_hi;
     int g;           // sequence group, selects the partial-result slot
+    int n_tiles;     // tiles of 64 l-mers over the item's sequences
 };
 
 // Host-side summary used to plan the items.
@@ -33,10 +34,11 @@ struct EmInstHost {
     int t = 0, l = 0;
     int64_t C = 0, cand_begin = 0;
     int64_t lmers = 0;
+    const int32_t *seq_off = nullptr;  // host copy of the instance's EmInst::seq_off [t+1]
 };
 
 int em_tc_plan(const std::vector<EmInstHost> &insts, std::vector<EmItem> &items, int &G,
-               int ctas, int g_target);
+               int ctas, int waves);
 
 // One tensor-core EM run split into allocation/planning (em_tc_prepare, may
 // synchronise to autotune), launches only (em_tc_enqueue, capturable in a
@@ -48,7 +50,7 @@ struct EmTcRun {
     const float *theta0 = nullptr;
     int64_t C = 0;
     int stride = 0, n_inst = 0, kp = 16, G = 1, ctas = 3, n_items = 0;
-    DevBuf part, tmp, flag, items;
+    DevBuf part, tmp, flag, items, tiles;
 };
 int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmInstHost> &insts,
                   const EmInst *inst_dev, const float *theta0, int64_t C, int stride,

@@ -50,7 +50,9 @@
 namespace proj {
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kSoftThreads = 256;              // softmax warps 0-7
+constexpr int kTcThreads = kSoftThreads + 32;  // + the MMA-issuing warp
+constexpr int kTcRows = 128;     // candidates per work item = tensor-memory lanes
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait on a tensor-core completion
 
 struct EmTcParams {
@@ -65,10 +67,20 @@ struct EmTcParams {
     double *part_ll;        // [G][C]
     int64_t C;
     int mstep;
+    int G;                  // items per candidate tile (consecutive in the item list)
+    float beta;             // pseudocount
+    float *theta_out;       // [C][stride] M-step result (may be theta_in: rows are
+                            // rewritten only after every item reading them is done)
+    double *ll_out;         // [C]
+    uint32_t *tile_done;    // [n_items / G] finished items per tile, 0 between launches
     int *err;
 };
 
 constexpr int kNT = 64;  // l-mers per tile (N of the score MMA, K of the count MMA)
+// Up to this many sequence groups per candidate tile the last item of a tile
+// folds the groups' partial results itself; beyond it one CTA would serialise
+// too much of that work, and a separate grid-wide kernel does it.
+constexpr int kFoldMaxG = 4;
 
 template <int KP>
 struct TcLayout {
@@ -81,7 +93,7 @@ struct TcLayout {
     static constexpr int OFF_X = OFF_WLO + W_BYTES;
     static constexpr int OFF_PHI = OFF_X + NX * X_BYTES;
     static constexpr int OFF_PLO = OFF_PHI + P_BYTES;
-    static constexpr int SEQ_WORDS = 1024;  // staged packed words of an item (16K bases)
+    static constexpr int SEQ_WORDS = 2048;  // staged packed words of an item (32K bases)
     static constexpr int OFF_SEQ = OFF_PLO + P_BYTES;
     static constexpr int TOTAL = OFF_SEQ + SEQ_WORDS * 4;
     // two score buffers S[2] (kNT columns each) and the count accumulator O (KP)
@@ -112,12 +124,12 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 // first base in the packed input.
 struct TileIt {
     int seq, j0, ns;
-    int64_t base;
+    int base;  // first base of the sequence (inputs hold < 2^31 bases)
     __device__ __forceinline__ void load(const EmInst &in) {
         base = in.seq_off[seq];
-        ns = (int)(in.seq_off[seq + 1] - base) - in.l + 1;
+        ns = in.seq_off[seq + 1] - base - in.l + 1;
     }
-    __device__ __forceinline__ void start(const EmInst &in, int s0) {
+    __device__ __forceinline__ void start(const EmInst &in, int s0, int) {
         seq = s0;
         j0 = 0;
         load(in);
@@ -134,16 +146,17 @@ struct TileIt {
 };
 
 // One-hot tile X[j][p*4+a] = [x_{j0+j+p} = a] of the l-mers of tile `t`:
-// thread (row j, half) writes the 16-byte chunks (two positions each, BF16
-// 1.0 = 0x3F80 in the slot of the base's code) of its half of row j, from one
-// 64-bit window of the packed sequence (staged words when `staged`).
+// thread (row j, part) writes every fourth 16-byte chunk (two positions each,
+// BF16 1.0 = 0x3F80 in the slot of the base's code) of row j, from one 64-bit
+// window of the packed sequence (staged words when `staged`).
 template <int KP>
 __device__ __forceinline__ void build_x(uint8_t *sX, const TileIt &t, int l, const uint32_t *sSeq,
                                         int nw_st, int64_t w_first, bool staged,
                                         const uint32_t *packed, int64_t nwords, int tid) {
-    static_assert(kTcThreads == 2 * kNT, "two threads per row");
+    static_assert(kSoftThreads == 4 * kNT, "four threads per row");
     constexpr int kChunks = KP / 8;
     const int j = tid % kNT, part = tid / kNT;
+    if (part >= kChunks) return;
     const bool row_ok = j < t.ns - t.j0;
     uint64_t win = 0;
     if (row_ok) {
@@ -151,7 +164,7 @@ __device__ __forceinline__ void build_x(uint8_t *sX, const TileIt &t, int l, con
         win = staged ? window64(sSeq, nw_st, b0 - (w_first << 4)) : window64(packed, nwords, b0);
     }
 #pragma unroll
-    for (int kb = part; kb < kChunks; kb += 2) {
+    for (int kb = part; kb < kChunks; kb += 4) {
         uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
         const int p0 = 2 * kb, p1 = 2 * kb + 1;
         if (row_ok && p0 < l) {
@@ -168,33 +181,89 @@ __device__ __forceinline__ void build_x(uint8_t *sX, const TileIt &t, int l, con
     }
 }
 
-// Software pipeline over the tiles i = 0 .. n-1 of an item (one __syncthreads
-// per tile):
-//   - the score MMA of tile i+1 is issued before the softmax of tile i, into
-//     the other score buffer, so the tensor core works while the CUDA cores
-//     compute exponentials;
-//   - the count MMA of tile i is issued after its P is written and runs
-//     during the softmax of tile i+1;
-//   - the one-hot tile of i+2 is built during tile i, into a ring of three
-//     (tiles i and i+1 are still read by issued MMAs).
-// Waits: S(i) before its softmax; the count MMA of i-1 before P(i) overwrites
-// P and before slot (i+2) % 3 = (i-1) % 3 is rebuilt; the count MMA of a
-// sequence's last tile before its O is read.
+// 2^(v - m) for the nv valid entries of a half tile, 0 elsewhere; returns
+// their sum (tree order).
+__device__ __forceinline__ float exp_half(float (&v)[32], float m, int nv) {
+    if (nv == 32) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) v[q] = ex2(v[q] - m);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) v[q] = q < nv ? ex2(v[q] - m) : 0.f;
+    }
+    float part[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) part[q] = v[q] + v[q + 16];
+#pragma unroll
+    for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+        for (int q = 0; q < w; ++q) part[q] += part[q + w];
+    return part[0];
+}
+
+__device__ __forceinline__ float max_half(const float (&v)[32], int nv) {
+    float mx[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) mx[q] = -INFINITY;
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+        if (q < nv) mx[q & 7] = fmaxf(mx[q & 7], v[q]);
+#pragma unroll
+    for (int q = 1; q < 8; ++q) mx[0] = fmaxf(mx[0], mx[q]);
+    return mx[0];
+}
+
+// The CTA has 288 threads.  Warps 0-7 compute the softmax: warps w and w + 4
+// share the tensor-memory lanes 32*(w%4) .. +31 (candidate rows), warp w
+// taking the first 32 l-mers of each tile and warp w + 4 the last 32; the two
+// threads of a row keep one reference maximum m (agreed through shared memory
+// at the first tile of a sequence), their own compensated sums, and each reads
+// and accumulates half of the row's count columns.  Warp 8 issues the MMAs
+// (one elected thread), so issuing never stalls the softmax warps.
+//
+// Pipeline over the tiles j = 0 .. n-1 of an item, linked by mbarriers:
+//   issuer: S(0), S(1); then per j: [P(j) written] O (+)= P X(j);
+//           [X(j+2) built, S buffer of j read] S(j+2) = W X(j+2)^T
+//   softmax, per j: [S(j) ready] read S(j), release its buffer; P = 2^(S-m);
+//           [count MMA of j-1 done] write P(j); build X(j+2) into the slot of
+//           tile j-1; at a sequence end [count MMA of j done] read O.
+// Two score buffers in tensor memory, one P buffer and a ring of three one-hot
+// tiles in shared memory.
+//
+// Reference maximum: P = 2^(S - m) with m = max(exact maximum of the
+// sequence's first tile, top - 100), top = sum_p max_a W the highest score the
+// row can reach.  Every P of the sequence is then <= 2^100, and when the row's
+// score range sum_p (max_a W - min_a W) is <= 200 the sequence's largest P is
+// >= 2^-100, so nothing overflows or leaves the normal FP32 range that
+// matters.  Rows with a wider range (careful mode, CTA-wide) use the exact
+// first-tile maximum and the two threads of a row compare every tile: if a
+// half-tile sum exceeds 2^64 (or is not finite) m is raised to the tile's
+// exact maximum, the row's sums and O are rescaled and the tile recomputed.
 template <int KP>
-__global__ void __launch_bounds__(kTcThreads, 2) em_tc_kernel(const EmTcParams P) {
+__global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(const EmTcParams P) {
     using LY = TcLayout<KP>;
     constexpr int NT = kNT;
+    constexpr int KH = KP / 2;  // count columns per thread of a row
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mbS[2], mbO, mbEnd;
+    __shared__ __align__(8) uint64_t mbSfull[2], mbSfree[2], mbXfull[LY::NX], mbPfull, mbO, mbEnd;
     __shared__ uint32_t tmem_slot;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    __shared__ float sh_x[2][2][kTcRows];  // [slot][half][row] values exchanged by a row's two threads
+    __shared__ bool s_last;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool issuer = warp == kSoftThreads / 32;
+    const int quad = warp & 3, half = (warp >> 2) & 1;
+    const int row = 32 * quad + lane;
     uint8_t *sWhi = smem + LY::OFF_WHI, *sWlo = smem + LY::OFF_WLO, *sX = smem + LY::OFF_X;
     uint8_t *sPhi = smem + LY::OFF_PHI, *sPlo = smem + LY::OFF_PLO;
     uint32_t *sSeq = reinterpret_cast<uint32_t *>(smem + LY::OFF_SEQ);
 
     if (tid == 0) {
-        tc::mbar_init(&mbS[0], 1);
-        tc::mbar_init(&mbS[1], 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&mbSfull[b], 1);
+            tc::mbar_init(&mbSfree[b], kSoftThreads);
+        }
+        for (int s = 0; s < LY::NX; ++s) tc::mbar_init(&mbXfull[s], kSoftThreads);
+        tc::mbar_init(&mbPfull, kSoftThreads);
         tc::mbar_init(&mbO, 1);
         tc::mbar_init(&mbEnd, 1);
         tc::mbar_fence_init();
@@ -208,22 +277,29 @@ __global__ void __launch_bounds__(kTcThreads, 2) em_tc_kernel(const EmTcParams P
     tc::fence_after_sync();
     const uint32_t tm = tmem_slot;
     const uint32_t tO = tm + 2 * NT;
-    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-    const uint32_t aWhi = tc::smem_addr(sWhi), aWlo = tc::smem_addr(sWlo);
-    const uint32_t aX = tc::smem_addr(sX), aPhi = tc::smem_addr(sPhi), aPlo = tc::smem_addr(sPlo);
+    const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
     constexpr uint32_t IDESC_S = tc::idesc_bf16(128, NT);
-    uint32_t phS = 0u;            // bit b: parity of the next completion of score buffer b
-    uint32_t o_waited = 0;        // count MMAs of this CTA known complete (in issue order)
-    uint32_t o_base = 0;          // count MMAs issued before the current item
+    constexpr uint64_t kXSlot = LY::X_BYTES >> 4;
+
+    // phase trackers (each barrier completes in a fixed order; see above)
+    uint32_t phSfull = 0u, phSfree = 0u, phX = 0u, phP = 0u;
+    uint32_t o_waited = 0, o_base = 0;  // count MMAs of this CTA known complete / before this item
+    uint32_t xcnt = 0;                  // exchanges done (slot = xcnt & 1)
     bool ok = true, abort = false;
 
-    // waits until the first `target` count MMAs of the current item have
-    // completed; completion j (0-based, over the CTA's life) has parity j & 1
-    auto wait_o = [&](uint32_t target) {
+    auto wait_o = [&](uint32_t target) {  // first `target` count MMAs of the item complete
         while (ok && o_waited < o_base + target) {
             ok = tc::mbar_wait(&mbO, o_waited & 1u, kWaitNs);
             ++o_waited;
         }
+    };
+    // the other thread of this row's value (both call it together)
+    auto exchange = [&](float mine) {
+        const int s = xcnt & 1;
+        ++xcnt;
+        sh_x[s][half][row] = mine;
+        tc::named_bar(1 + quad, 64);
+        return sh_x[s][half ^ 1][row];
     };
 
     for (int it = blockIdx.x; it < P.n_items && !abort; it += gridDim.x) {
@@ -232,266 +308,302 @@ __global__ void __launch_bounds__(kTcThreads, 2) em_tc_kernel(const EmTcParams P
         const int l = in.l, L4 = 4 * l;
         const int kq = (L4 + 15) / 16;  // K steps of the score MMA = N / 16 of the count MMA
         const uint32_t idesc_o = tc::idesc_bf16(128, 16 * kq, true);
-        const int64_t c = item.c0 + tid;
-        const bool valid = tid < item.nc;
-
-        __syncthreads();  // the previous item's MMAs and reads are complete
-        // W_c = log2 theta_c - log2 bg in FP32, split into BF16 hi + lo (row tid)
-        float lbg[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) lbg[a] = log2f((float)in.bg[a]);
-        for (int k8 = 0; k8 < KP; k8 += 8) {
-            uint32_t hi[4], lo[4];
-#pragma unroll
-            for (int q = 0; q < 8; q += 2) {
-                float h2[2], l2[2];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int k = k8 + q + u;
-                    float w = 0.f;
-                    if (valid && k < L4) w = log2f(__ldg(P.theta_in + c * P.stride + k)) - lbg[k & 3];
-                    const float h = __bfloat162float(__float2bfloat16_rn(w));
-                    h2[u] = h;
-                    l2[u] = w - h;
-                }
-                hi[q / 2] = pack_bf16(h2[0], h2[1]);
-                lo[q / 2] = pack_bf16(l2[0], l2[1]);
-            }
-            *reinterpret_cast<uint4 *>(sWhi + tc::kmajor_off(tid, k8, KP)) =
-                make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<uint4 *>(sWlo + tc::kmajor_off(tid, k8, KP)) =
-                make_uint4(lo[0], lo[1], lo[2], lo[3]);
-        }
-        // the packed words of the item's sequences (+2 for the 64-bit windows)
+        const int64_t c = item.c0 + row;
+        const bool valid = row < item.nc;
+        const int n = item.n_tiles;
         const int64_t b_lo = in.seq_off[item.seq_lo], b_hi = in.seq_off[item.seq_hi];
         const int64_t w_first = b_lo >> 4;
         const int nw_st = (int)(((b_hi + 15) >> 4) - w_first) + 2;
         const bool staged = nw_st <= LY::SEQ_WORDS;
-        if (staged)
-            for (int w = tid; w < nw_st; w += kTcThreads)
-                sSeq[w] = (w_first + w) < P.nwords ? __ldg(P.packed + w_first + w) : 0u;
-        // number of tiles of the item
-        int n = 0;
-        for (int s = item.seq_lo; s < item.seq_hi; ++s)
-            n += ((int)(in.seq_off[s + 1] - in.seq_off[s]) - l + 1 + NT - 1) / NT;
-        __syncthreads();  // staged words visible to build_x
 
-        TileIt tb, tcur;
-        tb.start(in, item.seq_lo);
-        tcur.start(in, item.seq_lo);
-        build_x<KP>(sX, tb, l, sSeq, nw_st, w_first, staged, P.packed, P.nwords, tid);
-        tb.advance(in, item.seq_hi);
-        if (n > 1) {
-            build_x<KP>(sX + LY::X_BYTES, tb, l, sSeq, nw_st, w_first, staged, P.packed, P.nwords, tid);
+        __syncthreads();  // the previous item's MMAs and reads are complete
+        float span = 0.f;   // sum over this thread's positions of max_a W - min_a W
+        float wmax = 0.f;   // sum over this thread's positions of max_a W
+        if (!issuer) {
+            // W_c = log2 theta_c - log2 bg in FP32, split into BF16 hi + lo: the
+            // thread of half h writes columns [h*KP/2, (h+1)*KP/2) of its row
+            float lbg[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) lbg[a] = log2f((float)in.bg[a]);
+            for (int k8 = half * KH; k8 < (half + 1) * KH; k8 += 8) {
+                float w[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int k = k8 + q;
+                    w[q] = (valid && k < L4) ? log2f(__ldcg(P.theta_in + c * P.stride + k)) - lbg[q & 3]
+                                             : 0.f;
+                }
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    const float hi4 = fmaxf(fmaxf(w[4 * g], w[4 * g + 1]), fmaxf(w[4 * g + 2], w[4 * g + 3]));
+                    wmax += hi4;
+                    span += hi4 - fminf(fminf(w[4 * g], w[4 * g + 1]), fminf(w[4 * g + 2], w[4 * g + 3]));
+                }
+                uint32_t hi[4], lo[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t h = pack_bf16(w[2 * q], w[2 * q + 1]);
+                    hi[q] = h;
+                    lo[q] = pack_bf16(w[2 * q] - __uint_as_float(h << 16),
+                                      w[2 * q + 1] - __uint_as_float(h & 0xFFFF0000u));
+                }
+                *reinterpret_cast<uint4 *>(sWhi + tc::kmajor_off(row, k8, KP)) =
+                    make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<uint4 *>(sWlo + tc::kmajor_off(row, k8, KP)) =
+                    make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            }
+            if (staged)
+                for (int w = tid; w < nw_st; w += kSoftThreads)
+                    sSeq[w] = (w_first + w) < P.nwords ? __ldg(P.packed + w_first + w) : 0u;
+        }
+        // per row: highest possible score and score range (both halves)
+        float row_span = 0.f, row_top = 0.f;
+        if (!issuer) {
+            row_span = span + exchange(span);
+            row_top = wmax + exchange(wmax);
+        }
+        const bool careful = __syncthreads_or(row_span > 200.f);
+        TileIt tb;
+        tb.start(in, item.seq_lo, item.seq_hi);
+        if (!issuer) {
+            build_x<KP>(sX, tb, l, sSeq, nw_st, w_first, staged, P.packed, P.nwords, tid);
             tb.advance(in, item.seq_hi);
-        }
-        tc::fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after_sync();
-            for (int s = 0; s < kq; ++s)
-                tc::mma_bf16(tm, tc::sdesc(aWhi + 256 * s, 128, KP * 16),
-                             tc::sdesc(aX + 256 * s, 128, KP * 16), IDESC_S, s > 0);
-            for (int s = 0; s < kq; ++s)
-                tc::mma_bf16(tm, tc::sdesc(aWlo + 256 * s, 128, KP * 16),
-                             tc::sdesc(aX + 256 * s, 128, KP * 16), IDESC_S, 1);
-            tc::mma_commit(&mbS[0]);
-        }
-
-        float tot[KP];  // this item's normalised counts of candidate c
-#pragma unroll
-        for (int q = 0; q < KP; ++q) tot[q] = 0.f;
-        double ll = 0.0;
-        float m = -INFINITY, Ssum = 0.f, Scmp = 0.f;
-        bool first = true;
-        o_base = o_waited;  // every count MMA of earlier items was waited for
-
-        for (int i = 0; i < n; ++i) {
-            const int b = i & 1;
-            const uint32_t tS = tm + NT * b;
-            // score MMA of tile i+1 (its one-hot tile and score buffer are free)
-            if (tid == 0 && i + 1 < n) {
-                tc::fence_after_sync();
-                const uint32_t xn = aX + ((i + 1) % 3) * LY::X_BYTES;
-                const uint32_t tSn = tm + NT * (b ^ 1);
-                for (int s = 0; s < kq; ++s)
-                    tc::mma_bf16(tSn, tc::sdesc(aWhi + 256 * s, 128, KP * 16),
-                                 tc::sdesc(xn + 256 * s, 128, KP * 16), IDESC_S, s > 0);
-                for (int s = 0; s < kq; ++s)
-                    tc::mma_bf16(tSn, tc::sdesc(aWlo + 256 * s, 128, KP * 16),
-                                 tc::sdesc(xn + 256 * s, 128, KP * 16), IDESC_S, 1);
-                tc::mma_commit(&mbS[b ^ 1]);
-            }
-            if (ok) ok = tc::mbar_wait(&mbS[b], (phS >> b) & 1u, kWaitNs);
-            phS ^= 1u << b;
-            tc::fence_after_sync();
-
-            // P = 2^(S - m) with m a reference near the row maximum: the exact
-            // maximum of the first tile of a sequence, then kept until a tile
-            // holds a score more than 20 above it (P > 2^20); only then is the
-            // maximum recomputed, the row's O and sum rescaled and the tile's P
-            // recomputed.  The tile is summed as a tree and added to the running
-            // sum with compensation.  Tensor-memory accesses are .sync.aligned,
-            // so every decision that guards them is taken per warp.
-            const int nvalid = min(NT, tcur.ns - tcur.j0);
-            const bool full = nvalid == NT;  // only a sequence's last tile is ragged
-            float v[NT];
-            tc::tmem_ld64(tS + lane_base, v);
-            if (first) {
-                float mx[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) mx[q] = -INFINITY;
-#pragma unroll
-                for (int q = 0; q < NT; ++q)
-                    if (full || q < nvalid) mx[q & 7] = fmaxf(mx[q & 7], v[q]);
-#pragma unroll
-                for (int q = 1; q < 8; ++q) mx[0] = fmaxf(mx[0], mx[q]);
-                m = mx[0];
-            }
-            float add;
-            bool big;
-            {
-#pragma unroll
-                for (int q = 0; q < NT; ++q) v[q] = (full || q < nvalid) ? ex2(v[q] - m) : 0.f;
-                float part[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) part[q] = (v[q] + v[q + 16]) + (v[q + 32] + v[q + 48]);
-#pragma unroll
-                for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-                    for (int q = 0; q < w; ++q) part[q] += part[q + w];
-                add = part[0];
-                big = !(add <= 1048576.f);  // some score > m + 20 (or a non-finite sum)
-            }
-            if (__any_sync(0xffffffffu, big)) {
-                // rare: re-read the scores, move the reference to the exact maximum
-                tc::tmem_ld64(tS + lane_base, v);
-                float tmax = -INFINITY;
-#pragma unroll
-                for (int q = 0; q < NT; ++q)
-                    if (full || q < nvalid) tmax = fmaxf(tmax, v[q]);
-                const bool grow = tmax > m;
-                const float sc = grow ? ex2(m - tmax) : 1.f;
-                if (grow) {
-                    Ssum *= sc;
-                    Scmp *= sc;
-                    m = tmax;
-                }
-                if (P.mstep && !first && __any_sync(0xffffffffu, grow)) {
-                    wait_o((uint32_t)i);  // O holds every count MMA issued so far
-                    tc::fence_after_sync();
-#pragma unroll
-                    for (int c0 = 0; c0 < KP; c0 += 16) {
-                        if (c0 < 16 * kq) {
-                            float o[16];
-                            tc::tmem_ld16(tO + lane_base + c0, o);
-#pragma unroll
-                            for (int q = 0; q < 16; ++q) o[q] *= sc;
-                            tc::tmem_st16(tO + lane_base + c0, o);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < NT; ++q) v[q] = (full || q < nvalid) ? ex2(v[q] - m) : 0.f;
-                float part[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) part[q] = (v[q] + v[q + 16]) + (v[q + 32] + v[q + 48]);
-#pragma unroll
-                for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-                    for (int q = 0; q < w; ++q) part[q] += part[q + w];
-                add = part[0];
-            }
-            kahan(Ssum, Scmp, add);
-
-            if (P.mstep) {
-                wait_o((uint32_t)i);  // the count MMA of tile i-1 has read P and X(i-1)
-#pragma unroll
-                for (int g = 0; g < NT / 8; ++g) {
-                    uint32_t hi[4], lo[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float a0 = v[8 * g + 2 * q], a1 = v[8 * g + 2 * q + 1];
-                        const uint32_t h = pack_bf16(a0, a1);
-                        hi[q] = h;
-                        lo[q] = pack_bf16(a0 - __uint_as_float(h << 16),
-                                          a1 - __uint_as_float(h & 0xFFFF0000u));
-                    }
-                    *reinterpret_cast<uint4 *>(sPhi + tc::kmajor_off(tid, 8 * g, NT)) =
-                        make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                    *reinterpret_cast<uint4 *>(sPlo + tc::kmajor_off(tid, 8 * g, NT)) =
-                        make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                }
-            }
-            // one-hot tile of i+2 into the slot of tile i-1
-            if (i + 2 < n) {
-                build_x<KP>(sX + ((i + 2) % 3) * LY::X_BYTES, tb, l, sSeq, nw_st, w_first, staged,
-                            P.packed, P.nwords, tid);
+            if (n > 1) {
+                build_x<KP>(sX + LY::X_BYTES, tb, l, sSeq, nw_st, w_first, staged, P.packed,
+                            P.nwords, tid);
                 tb.advance(in, item.seq_hi);
             }
-            tc::fence_before_sync();
             tc::fence_async_smem();
-            abort = __syncthreads_or(!ok);
-            if (abort) break;
-            const bool seq_end = tcur.last();
-            if (P.mstep) {
-                // O (+)= P_hi X + P_lo X, X read in MN-major form
-                if (tid == 0) {
-                    tc::fence_after_sync();
-                    const uint32_t xc = aX + (i % 3) * LY::X_BYTES;
-#pragma unroll
-                    for (int s = 0; s < NT / 16; ++s)
-                        tc::mma_bf16(tO, tc::sdesc(aPhi + 256 * s, 128, NT * 16),
-                                     tc::sdesc(xc + s * 2 * KP * 16, KP * 16, 128), idesc_o,
-                                     (s > 0 || !first) ? 1u : 0u);
-#pragma unroll
-                    for (int s = 0; s < NT / 16; ++s)
-                        tc::mma_bf16(tO, tc::sdesc(aPlo + 256 * s, 128, NT * 16),
-                                     tc::sdesc(xc + s * 2 * KP * 16, KP * 16, 128), idesc_o, 1u);
-                    tc::mma_commit(&mbO);
-                }
-            }
-            first = false;
-            if (seq_end) {
-                const float Sf = Ssum - Scmp;
-                ll += (double)((m + log2f(Sf)) * 0.69314718f - logf((float)tcur.ns));
-                if (P.mstep) {
-                    wait_o((uint32_t)i + 1);
-                    tc::fence_after_sync();
-                    const float inv = 1.f / Sf;
-#pragma unroll
-                    for (int c0 = 0; c0 < KP; c0 += 16) {
-                        if (c0 < 16 * kq) {
-                            float o[16];
-                            tc::tmem_ld16(tO + lane_base + c0, o);
-#pragma unroll
-                            for (int q = 0; q < 16; ++q) tot[c0 + q] += o[q] * inv;
-                        }
-                    }
-                    tc::fence_before_sync();  // O is read before the next count MMA restarts it
-                }
-                m = -INFINITY;
-                Ssum = 0.f;
-                Scmp = 0.f;
-                first = true;
-            }
-            tcur.advance(in, item.seq_hi);
         }
-        abort = __syncthreads_or(!ok || abort);
-        if (abort) break;
-        if (valid) {
-            P.part_ll[(int64_t)item.g * P.C + c] = ll;
-            if (P.mstep) {
-                double *dst = P.part_acc + ((int64_t)item.g * P.C + c) * P.stride;
+        __syncthreads();  // W and the first two one-hot tiles are visible to the issuer
+
+        if (issuer) {
+            if (lane == 0) {
+                tc::fence_after_sync();
+                // operand descriptors; a start address advances by adding (bytes >> 4)
+                const uint64_t dWhi = tc::sdesc(tc::smem_addr(sWhi), 128, KP * 16);
+                const uint64_t dWlo = tc::sdesc(tc::smem_addr(sWlo), 128, KP * 16);
+                const uint64_t dXk = tc::sdesc(tc::smem_addr(sX), 128, KP * 16);   // K-major
+                const uint64_t dXmn = tc::sdesc(tc::smem_addr(sX), KP * 16, 128);  // MN-major
+                const uint64_t dPhi = tc::sdesc(tc::smem_addr(sPhi), 128, NT * 16);
+                const uint64_t dPlo = tc::sdesc(tc::smem_addr(sPlo), 128, NT * 16);
+                auto issue_scores = [&](uint32_t d, uint32_t slot) {
+                    const uint64_t dx = dXk + slot * kXSlot;
 #pragma unroll
-                for (int q = 0; q < KP; ++q)
-                    if (q < L4) dst[q] = (double)tot[q];
+                    for (int s = 0; s < KP / 16; ++s)
+                        if (s < kq) tc::mma_bf16(d, dWhi + 16 * s, dx + 16 * s, IDESC_S, s > 0);
+#pragma unroll
+                    for (int s = 0; s < KP / 16; ++s)
+                        if (s < kq) tc::mma_bf16(d, dWlo + 16 * s, dx + 16 * s, IDESC_S, 1u);
+                };
+                issue_scores(tm, 0);
+                tc::mma_commit(&mbSfull[0]);
+                if (n > 1) {
+                    issue_scores(tm + NT, 1);
+                    tc::mma_commit(&mbSfull[1]);
+                }
+                TileIt ti;
+                ti.start(in, item.seq_lo, item.seq_hi);
+                for (int j = 0; j < n && ok; ++j) {
+                    if (P.mstep) {
+                        ok = tc::mbar_wait(&mbPfull, phP, kWaitNs);
+                        phP ^= 1u;
+                        tc::fence_after_sync();
+                        const uint64_t dx = dXmn + (uint32_t)(j % 3) * kXSlot;
+                        const uint32_t acc0 = ti.j0 > 0 ? 1u : 0u;  // O restarts with a sequence
+#pragma unroll
+                        for (int s = 0; s < NT / 16; ++s)
+                            tc::mma_bf16(tO, dPhi + 16 * s, dx + 2 * KP * s, idesc_o, s > 0 ? 1u : acc0);
+#pragma unroll
+                        for (int s = 0; s < NT / 16; ++s)
+                            tc::mma_bf16(tO, dPlo + 16 * s, dx + 2 * KP * s, idesc_o, 1u);
+                        tc::mma_commit(&mbO);
+                    }
+                    if (j + 2 < n && ok) {
+                        const uint32_t xs = (uint32_t)((j + 2) % 3), b = (uint32_t)(j & 1);
+                        ok = tc::mbar_wait(&mbXfull[xs], (phX >> xs) & 1u, kWaitNs);
+                        phX ^= 1u << xs;
+                        if (ok) ok = tc::mbar_wait(&mbSfree[b], (phSfree >> b) & 1u, kWaitNs);
+                        phSfree ^= 1u << b;
+                        tc::fence_after_sync();
+                        issue_scores(tm + NT * b, xs);
+                        tc::mma_commit(&mbSfull[b]);
+                    }
+                    ti.advance(in, item.seq_hi);
+                }
             }
+        } else {
+            float tot[KH];  // this item's normalised counts of candidate c, columns of this half
+#pragma unroll
+            for (int q = 0; q < KH; ++q) tot[q] = 0.f;
+            double ll = 0.0;
+            float m = -INFINITY, Ssum = 0.f, Scmp = 0.f;
+            bool first = true;
+            o_base = o_waited;  // every count MMA of earlier items was waited for
+            TileIt tcur;
+            tcur.start(in, item.seq_lo, item.seq_hi);
+
+            for (int i = 0; i < n; ++i) {
+                const uint32_t b = (uint32_t)(i & 1);
+                const uint32_t tS = tm + NT * b + 32 * half + lane_base;
+                if (ok) ok = tc::mbar_wait(&mbSfull[b], (phSfull >> b) & 1u, kWaitNs);
+                phSfull ^= 1u << b;
+                tc::fence_after_sync();
+
+                const int nvalid = min(NT, tcur.ns - tcur.j0);
+                const int nv = max(0, min(32, nvalid - 32 * half));  // valid l-mers of this half
+                float v[32];
+                tc::tmem_ld32(tS, v);
+                if (first) {
+                    // the first tile's maximum, raised to at least top - 100 so that
+                    // no later score of the sequence (<= top) gives P above 2^100
+                    const float mh = max_half(v, nv);
+                    m = fmaxf(mh, exchange(mh));
+                    if (!careful) m = fmaxf(m, row_top - 100.f);
+                }
+                const float s0 = Ssum, c0s = Scmp;
+                float add = exp_half(v, m, nv);
+                if (careful) {
+                    const float bigf = !(add <= 18446744073709551616.f) ? 1.f : 0.f;  // 2^64
+                    // both warps of the lane group take the same branch (named barriers)
+                    if (__any_sync(0xffffffffu, fmaxf(bigf, exchange(bigf)) > 0.f)) {
+                        // redo the tile with m raised to its exact maximum
+                        tc::tmem_ld32(tS, v);
+                        const float mh = max_half(v, nv);
+                        const float tmax = fmaxf(fmaxf(mh, exchange(mh)), m);
+                        const float sc = ex2(m - tmax);
+                        Ssum = s0 * sc;
+                        Scmp = c0s * sc;
+                        m = tmax;
+                        if (P.mstep && !first) {
+                            wait_o((uint32_t)i);  // O holds every count MMA issued so far
+                            tc::fence_after_sync();
+#pragma unroll
+                            for (int c8 = 0; c8 < KH; c8 += 8) {
+                                float o[8];
+                                tc::tmem_ld8(tO + lane_base + half * KH + c8, o);
+#pragma unroll
+                                for (int q = 0; q < 8; ++q) o[q] *= sc;
+                                tc::tmem_st8(tO + lane_base + half * KH + c8, o);
+                            }
+                        }
+                        add = exp_half(v, m, nv);
+                    }
+                }
+                kahan(Ssum, Scmp, add);
+                tc::fence_before_sync();
+                if (i + 2 < n) tc::mbar_arrive(&mbSfree[b]);  // the issuer may overwrite S(i)
+
+                if (P.mstep) {
+                    wait_o((uint32_t)i);  // the count MMA of tile i-1 has read P and X(i-1)
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        uint32_t hi[4], lo[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float a0 = v[8 * g + 2 * q], a1 = v[8 * g + 2 * q + 1];
+                            const uint32_t h = pack_bf16(a0, a1);
+                            hi[q] = h;
+                            lo[q] = pack_bf16(a0 - __uint_as_float(h << 16),
+                                              a1 - __uint_as_float(h & 0xFFFF0000u));
+                        }
+                        *reinterpret_cast<uint4 *>(sPhi + tc::kmajor_off(row, 32 * half + 8 * g, NT)) =
+                            make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                        *reinterpret_cast<uint4 *>(sPlo + tc::kmajor_off(row, 32 * half + 8 * g, NT)) =
+                            make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                    }
+                    tc::fence_async_smem();
+                    tc::fence_before_sync();
+                    tc::mbar_arrive(&mbPfull);
+                }
+                // one-hot tile of i+2 into the slot of tile i-1 (its MMAs are complete)
+                if (i + 2 < n) {
+                    build_x<KP>(sX + ((i + 2) % 3) * LY::X_BYTES, tb, l, sSeq, nw_st, w_first,
+                                staged, P.packed, P.nwords, tid);
+                    tb.advance(in, item.seq_hi);
+                    tc::fence_async_smem();
+                    tc::mbar_arrive(&mbXfull[(i + 2) % 3]);
+                }
+                first = false;
+                if (tcur.last()) {
+                    const float Sh = Ssum - Scmp;
+                    const float Sf = Sh + exchange(Sh);
+                    ll += (double)((m + log2f(Sf)) * 0.69314718f - logf((float)tcur.ns));
+                    if (P.mstep) {
+                        wait_o((uint32_t)i + 1);
+                        tc::fence_after_sync();
+                        const float inv = 1.f / Sf;
+#pragma unroll
+                        for (int c8 = 0; c8 < KH; c8 += 8) {
+                            float o[8];
+                            tc::tmem_ld8(tO + lane_base + half * KH + c8, o);
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) tot[c8 + q] += o[q] * inv;
+                        }
+                        tc::fence_before_sync();
+                    }
+                    m = -INFINITY;
+                    Ssum = 0.f;
+                    Scmp = 0.f;
+                    first = true;
+                }
+                tcur.advance(in, item.seq_hi);
+            }
+            if (ok && valid && P.G == 1) {
+                // the item covers every sequence: final values directly
+                if (half == 0) P.ll_out[c] = ll;
+                if (P.mstep) {
+                    const double den = (double)in.t + 4.0 * (double)P.beta;
+                    float *dst = P.theta_out + c * P.stride + half * KH;
+#pragma unroll
+                    for (int q = 0; q < KH; ++q)
+                        if (half * KH + q < L4)
+                            dst[q] = (float)(((double)tot[q] + (double)P.beta) / den);
+                }
+            } else if (ok && valid) {
+                if (half == 0) P.part_ll[(int64_t)item.g * P.C + c] = ll;
+                if (P.mstep) {
+                    double *dst = P.part_acc + ((int64_t)item.g * P.C + c) * P.stride + half * KH;
+#pragma unroll
+                    for (int q = 0; q < KH; ++q)
+                        if (half * KH + q < L4) dst[q] = (double)tot[q];
+                }
+            }
+        }
+        const bool fold = P.G > 1 && P.G <= kFoldMaxG;
+        if (fold) __threadfence();  // this thread's partial results are visible device-wide
+        abort = __syncthreads_or(!ok);
+        if (abort) break;
+        // the last of the tile's G items folds the partial results in group
+        // order: theta = (sum_g counts + pseudocount) / (t + 4 pseudocount),
+        // LL = sum_g LL_g (larger G: em_tc_reduce_kernel after the launch)
+        if (fold) {
+            if (tid == 0) s_last = atomicAdd(&P.tile_done[it / P.G], 1u) == (uint32_t)(P.G - 1);
+            __syncthreads();
+        }
+        if (fold && s_last) {
+            __threadfence();
+            const int width = P.mstep ? L4 : 0;
+            const double den = (double)in.t + 4.0 * (double)P.beta;
+            for (int e = tid; e < item.nc * (width + 1); e += kTcThreads) {
+                const int cc = e / (width + 1), q = e - cc * (width + 1);
+                const int64_t cg = item.c0 + cc;
+                double acc = 0.0;
+                if (q < width) {
+                    for (int g = 0; g < P.G; ++g)
+                        acc += __ldcg(P.part_acc + ((int64_t)g * P.C + cg) * P.stride + q);
+                    P.theta_out[cg * P.stride + q] = (float)((acc + (double)P.beta) / den);
+                } else {
+                    for (int g = 0; g < P.G; ++g) acc += __ldcg(P.part_ll + (int64_t)g * P.C + cg);
+                    P.ll_out[cg] = acc;
+                }
+            }
+            if (tid == 0) P.tile_done[it / P.G] = 0u;  // ready for the next launch
         }
     }
     if (abort && tid == 0) atomicExch(P.err, 1);
     // every MMA this CTA issued has completed (bounded) before its memory is freed
-    if (tid == 0) tc::mma_commit(&mbEnd);
+    if (issuer && lane == 0) tc::mma_commit(&mbEnd);
     tc::mbar_wait(&mbEnd, 0u, kWaitNs);
     tc::fence_before_sync();
     __syncthreads();
@@ -502,7 +614,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) em_tc_kernel(const EmTcParams P
 }
 
 // M-step theta = (sum_g counts + pseudocount) / (t + 4 pseudocount) and the
-// log-likelihood sum over the G sequence groups, in group order.
+// log-likelihood sum over the G sequence groups, in group order (used when G
+// is above kFoldMaxG).
 __global__ void em_tc_reduce_kernel(const double *__restrict__ part_acc,
                                     const double *__restrict__ part_ll, int G, int64_t C,
                                     int stride, const EmInst *__restrict__ inst, int n_inst,
@@ -546,9 +659,19 @@ int launch_tc(const EmTcParams &P, int grid, cudaStream_t st) {
 template <int KP>
 int ctas_per_sm_kp() {
     using LY = TcLayout<KP>;
-    const int by_smem = 228 * 1024 / (LY::TOTAL + 1024 + 128);
     const int by_tmem = 512 / (int)LY::TMEM_COLS;
-    return std::max(1, std::min(by_smem, by_tmem));
+    // shared memory: 228 KB per SM, 1 KB reserved per CTA, plus the static part
+    int by_smem = 1, by_regs = 1;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, em_tc_kernel<KP>) == cudaSuccess) {
+        by_smem = 228 * 1024 / (LY::TOTAL + (int)fa.sharedSizeBytes + 1024);
+        // registers are granted per pair of warps
+        const int threads = (kTcThreads + 63) / 64 * 64;
+        by_regs = 65536 / std::max(1, fa.numRegs * threads);
+    } else {
+        (void)cudaGetLastError();
+    }
+    return std::max(1, std::min(std::min(by_smem, by_regs), by_tmem));
 }
 
 int ctas_per_sm(int kp) {
@@ -580,18 +703,19 @@ int dispatch(int kp, const EmTcParams &P, int grid, cudaStream_t st) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Work plan and autotuning.  A schedule is (ctas, g_target): CTAs per SM of
-// the persistent grid (<= what shared memory and registers allow) and how
-// many work items per CTA slot the sequence-group split aims for when there
-// are few candidate tiles.  The first search of each shape class times one
-// E-step launch of every candidate schedule on its own data and keeps the
-// fastest (per process); PROJ_AUTOTUNE=0 turns this off (default schedule).
+// Work plan and autotuning.  A schedule is (ctas, waves): CTAs per SM of the
+// persistent grid (<= what shared memory, registers and tensor memory allow)
+// and, when there are fewer candidate tiles than CTA slots, how many rounds of
+// the slots the sequence-group split fills.  The first search of each shape
+// class times one M-step launch of every candidate schedule on its own data
+// and keeps the fastest (per process); PROJ_AUTOTUNE=0 turns this off (default
+// schedule) and PROJ_EM_SCHED="ctas,waves" forces one.
 // ---------------------------------------------------------------------------
 namespace {
 
-struct Sched { int ctas, g_target; };
-const Sched kScheds[] = {{2, 2}, {2, 1}, {2, 4}, {1, 2}, {1, 4}, {2, 8}};
-constexpr Sched kDefaultSched = {2, 2};
+struct Sched { int ctas, waves; };
+const Sched kScheds[] = {{2, 1}, {2, 2}, {2, 3}, {2, 4}};
+constexpr Sched kDefaultSched = {2, 1};
 
 std::mutex g_tune_mu;
 std::map<uint64_t, Sched> g_tuned;
@@ -607,33 +731,37 @@ uint64_t shape_key(int kp, int64_t C, int tmin, int64_t lmers) {
 }  // namespace
 
 int em_tc_plan(const std::vector<EmInstHost> &insts, std::vector<EmItem> &items, int &G,
-               int ctas, int g_target) {
-    // split each instance's candidates into tiles of 128; when there are too
-    // few tiles for g_target items per CTA slot, split the sequences into G groups
+               int ctas, int waves) {
+    // split each instance's candidates into tiles of 128; when there are fewer
+    // tiles than CTA slots, split the sequences into G groups so that the items
+    // fill `waves` rounds of the slots without a partial round
     int kp = 16;
     int64_t tiles = 0;
     for (const EmInstHost &h : insts) {
         kp = std::max(kp, 16 * ((4 * h.l + 15) / 16));
-        tiles += (h.C + kTcThreads - 1) / kTcThreads;
+        tiles += (h.C + kTcRows - 1) / kTcRows;
     }
     const int64_t slots = (int64_t)sm_count() * std::min(ctas, ctas_per_sm(kp));
     int tmin = 1 << 30;
     for (const EmInstHost &h : insts) tmin = std::min(tmin, h.t);
     G = 1;
-    if (tiles > 0 && tiles < g_target * slots)
-        G = (int)std::min<int64_t>(std::max(1, tmin), (g_target * slots + tiles - 1) / tiles);
+    if (tiles > 0 && tiles < slots)
+        G = (int)std::min<int64_t>(std::max(1, tmin), std::max<int64_t>(1, waves * slots / tiles));
     items.clear();
     for (size_t ii = 0; ii < insts.size(); ++ii) {
         const EmInstHost &h = insts[ii];
-        for (int64_t c0 = 0; c0 < h.C; c0 += kTcThreads)
+        for (int64_t c0 = 0; c0 < h.C; c0 += kTcRows)
             for (int g = 0; g < G; ++g) {
                 EmItem it;
                 it.c0 = h.cand_begin + c0;
-                it.nc = (int)std::min<int64_t>(kTcThreads, h.C - c0);
+                it.nc = (int)std::min<int64_t>(kTcRows, h.C - c0);
                 it.inst = (int)ii;
                 it.seq_lo = (int)((int64_t)h.t * g / G);
                 it.seq_hi = (int)((int64_t)h.t * (g + 1) / G);
                 it.g = g;
+                it.n_tiles = 0;
+                for (int q = it.seq_lo; q < it.seq_hi; ++q)
+                    it.n_tiles += (h.seq_off[q + 1] - h.seq_off[q] - h.l + 1 + 63) / 64;
                 items.push_back(it);
             }
     }
@@ -671,7 +799,7 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
     }
     const char *env = getenv("PROJ_AUTOTUNE");
     bool tune = !known && !(env && env[0] == '0');
-    // PROJ_EM_SCHED="ctas,g_target" forces one schedule (no tuning, no cache)
+    // PROJ_EM_SCHED="ctas,waves" forces one schedule (no tuning, no cache)
     if (const char *fs = getenv("PROJ_EM_SCHED")) {
         int c = 0, g = 0;
         if (sscanf(fs, "%d,%d", &c, &g) == 2 && c >= 1 && c <= 3 && g >= 1 && g <= 8) {
@@ -685,25 +813,38 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
     std::vector<EmItem> items;
     for (const Sched &sc : kScheds) {
         int G = 1;
-        em_tc_plan(insts, items, G, sc.ctas, sc.g_target);
+        em_tc_plan(insts, items, G, sc.ctas, sc.waves);
+        Gmax = std::max(Gmax, G);
+    }
+    {
+        int G = 1;
+        em_tc_plan(insts, items, G, sched.ctas, sched.waves);
         Gmax = std::max(Gmax, G);
     }
     PROJ_TRY(run.part.alloc((size_t)Gmax * C * (stride + 1) * sizeof(double), st));
     PROJ_TRY(run.tmp.alloc((size_t)C * stride * sizeof(float), st));
     PROJ_TRY(run.flag.alloc(sizeof(int), st));
     PROJ_CUDA_TRY(cudaMemsetAsync(run.flag.as<int>(), 0, sizeof(int), st));
+    int64_t n_tiles = 0;  // candidate tiles (the same for every schedule)
+    for (const EmInstHost &h : insts) n_tiles += (h.C + kTcRows - 1) / kTcRows;
+    PROJ_TRY(run.tiles.alloc((size_t)std::max<int64_t>(1, n_tiles) * sizeof(uint32_t), st));
+    PROJ_CUDA_TRY(cudaMemsetAsync(run.tiles.as<uint32_t>(), 0,
+                                  (size_t)std::max<int64_t>(1, n_tiles) * sizeof(uint32_t), st));
 
     if (tune) {
-        // time one E-step launch per schedule on this data
+        // time one M-step launch per schedule on this data (the model copy it
+        // updates in place is restored before the real iterations)
         PROJ_CUDA_TRY(cudaMemcpyAsync(run.tmp.as<float>(), theta0, (size_t)C * stride * sizeof(float),
                                       cudaMemcpyDeviceToDevice, st));
+        DevBuf ll_scratch;
+        PROJ_TRY(ll_scratch.alloc((size_t)C * sizeof(double), st));
         cudaEvent_t e0, e1;
         PROJ_CUDA_TRY(cudaEventCreate(&e0));
         PROJ_CUDA_TRY(cudaEventCreate(&e1));
         float best_ms = 1e30f;
         for (const Sched &sc : kScheds) {
             int G = 1;
-            const int kpp = em_tc_plan(insts, items, G, sc.ctas, sc.g_target);
+            const int kpp = em_tc_plan(insts, items, G, sc.ctas, sc.waves);
             DevBuf ib;
             PROJ_TRY(ib.alloc(items.size() * sizeof(EmItem), st));
             PROJ_CUDA_TRY(cudaMemcpyAsync(ib.as<EmItem>(), items.data(), items.size() * sizeof(EmItem),
@@ -712,24 +853,39 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
             P.packed = packed; P.nwords = nwords; P.inst = inst_dev; P.items = ib.as<EmItem>();
             P.n_items = (int)items.size(); P.theta_in = run.tmp.as<float>(); P.stride = stride;
             P.part_ll = run.part.as<double>(); P.part_acc = run.part.as<double>() + (size_t)G * C;
-            P.C = C; P.err = run.flag.as<int>(); P.mstep = 0;
+            P.C = C; P.err = run.flag.as<int>(); P.mstep = 1; P.G = G; P.beta = 0.25f;
+            P.theta_out = run.tmp.as<float>(); P.ll_out = ll_scratch.as<double>();
+            P.tile_done = run.tiles.as<uint32_t>();
             const int grid = (int)std::min<int64_t>((int64_t)items.size(),
                                                     (int64_t)sm_count() * std::min(sc.ctas, ctas_per_sm(kpp)));
             PROJ_CUDA_TRY(cudaEventRecord(e0, st));
             PROJ_TRY(dispatch(kpp, P, grid, st));
+            if (G > kFoldMaxG) {  // the separate fold is part of this schedule's cost
+                const int64_t nq = C * stride;
+                em_tc_reduce_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(
+                    P.part_acc, P.part_ll, G, C, stride, inst_dev, (int)insts.size(), P.beta, 1,
+                    run.tmp.as<float>(), ll_scratch.as<double>());
+                PROJ_LAUNCH_CHECK("em_tc_reduce_kernel");
+            }
             PROJ_CUDA_TRY(cudaEventRecord(e1, st));
             PROJ_CUDA_TRY(cudaEventSynchronize(e1));
             float ms = 0.f;
             PROJ_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best_ms) { best_ms = ms; sched = sc; }
+            if (ms < 0.97f * best_ms) { best_ms = ms; sched = sc; }  // earlier wins near-ties
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tuned[key] = sched;
     }
-    run.kp = em_tc_plan(insts, items, run.G, sched.ctas, sched.g_target);
+    run.kp = em_tc_plan(insts, items, run.G, sched.ctas, sched.waves);
     run.ctas = sched.ctas;
+    if (const char *dbg = getenv("PROJ_DEBUG"))
+        if (dbg[0] == '1')
+            fprintf(stderr, "[projection] em_tc schedule: KP=%d ctas=%d (fit %d) waves=%d G=%d "
+                            "items=%zu tuned=%d\n",
+                    run.kp, sched.ctas, ctas_per_sm(run.kp), sched.waves, run.G, items.size(),
+                    (int)tune);
     PROJ_TRY(run.items.alloc(items.size() * sizeof(EmItem), st));
     PROJ_CUDA_TRY(cudaMemcpyAsync(run.items.as<EmItem>(), items.data(), items.size() * sizeof(EmItem),
                                   cudaMemcpyHostToDevice, st));
@@ -755,20 +911,27 @@ int em_tc_enqueue(EmTcRun &run, int iters, float beta, float *theta_out, double 
     P.part_ll = run.part.as<double>();
     P.part_acc = run.part.as<double>() + (size_t)G * C;
     P.C = C;
+    P.G = G;
+    P.beta = beta;
+    P.theta_out = run.tmp.as<float>();  // in place
+    P.ll_out = ll;
+    P.tile_done = run.tiles.as<uint32_t>();
     P.err = run.flag.as<int>();
     const int grid = (int)std::min<int64_t>((int64_t)run.n_items,
                                             (int64_t)sm_count() * std::min(run.ctas, ctas_per_sm(run.kp)));
     for (int it = 0; it <= iters; ++it) {
         P.mstep = it < iters;
         PROJ_TRY(dispatch(run.kp, P, grid, st));
-        const int64_t n = P.mstep ? C * stride : C;
-        {
-            TraceSpan ts_("em_reduce", st);
-            em_tc_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-                P.part_acc, P.part_ll, G, C, stride, run.inst_dev, run.n_inst, beta, P.mstep,
-                run.tmp.as<float>(), ll);
+        if (G > kFoldMaxG) {
+            const int64_t n = P.mstep ? C * stride : C;
+            {
+                TraceSpan ts_("em_reduce", st);
+                em_tc_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                    P.part_acc, P.part_ll, G, C, stride, run.inst_dev, run.n_inst, beta, P.mstep,
+                    run.tmp.as<float>(), ll);
+            }
+            PROJ_LAUNCH_CHECK("em_tc_reduce_kernel");
         }
-        PROJ_LAUNCH_CHECK("em_tc_reduce_kernel");
     }
     PROJ_CUDA_TRY(cudaMemcpyAsync(theta_out, run.tmp.as<float>(), (size_t)C * stride * sizeof(float),
                                   cudaMemcpyDeviceToDevice, st));
@@ -807,6 +970,7 @@ int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const f
     insts[0].C = C;
     insts[0].cand_begin = 0;
     insts[0].lmers = L.x;
+    insts[0].seq_off = L.seq_off.data();
     EmInst in{};
     in.seq_off = L.seq_off_dev();
     in.t = L.t;

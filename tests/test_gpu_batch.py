@@ -50,13 +50,25 @@ def test_batch_equals_single_searches(P):
                                 precision=P.PROJ_EM_BF16_SPLIT)
         assert g["n_candidates"] == one["n_candidates"] and g["n_members"] == one["n_members"]
         assert (g["k"], g["s"], g["m"]) == (one["k"], one["s"], one["m"])
-        assert g["consensus"] == one["consensus"]
-        assert np.array_equal(g["sites"], one["sites"])
-        assert g["score"] == one["score"]
         # both are BF16-split results that differ only in the order of the FP32
         # count sums over sequence groups; bounded by the BF16-split tolerances
         assert abs(g["loglik"] - one["loglik"]) <= ll_tol(one["loglik"], inst.t, LL_REL_BF16)
-        assert np.max(np.abs(g["pwm"] - one["pwm"])) <= 5e-5
+        if g["win_index"] == one["win_index"]:
+            assert g["consensus"] == one["consensus"]
+            assert np.array_equal(g["sites"], one["sites"])
+            assert g["score"] == one["score"]
+            assert np.max(np.abs(g["pwm"] - one["pwm"])) <= 5e-5
+        else:
+            # two candidates whose likelihoods tie within BF16-split noise: each
+            # side's winner must be a near-best candidate of the FP64 oracle, and
+            # each side's model must be the oracle's model of its own winner
+            want = O.find([q.decode() for q in inst.seqs], inst.l, inst.d, p["k"], p["s"],
+                          p["m"], seed=sd, em_iters=5, beta=0.25, nthreads=16)
+            for r in (g, one):
+                w = r["win_index"]
+                assert abs(want["ll_all"][w] - want["loglik"]) <= ll_tol(want["loglik"], inst.t,
+                                                                          LL_REL_BF16)
+                assert np.max(np.abs(r["pwm"] - want["pwm_all"][w])) <= 5e-5
 
 
 def test_batch_matches_oracle(P):
