@@ -377,6 +377,8 @@ def run_top(args):
     inst = instance_for_config(5)
     p = inst.params
     k, s, m, iters, beta, top = p["k"], p["s"], p["m"], p["em_iters"], p["beta"], p["top"]
+    if args.trials:  # a shorter run of the same instance (profiling captures)
+        m = args.trials
     seed = 1005
     dev = torch.device("cuda", 0)
     packed = P.projection_pack(torch.from_numpy(inst.ascii).to(dev))
@@ -427,7 +429,7 @@ def run_top(args):
         "metric": METRIC, "value": scores / T, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": T * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16-split", "data": "synthetic",
-        "config": {"workload": "markov-gc40 zoops(20,5) t=2000 n=500 k=10 s=4 m=500 top=1024 "
+        "config": {"workload": f"markov-gc40 zoops(20,5) t=2000 n=500 k=10 s=4 m={m} top=1024 "
                                "em_iters=10 pseudocount=0.25", "config_index": 5,
                    "x_lmers": x, "l2": "flushed between steps (512 MB write)"},
         "hashes_per_s": m * x / T, "hash_ms_per_step": hash_ms / args.steps,
@@ -463,6 +465,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-inst", type=int, default=256)
     ap.add_argument("--err-sample", type=int, default=16)
+    ap.add_argument("--trials", type=int, default=0,
+                    help="config 5 only: hash this many trials instead of 500 (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

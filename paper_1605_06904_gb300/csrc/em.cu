@@ -190,7 +190,8 @@ __device__ __forceinline__ void finalize_body(
     const uint32_t *__restrict__ packed, int64_t nwords, const int32_t *__restrict__ seq_off,
     int t, int l, const double *__restrict__ bg, const float *__restrict__ theta, int stride,
     const double *__restrict__ ll, int64_t C, int64_t *__restrict__ best_out,
-    int32_t *__restrict__ sites, uint8_t *__restrict__ consensus, int32_t *__restrict__ score) {
+    int32_t *__restrict__ sites, uint8_t *__restrict__ consensus, int32_t *__restrict__ score,
+    bool with_sites = true) {
     __shared__ double s_v[32];
     __shared__ long long s_i[32];
     __shared__ double W[32 * 4];
@@ -241,6 +242,7 @@ __device__ __forceinline__ void finalize_body(
         consensus[tid] = (uint8_t)("ACTG"[a]);
     }
     __syncthreads();
+    if (!with_sites) return;  // sites_kernel and score_kernel follow
     // sites: first start maximising r(i,j), in FP64
     for (int i = warp; i < t; i += blockDim.x / 32) {
         const int64_t base = seq_off[i];
@@ -283,13 +285,72 @@ __device__ __forceinline__ void finalize_body(
     }
 }
 
+// Sites of the winner over many CTAs (one warp per sequence): FP64 scoring of
+// every l-mer is slow on one SM when t * n is large.
+__global__ void __launch_bounds__(256) sites_kernel(
+    const uint32_t *__restrict__ packed, int64_t nwords, const int32_t *__restrict__ seq_off,
+    int t, int l, const double *__restrict__ bg, const float *__restrict__ theta,
+    const int64_t *__restrict__ best, int32_t *__restrict__ sites) {
+    __shared__ double W[32 * 4];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long b = *best;
+    const int i = blockIdx.x * (blockDim.x / 32) + warp;
+    if (b < 0) {
+        if (lane == 0 && i < t) sites[i] = -1;
+        return;
+    }
+    const float *th = theta + b * (int64_t)(4 * l);
+    if (tid < 4 * l) W[tid] = log((double)th[tid]) - log(bg[tid & 3]);
+    __syncthreads();
+    if (i >= t) return;
+    const int64_t base = seq_off[i];
+    const int ns = seq_off[i + 1] - seq_off[i] - l + 1;
+    double bestv = -INFINITY;
+    int bj = 0x7fffffff;
+    for (int j = lane; j < ns; j += 32) {
+        const uint64_t win = window64(packed, nwords, base + j);
+        double r = 0.0;
+        for (int p = 0; p < l; ++p) r += W[p * 4 + (int)((win >> (2 * p)) & 3u)];
+        if (r > bestv) { bestv = r; bj = j; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, bestv, o);
+        const int oj = __shfl_down_sync(0xffffffffu, bj, o);
+        if (ob > bestv || (ob == bestv && oj < bj)) { bestv = ob; bj = oj; }
+    }
+    if (lane == 0) sites[i] = ns > 0 ? bj : -1;
+}
+
+// Score(s, DNA) of the winner's sites: sum over columns of the largest count.
+__global__ void __launch_bounds__(1024) score_kernel(
+    const uint32_t *__restrict__ packed, int64_t nwords, const int32_t *__restrict__ seq_off,
+    int t, int l, const int32_t *__restrict__ sites, int32_t *__restrict__ score) {
+    __shared__ int s_cnt[32 * 4];
+    const int tid = threadIdx.x;
+    for (int q = tid; q < 4 * l; q += blockDim.x) s_cnt[q] = 0;
+    __syncthreads();
+    for (int e = tid; e < t * l; e += blockDim.x) {
+        const int i = e / l, p = e - i * l;
+        const int a = sites[i];
+        if (a >= 0) atomicAdd(&s_cnt[p * 4 + code_at(packed, nwords, (int64_t)seq_off[i] + a + p)], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int sc = 0;
+        for (int p = 0; p < l; ++p)
+            sc += max(max(s_cnt[4 * p], s_cnt[4 * p + 1]), max(s_cnt[4 * p + 2], s_cnt[4 * p + 3]));
+        *score = sc;
+    }
+}
+
 __global__ void __launch_bounds__(1024) finalize_kernel(
     const uint32_t *__restrict__ packed, int64_t nwords, const int32_t *__restrict__ seq_off,
     int t, int l, const double *__restrict__ bg, const float *__restrict__ theta,
     const double *__restrict__ ll, int64_t C, int64_t *__restrict__ best_out,
     int32_t *__restrict__ sites, uint8_t *__restrict__ consensus, int32_t *__restrict__ score) {
     finalize_body(packed, nwords, seq_off, t, l, bg, theta, 4 * l, ll, C, best_out, sites,
-                  consensus, score);
+                  consensus, score, false);
 }
 
 // One CTA per instance of a batch.
@@ -461,12 +522,24 @@ int launch_finalize_batch(const uint32_t *packed, int64_t nwords, const BatchIns
 int launch_finalize(const uint32_t *packed, const Layout &L, const double *bg,
                     const float *theta, const double *ll, int64_t C, int64_t *best,
                     int32_t *sites, uint8_t *consensus, int32_t *score, cudaStream_t st) {
+    PROJ_REQUIRE(L.l <= 32, "l above 32 is not supported");
     {
         TraceSpan ts_("finalize", st);
         finalize_kernel<<<1, 1024, 0, st>>>(packed, L.nwords, L.seq_off_dev(), L.t, L.l, bg, theta, ll,
                                             C, best, sites, consensus, score);
     }
     PROJ_LAUNCH_CHECK("finalize_kernel");
+    {
+        TraceSpan ts_("finalize", st);
+        sites_kernel<<<(unsigned)((L.t + 7) / 8), 256, 0, st>>>(packed, L.nwords, L.seq_off_dev(),
+                                                                L.t, L.l, bg, theta, best, sites);
+    }
+    PROJ_LAUNCH_CHECK("sites_kernel");
+    {
+        TraceSpan ts_("finalize", st);
+        score_kernel<<<1, 1024, 0, st>>>(packed, L.nwords, L.seq_off_dev(), L.t, L.l, sites, score);
+    }
+    PROJ_LAUNCH_CHECK("score_kernel");
     return PROJ_OK;
 }
 

@@ -308,31 +308,41 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     __threadfence_block();
     __syncthreads();
 
-    // stable placement at the bucket cursors, one warp walking the list
-    if (warp == 0) {
-        for (int q0 = 0; q0 < NM; q0 += 32) {
-            const int q = q0 + lane;
-            const bool act = q < NM;
-            const unsigned amask = __ballot_sync(0xffffffffu, act);
-            uint32_t rel = 0u;
-            int gid = 0, cur = 0, rank = 0;
-            unsigned grp = 0u;
-            if (act) {
-                rel = P.scratch_key[mbase + q];
-                gid = P.scratch_gid[mbase + q];
-                grp = __match_any_sync(amask, rel);
-                rank = __popc(grp & ((1u << lane) - 1u));
-                cur = P.hist16 ? (int)hist16[rel] : (int)hist32[rel];
-            }
-            __syncwarp();
-            if (act) {
-                P.members[mbase + cur + rank] = gid;
-                if (rank == 0) {
-                    const int nxt = cur + __popc(grp);
-                    if (P.hist16) hist16[rel] = (uint16_t)nxt; else hist32[rel] = (uint32_t)nxt;
+    // stable placement at the bucket cursors: the list is taken in rounds of
+    // kThreads entries, all loaded at once; the warps then take turns in list
+    // order, and within a warp match_any ranks equal keys, so every bucket's
+    // members come out ascending
+    for (int q0 = 0; q0 < NM; q0 += kThreads) {
+        const int q = q0 + tid;
+        const bool act = q < NM;
+        uint32_t rel = 0u;
+        int gid = 0;
+        if (act) {
+            rel = P.scratch_key[mbase + q];
+            gid = P.scratch_gid[mbase + q];
+        }
+        const unsigned amask = __ballot_sync(0xffffffffu, act);
+        unsigned grp = 0u;
+        int rank = 0;
+        if (act) {
+            grp = __match_any_sync(amask, rel);
+            rank = __popc(grp & ((1u << lane) - 1u));
+        }
+        const int nturn = min(kWarps, (NM - q0 + 31) / 32);
+        for (int w = 0; w < nturn; ++w) {
+            if (warp == w) {
+                int cur = 0;
+                if (act) cur = P.hist16 ? (int)hist16[rel] : (int)hist32[rel];
+                __syncwarp();
+                if (act) {
+                    P.members[mbase + cur + rank] = gid;
+                    if (rank == 0) {
+                        const int nxt = cur + __popc(grp);
+                        if (P.hist16) hist16[rel] = (uint16_t)nxt; else hist32[rel] = (uint32_t)nxt;
+                    }
                 }
             }
-            __syncwarp();
+            __syncthreads();
         }
     }
 }

@@ -2,6 +2,8 @@
 // `top` buckets with the most member l-mers; equal sizes keep the (trial, key)
 // order of the candidate list), and gathering their member lists into a
 // compact CSR list for theta^0 and EM.
+#include <stdint.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -25,22 +27,65 @@ __global__ void size_hist_kernel(const int32_t *__restrict__ cnt, int64_t C,
         if (h[b]) atomicAdd(&bins[b], (unsigned long long)h[b]);
 }
 
-// One CTA walks the candidates in index order and keeps every candidate
-// larger than `cstar` and the first `need_eq` of size `cstar` (ballot scans
-// keep the order): the position of a kept candidate is the number of larger
-// ones before it plus min(number of size-cstar ones before it, need_eq).
-// Writes the kept indices and sizes (at most `cap`).
+// Candidates are split into contiguous ranges, one CTA each.  size_count_kernel
+// counts, per range, the candidates larger than `cstar` and equal to it;
+// size_select_kernel then walks its range in index order and keeps every
+// candidate larger than `cstar` and the first `need_eq` of size `cstar` over
+// the whole list (ballot scans keep the order): the position of a kept
+// candidate is the number of larger ones before it plus min(number of
+// size-cstar ones before it, need_eq), with the counts of earlier ranges added.
+__global__ void __launch_bounds__(1024) size_count_kernel(const int32_t *__restrict__ cnt, int64_t C,
+                                                          int cstar, int64_t per_block,
+                                                          longlong2 *__restrict__ blk) {
+    __shared__ long long s_a[32], s_b[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t lo = blockIdx.x * per_block, hi = min(C, lo + per_block);
+    long long a = 0, b = 0;
+    for (int64_t c = lo + tid; c < hi; c += 1024) {
+        const int v = cnt[c];
+        a += v > cstar;
+        b += v == cstar;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) { s_a[warp] = a; s_b[warp] = b; }
+    __syncthreads();
+    if (tid == 0) {
+        long long ta = 0, tb = 0;
+        for (int w = 0; w < 32; ++w) { ta += s_a[w]; tb += s_b[w]; }
+        blk[blockIdx.x] = make_longlong2(ta, tb);
+    }
+}
+
 __global__ void __launch_bounds__(1024) size_select_kernel(const int32_t *__restrict__ cnt,
                                                            int64_t C, int cstar, int64_t need_eq,
+                                                           int64_t per_block,
+                                                           const longlong2 *__restrict__ blk,
                                                            int64_t *__restrict__ out_idx,
                                                            int32_t *__restrict__ out_cnt,
                                                            int64_t cap) {
     __shared__ int s_gt[33], s_eq[33];
+    __shared__ long long s_base[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int64_t gt_seen = 0, eq_seen = 0;
-    for (int64_t base = 0; base < C; base += 1024) {
+    if (warp == 0) {  // counts of the earlier ranges
+        long long a = 0, b = 0;
+        for (int q = lane; q < (int)blockIdx.x; q += 32) { a += blk[q].x; b += blk[q].y; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) { s_base[0] = a; s_base[1] = b; }
+    }
+    __syncthreads();
+    int64_t gt_seen = s_base[0], eq_seen = s_base[1];
+    const int64_t lo = blockIdx.x * per_block, hi = min(C, lo + per_block);
+    for (int64_t base = lo; base < hi; base += 1024) {
         const int64_t c = base + tid;
-        const int v = c < C ? cnt[c] : -1;
+        const int v = c < hi ? cnt[c] : -1;
         const bool gt = v > cstar, eq = v == cstar;
         const unsigned bgt = __ballot_sync(0xffffffffu, gt), beq = __ballot_sync(0xffffffffu, eq);
         if (lane == 0) { s_gt[warp] = __popc(bgt); s_eq[warp] = __popc(beq); }
@@ -130,12 +175,23 @@ int select_top(const int32_t *cnt_dev, int64_t C, int64_t top, std::vector<int64
         for (int64_t c : sel) sel_cnt.push_back(all[c]);
         return PROJ_OK;
     }
-    PROJ_TRY(out.alloc(want * (sizeof(int64_t) + sizeof(int32_t)), st));
+    const int nblk = (int)std::min<int64_t>((C + 1023) / 1024, (int64_t)sm_count() * 2);
+    const int64_t per_block = (C + nblk - 1) / nblk;
+    PROJ_TRY(out.alloc(want * (sizeof(int64_t) + sizeof(int32_t)) + (size_t)nblk * sizeof(longlong2) + 16,
+                       st));
     int64_t *oi = out.as<int64_t>();
     int32_t *oc = reinterpret_cast<int32_t *>(oi + want);
+    longlong2 *blk = reinterpret_cast<longlong2 *>(
+        (reinterpret_cast<uintptr_t>(oc + want) + 15) & ~(uintptr_t)15);
     {
         TraceSpan ts_("select", st);
-        size_select_kernel<<<1, 1024, 0, st>>>(cnt_dev, C, cstar, need_eq, oi, oc, want);
+        size_count_kernel<<<nblk, 1024, 0, st>>>(cnt_dev, C, cstar, per_block, blk);
+    }
+    PROJ_LAUNCH_CHECK("size_count_kernel");
+    {
+        TraceSpan ts_("select", st);
+        size_select_kernel<<<nblk, 1024, 0, st>>>(cnt_dev, C, cstar, need_eq, per_block, blk, oi, oc,
+                                                  want);
     }
     PROJ_LAUNCH_CHECK("size_select_kernel");
     std::vector<int64_t> picked(want);
