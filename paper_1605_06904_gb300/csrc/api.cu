@@ -292,8 +292,10 @@ static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int 
 
     // pass sizes: count first, then size the candidate list exactly
     HashOut probe;
+    HashState hstate;  // the counting pass's partition and offsets, reused by the fill
     DevBuf off0;
     PROJ_TRY(off0.alloc(sizeof(int64_t), st));
+    probe.state = &hstate;
     probe.totals = totals;
     probe.cand_off = off0.as<int64_t>();
     probe.count_only = true;
@@ -317,6 +319,7 @@ static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int 
     ho.cand_cnt = reinterpret_cast<int32_t *>(ho.cand_key + C);
     ho.members = ho.cand_cnt + C;
     ho.totals = totals;
+    ho.state = &hstate;
     PROJ_TRY(run_trial_hash(packed, L, k, s, seed, 0, m, nullptr, ho, st));
 
     // keep only the `top` largest buckets when asked (serving-scale inputs)

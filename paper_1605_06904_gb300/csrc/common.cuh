@@ -96,7 +96,16 @@ int launch_background(const uint32_t *packed, int64_t total, double *bg, cudaStr
 int launch_positions(uint64_t seed, int64_t trial_begin, int64_t n_trials, int l, int k,
                      uint8_t *pos, cudaStream_t st);
 
+// What a counting call of run_trial_hash computed, kept for the filling call of
+// the same search (same input, k, s, seed and trials) so that the key-range
+// partition, the per-unit counts and their offsets are not computed twice.
+struct HashState {
+    DevBuf meta, part_buf;
+    bool valid = false;
+};
+
 struct HashOut {
+    HashState *state = nullptr;     // optional: filled by a count_only call, reused after
     uint8_t *positions = nullptr;   // [n_trials][k] or null
     uint32_t *counts = nullptr;     // [n_trials][4^k] or null
     int64_t cap_cand = 0, cap_members = 0;

@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_batch_kernel(const HashParam
 // ---------------------------------------------------------------------------
 constexpr int kPartThreads = 256;
 constexpr int kPartWarps = kPartThreads / 32;
-constexpr int kChunk = 8192;  // l-mers per (trial, chunk)
+constexpr int kChunk = 32768;  // l-mers per (trial, chunk)
 constexpr int kMaxParts = 32;
 
 __device__ __forceinline__ void part_setup(const HashParams &P, int trial_local, int *s_pos) {
@@ -474,6 +474,7 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const HashPa
 #pragma unroll
     for (int q = 0; q < 16; ++q) pos[q] = q < P.k ? s_pos[q] : 0;
     const int g0 = chunk * kChunk, g1 = min(P.x, g0 + kChunk);
+    int i = g0 + tid < g1 ? seq_of(P.lmer_off, P.t, g0 + tid) : 0;  // advanced as g grows
     for (int r0 = g0; r0 < g1; r0 += kPartThreads) {
         for (int q = tid; q < kPartWarps * kMaxParts; q += kPartThreads) (&s_w[0][0])[q] = 0;
         __syncthreads();
@@ -481,7 +482,7 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const HashPa
         const bool ok = g < g1;
         uint32_t key = 0u, part = 0u;
         if (ok) {
-            const int i = seq_of(P.lmer_off, P.t, g);
+            while (__ldg(P.lmer_off + i + 1) <= g) ++i;
             const int64_t b0 = (int64_t)__ldg(P.seq_off + i) + (g - __ldg(P.lmer_off + i));
             key = lmer_key(window64(P.packed, P.nwords, b0), pos, P.k);
             part = key / (uint32_t)P.hb;
@@ -550,6 +551,12 @@ __global__ void __launch_bounds__(1024) hash_scan_kernel(const int32_t *__restri
     }
 }
 
+// cand_off[C] = total members (C = totals[0]) when it fits the capacity.
+__global__ void cand_end_kernel(const int64_t *__restrict__ totals, int64_t cap_cand,
+                                int64_t *__restrict__ cand_off) {
+    if (totals[0] <= cap_cand) cand_off[totals[0]] = totals[1];
+}
+
 }  // namespace
 
 int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64_t seed,
@@ -613,8 +620,11 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
         return PROJ_OK;
     }
     PROJ_REQUIRE(n_units < (int64_t)1 << 31, "too many (trial, part) units");
-    DevBuf meta;
-    PROJ_TRY(meta.alloc((size_t)n_units * (4 + 4 + 8 + 8), st));
+    const bool reuse = out.state && out.state->valid;
+    DevBuf meta_own, part_own;
+    DevBuf &meta = out.state ? out.state->meta : meta_own;
+    DevBuf &part_buf = out.state ? out.state->part_buf : part_own;
+    if (!reuse) PROJ_TRY(meta.alloc((size_t)n_units * (4 + 4 + 8 + 8), st));
     P.part_nb = meta.as<int32_t>();
     P.part_nm = P.part_nb + n_units;
     int64_t *cbase = reinterpret_cast<int64_t *>(P.part_nm + n_units);
@@ -623,13 +633,21 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
     P.mem_base = mbase;
 
     // large inputs over several key-range parts: partition (key, id) pairs first
-    DevBuf part_buf;
     if (partitioned) {
         PROJ_REQUIRE(P.parts <= kMaxParts, "too many key-range parts");
         P.n_chunks = (int)((L.x + kChunk - 1) / kChunk);
         const int64_t n_cnt = n_trials * P.parts * P.n_chunks;
         PROJ_REQUIRE(n_trials * L.x < ((int64_t)1 << 40), "partition too large");
-        PROJ_TRY(part_buf.alloc((size_t)(2 * n_cnt + 1) * 8 + (size_t)n_trials * L.x * 8, st));
+        if (!reuse)
+            PROJ_TRY(part_buf.alloc((size_t)(2 * n_cnt + 1) * 8 + (size_t)n_trials * L.x * 8, st));
+        int64_t *cnt = part_buf.as<int64_t>();
+        int64_t *seg = cnt + n_cnt;
+        uint2 *pairs = reinterpret_cast<uint2 *>(seg + n_cnt + 1);
+        P.pairs = pairs;
+        P.seg_off = seg;
+    }
+    if (partitioned && !reuse) {
+        const int64_t n_cnt = n_trials * P.parts * P.n_chunks;
         int64_t *cnt = part_buf.as<int64_t>();
         int64_t *seg = cnt + n_cnt;
         uint2 *pairs = reinterpret_cast<uint2 *>(seg + n_cnt + 1);
@@ -649,25 +667,32 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
             part_scatter_kernel<<<grid, kPartThreads, 0, st>>>(P, seg, pairs);
         }
         PROJ_LAUNCH_CHECK("part_scatter_kernel");
-        P.pairs = pairs;
-        P.seg_off = seg;
     }
     PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
     PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
-    {
-        TraceSpan ts_("hash_count", st);
-        hash_kernel<false><<<(unsigned)n_units, kThreads, S1.total, st>>>(P);
+    if (!reuse) {
+        {
+            TraceSpan ts_("hash_count", st);
+            hash_kernel<false><<<(unsigned)n_units, kThreads, S1.total, st>>>(P);
+        }
+        PROJ_LAUNCH_CHECK("hash_kernel<count>");
+        {
+            TraceSpan ts_("hash_scan", st);
+            hash_scan_kernel<<<1, 1024, 0, st>>>(P.part_nb, P.part_nm, (int)n_units, cbase, mbase,
+                                                 out.totals, out.cap_cand, out.cand_off);
+        }
+        PROJ_LAUNCH_CHECK("hash_scan_kernel");
+    } else {
+        // the counting call wrote the totals; only the end of the offsets is new
+        cand_end_kernel<<<1, 1, 0, st>>>(out.totals, out.cap_cand, out.cand_off);
+        PROJ_LAUNCH_CHECK("cand_end_kernel");
     }
-    PROJ_LAUNCH_CHECK("hash_kernel<count>");
-    {
-        TraceSpan ts_("hash_scan", st);
-        hash_scan_kernel<<<1, 1024, 0, st>>>(P.part_nb, P.part_nm, (int)n_units, cbase, mbase,
-                                             out.totals, out.cap_cand, out.cand_off);
+    if (out.count_only) {
+        if (out.state) out.state->valid = true;
+        return PROJ_OK;
     }
-    PROJ_LAUNCH_CHECK("hash_scan_kernel");
-    if (out.count_only) return PROJ_OK;
 
     DevBuf scratch;
     if (out.cap_members > 0) PROJ_TRY(scratch.alloc((size_t)out.cap_members * 8, st));
