@@ -411,7 +411,13 @@ def run_top(args):
     clk = clocks.stop()
     em_ms, em_launches = P.projection_trace_read("em_tc")
     hash_ms, _ = P.projection_trace_read("hash")
+    hc_ms, hc_launches = P.projection_trace_read("hash_count")
     _, all_launches = P.projection_trace_read("")
+    phases = {name: P.projection_trace_read(name)[0] / args.steps
+              for name in ("hash_partition", "hash_count", "hash_scan", "hash_fill", "select",
+                           "theta0", "em_tc", "em_reduce", "finalize")}
+    hist_peak = P.projection_hist_peak(k)
+    hc_rate = m * x * hc_launches / (hc_ms / 1e3) if hc_ms > 0 else None
     T = float(np.mean(ms)) / 1e3
     fp32_t0 = time.perf_counter()
     res32 = step(P.PROJ_EM_FP32)
@@ -433,6 +439,7 @@ def run_top(args):
                                "em_iters=10 pseudocount=0.25", "config_index": 5,
                    "x_lmers": x, "l2": "flushed between steps (512 MB write)"},
         "hashes_per_s": m * x / T, "hash_ms_per_step": hash_ms / args.steps,
+        "ms_per_step_by_phase": phases,
         "n_candidates": res["n_candidates"], "n_refined": R,
         "fp32_ms_per_step": T32 * 1e3, "motif_found": res["consensus"],
         "motif_found_fp32": res32["consensus"], "motif_planted": inst.motif,
@@ -443,6 +450,11 @@ def run_top(args):
                      "kernel": "em_tc_kernel", "launches": em_launches,
                      "avg_launch_ms": em_ms / max(1, em_launches),
                      "peak_source": f"bf16_tflops_sustained ({pk_kind})"},
+        "hash_roofline": {"kernel": "hash_kernel<count>", "bound": "smem_atomic",
+                          "achieved": hc_rate, "peak": hist_peak, "unit": "updates/s",
+                          "frac": hc_rate / hist_peak if hc_rate else None,
+                          "avg_launch_ms": hc_ms / max(1, hc_launches),
+                          "peak_source": f"projection_hist_peak({k}) measured in this run"},
         "clocks": clk, "gpu_launches": all_launches / max(1, args.steps), "cpu_baseline": None,
     }
     print(json.dumps(line), flush=True)
@@ -545,6 +557,7 @@ def main():
     scores_step = x * C * (iters + 1)
     em_name = "em_fp32" if prec == P.PROJ_EM_FP32 else "em_tc"
     em_ms, em_launches = P.projection_trace_read(em_name)
+    hc_ms, hc_launches = P.projection_trace_read("hash_count")
     _, all_launches = P.projection_trace_read("")
 
     (job_scores, job_hashes, job_steps), T_job = reduce_over_ranks(
@@ -581,6 +594,15 @@ def main():
                 "kernel": "em_tc_kernel", "launches": em_launches,
                 "avg_launch_ms": em_ms / max(1, em_launches),
                 "peak_source": f"bf16_tflops_sustained ({pk_kind})"}
+
+    # ---- the bucket-counting kernel against the shared-memory histogram rate
+    hist_peak = P.projection_hist_peak(k)
+    hc_rate = m * x * hc_launches / (hc_ms / 1e3) if hc_ms > 0 else None
+    hash_roof = {"kernel": "hash_kernel<count>", "bound": "smem_atomic", "achieved": hc_rate,
+                 "peak": hist_peak, "unit": "updates/s",
+                 "frac": hc_rate / hist_peak if hc_rate else None,
+                 "avg_launch_ms": hc_ms / max(1, hc_launches),
+                 "peak_source": f"projection_hist_peak({k}) measured in this run"}
 
     # ---- end to end through the public API: host ASCII in, result out
     e2e_times = []
@@ -631,7 +653,7 @@ def main():
                          f"theta0), {iters} EM iters") if errs else None,
         "wall_ms_per_step": wall * 1e3 / args.steps,
         "flush_ms_per_step": float(np.mean(flush_ms)),
-        "roofline": roof, "clocks": clk, "e2e": e2e,
+        "roofline": roof, "hash_roofline": hash_roof, "clocks": clk, "e2e": e2e,
         "gpu_launches": all_launches / max(1, args.steps),
         "cpu_baseline": None,
     }

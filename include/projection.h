@@ -272,6 +272,17 @@ void projection_result_free(projection_result *r);
  * Synchronises `stream`. */
 int projection_selftest_wait(int64_t timeout_ns, void *stream);
 
+/* ---- measurement helper (no counterpart in the paper) -------------------- */
+
+/* The shared-memory histogram rate that the bucket kernels (Algorithm 2 steps
+ * 2b-2c) are measured against: one 1024-thread CTA per SM counts
+ * register-generated pseudo-random keys into a shared-memory histogram laid out
+ * as the bucket kernels lay out 4^k buckets (u32 counters up to 128 KB, else
+ * u16 pairs over 65,536 buckets).  *updates_per_s = increments per second,
+ * whole GPU (fastest of three timed launches after one warm-up).  k in 1..10.
+ * Synchronises `stream`. */
+int projection_hist_peak(int k, double *updates_per_s, void *stream);
+
 /* ---- tracing (CUDA-event timers per kernel) ----------------------------- */
 
 /* on != 0: start recording a CUDA event pair around every kernel the library

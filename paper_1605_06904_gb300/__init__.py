@@ -326,6 +326,14 @@ def projection_selftest_wait(timeout_ns: int = 50_000_000, stream=None) -> int:
     return int(lib().projection_selftest_wait(int(timeout_ns), _stream(stream)))
 
 
+def projection_hist_peak(k: int, stream=None) -> float:
+    """Shared-memory histogram increments per second for 4^k buckets (the
+    bucket kernels' roofline denominator)."""
+    out = ctypes.c_double(0.0)
+    check(lib().projection_hist_peak(int(k), ctypes.byref(out), _stream(stream)))
+    return float(out.value)
+
+
 # ---- tracing -----------------------------------------------------------------
 
 def projection_trace_enable(on: bool = True) -> None:

@@ -62,6 +62,7 @@ SIGNATURES = {
                                ctypes.POINTER(ProjectionResult), P], i32),
     "projection_result_free": ([ctypes.POINTER(ProjectionResult)], None),
     "projection_selftest_wait": ([i64, P], i32),
+    "projection_hist_peak": ([i32, P, P], i32),
     "projection_trace_enable": ([i32], i32),
     "projection_trace_read": ([ctypes.c_char_p, P, P], i32),
 }

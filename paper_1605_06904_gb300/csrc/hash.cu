@@ -1048,3 +1048,71 @@ extern "C" int trial_hash_noalloc(const uint32_t *packed_dev, const int64_t *seq
     PROJ_LAUNCH_CHECK("hash_kernel<fill>");
     return PROJ_OK;
 }
+
+// ---------------------------------------------------------------------------
+// projection_hist_peak: the shared-memory histogram rate the bucket kernels
+// are measured against.  Every CTA (1024 threads, one per SM) counts
+// register-generated pseudo-random keys into a shared-memory histogram laid
+// out as the bucket kernels lay out the 4^k buckets of one CTA (u32 counters
+// when 4^k of them fit in 128 KB, else u16 pairs over 65,536 buckets).
+// ---------------------------------------------------------------------------
+namespace proj {
+namespace {
+
+__global__ void __launch_bounds__(kThreads, 1) hist_peak_kernel(uint32_t mask, int hist16, int iters,
+                                                                 uint32_t *sink) {
+    extern __shared__ uint32_t h[];
+    const int words = hist16 ? (int)((mask + 1) / 2) : (int)(mask + 1);
+    for (int w = threadIdx.x; w < words; w += kThreads) h[w] = 0u;
+    __syncthreads();
+    uint32_t x = 0x9E3779B9u * (blockIdx.x * kThreads + threadIdx.x + 1);
+    for (int i = 0; i < iters; ++i) {
+        x ^= x << 13;  // xorshift32 (Marsaglia 2003)
+        x ^= x >> 17;
+        x ^= x << 5;
+        const uint32_t key = x & mask;
+        if (hist16) atomicAdd(&h[key >> 1], 1u << (16 * (key & 1u)));
+        else atomicAdd(&h[key], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sink[blockIdx.x] = h[x & (uint32_t)(words - 1)];  // keep the work
+}
+
+}  // namespace
+}  // namespace proj
+
+extern "C" int projection_hist_peak(int k, double *updates_per_s, void *stream) {
+    using namespace proj;
+    clear_error();
+    PROJ_REQUIRE(updates_per_s != nullptr, "updates_per_s must not be NULL");
+    PROJ_REQUIRE(k >= 1 && k <= 10, "need 1 <= k <= 10");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t nbuck = 1ull << (2 * k);
+    const int hist16 = nbuck * 4 > (uint64_t)kHistBytes;
+    const uint32_t mask = (uint32_t)(hist16 ? std::min<uint64_t>(nbuck, 65536) : nbuck) - 1u;
+    const size_t smem = hist16 ? (size_t)(mask + 1) * 2 : (size_t)(mask + 1) * 4;
+    const int grid = sm_count();
+    const int iters = 16384;
+    DevBuf sink;
+    PROJ_TRY(sink.alloc((size_t)grid * 4, st));
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(hist_peak_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    cudaEvent_t e0, e1;
+    PROJ_CUDA_TRY(cudaEventCreate(&e0));
+    PROJ_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {  // first launch warms up; keep the fastest
+        PROJ_CUDA_TRY(cudaEventRecord(e0, st));
+        hist_peak_kernel<<<grid, kThreads, smem, st>>>(mask, hist16, iters, sink.as<uint32_t>());
+        PROJ_CUDA_TRY(cudaEventRecord(e1, st));
+        PROJ_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PROJ_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    PROJ_LAUNCH_CHECK("hist_peak_kernel");
+    *updates_per_s = (double)grid * kThreads * iters / (best * 1e-3);
+    return PROJ_OK;
+}
