@@ -94,6 +94,17 @@ __device__ __forceinline__ uint32_t lmer_key(uint64_t win, const int *pos, int k
     return key;
 }
 
+// The same with the number of projected positions fixed at compile time (K > 0);
+// K = 0 falls back to the run-time k.
+template <int K>
+__device__ __forceinline__ uint32_t lmer_key_k(uint64_t win, const int *pos, int k) {
+    if (K == 0) return lmer_key(win, pos, k);
+    uint32_t key = 0u;
+#pragma unroll
+    for (int q = 0; q < K; ++q) key = (key << 2) | (uint32_t)((win >> (2 * pos[q])) & 3u);
+    return key;
+}
+
 // Block-wide exclusive scan of two ints; returns the prefixes and the totals.
 __device__ inline void block_scan2(int a, int b, int &pa, int &pb, int &ta, int &tb,
                                    int2 *warp_tot) {
@@ -129,7 +140,7 @@ __device__ inline void block_scan2(int a, int b, int &pa, int &pb, int &ta, int 
 
 // One (trial, key-range part) unit of the bucket kernels; `unit` indexes the
 // per-unit arrays of P (part_nb, part_nm, cand_base, mem_base).
-template <bool FILL>
+template <bool FILL, int K>
 __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, uint8_t *smem,
                                           int *s_pos, int2 *s_warp, int *s_round) {
 
@@ -204,7 +215,7 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
         for (int gid = tid; gid < P.x; gid += kThreads) {
             while (s_lmer[i + 1] <= gid) ++i;
             const int64_t b0 = (int64_t)s_seq[i] + (gid - s_lmer[i]);
-            const uint32_t rel = lmer_key(window64(words, nwords, b0), pos, P.k) - lo_key;
+            const uint32_t rel = lmer_key_k<K>(window64(words, nwords, b0), pos, P.k) - lo_key;
             if (rel < hb) {
                 if (P.hist16) atomicAdd(&hist32[rel >> 1], 1u << (16 * (rel & 1u)));
                 else atomicAdd(&hist32[rel], 1u);
@@ -277,7 +288,7 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
                     gid = (int)it;
                     while (s_lmer[i + 1] <= gid) ++i;
                     const int64_t b0 = (int64_t)s_seq[i] + (gid - s_lmer[i]);
-                    rel = lmer_key(window64(words, nwords, b0), pos, P.k) - lo_key;
+                    rel = lmer_key_k<K>(window64(words, nwords, b0), pos, P.k) - lo_key;
                 }
                 e = rel < hb && ((bitmap[rel >> 5] >> (rel & 31u)) & 1u);
             }
@@ -347,13 +358,13 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     }
 }
 
-template <bool FILL>
+template <bool FILL, int K>
 __global__ void __launch_bounds__(kThreads, 1) hash_kernel(const HashParams P) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_pos[16];
     __shared__ int2 s_warp[kWarps + 1];
     __shared__ int s_round[kWarps + 1];
-    hash_unit<FILL>(P, (int)blockIdx.x, smem, s_pos, s_warp, s_round);
+    hash_unit<FILL, K>(P, (int)blockIdx.x, smem, s_pos, s_warp, s_round);
 }
 
 // Many instances in one launch: block u runs unit u - unit_begin[i] of the
@@ -373,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1) hash_batch_kernel(const HashParam
         const int mid = (lo + hi + 1) >> 1;
         if (unit_begin[mid] <= u) lo = mid; else hi = mid - 1;
     }
-    hash_unit<FILL>(insts[lo], (int)(u - unit_begin[lo]), smem, s_pos, s_warp, s_round);
+    hash_unit<FILL, 0>(insts[lo], (int)(u - unit_begin[lo]), smem, s_pos, s_warp, s_round);
 }
 
 // ---------------------------------------------------------------------------
@@ -411,6 +422,7 @@ __device__ __forceinline__ int seq_of(const int32_t *lmer_off, int t, int g) {
     return lo;
 }
 
+template <int K>
 __global__ void __launch_bounds__(kPartThreads) part_count_kernel(const HashParams P,
                                                                   int64_t *__restrict__ counts) {
     __shared__ int s_pos[16];
@@ -426,7 +438,7 @@ __global__ void __launch_bounds__(kPartThreads) part_count_kernel(const HashPara
     for (int g = g0 + tid; g < g1; g += kPartThreads) {
         while (__ldg(P.lmer_off + i + 1) <= g) ++i;
         const int64_t b0 = (int64_t)__ldg(P.seq_off + i) + (g - __ldg(P.lmer_off + i));
-        const uint32_t key = lmer_key(window64(P.packed, P.nwords, b0), pos, P.k);
+        const uint32_t key = lmer_key_k<K>(window64(P.packed, P.nwords, b0), pos, P.k);
         atomicAdd(&s_cnt[key / (uint32_t)P.hb], 1u);
     }
     __syncthreads();
@@ -459,6 +471,7 @@ __global__ void __launch_bounds__(1024) scan_i64_kernel(const int64_t *__restric
     if (tid == 1023) out[n] = s[1023];
 }
 
+template <int K>
 __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const HashParams P,
                                                                     const int64_t *__restrict__ offs,
                                                                     uint2 *__restrict__ pairs) {
@@ -484,7 +497,7 @@ __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const HashPa
         if (ok) {
             while (__ldg(P.lmer_off + i + 1) <= g) ++i;
             const int64_t b0 = (int64_t)__ldg(P.seq_off + i) + (g - __ldg(P.lmer_off + i));
-            key = lmer_key(window64(P.packed, P.nwords, b0), pos, P.k);
+            key = lmer_key_k<K>(window64(P.packed, P.nwords, b0), pos, P.k);
             part = key / (uint32_t)P.hb;
         }
         const unsigned act = __ballot_sync(0xffffffffu, ok);
@@ -555,6 +568,62 @@ __global__ void __launch_bounds__(1024) hash_scan_kernel(const int32_t *__restri
 __global__ void cand_end_kernel(const int64_t *__restrict__ totals, int64_t cap_cand,
                                 int64_t *__restrict__ cand_off) {
     if (totals[0] <= cap_cand) cand_off[totals[0]] = totals[1];
+}
+
+// Launches of the bucket kernels specialised on k.
+template <bool FILL, int K>
+int launch_hash_k(const HashParams &P, unsigned grid, int smem, cudaStream_t st) {
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<FILL, K>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+    hash_kernel<FILL, K><<<grid, kThreads, smem, st>>>(P);
+    PROJ_LAUNCH_CHECK(FILL ? "hash_kernel<fill>" : "hash_kernel<count>");
+    return PROJ_OK;
+}
+
+template <bool FILL>
+int launch_hash(const HashParams &P, unsigned grid, int smem, cudaStream_t st) {
+    switch (P.k) {
+        case 1: return launch_hash_k<FILL, 1>(P, grid, smem, st);
+        case 2: return launch_hash_k<FILL, 2>(P, grid, smem, st);
+        case 3: return launch_hash_k<FILL, 3>(P, grid, smem, st);
+        case 4: return launch_hash_k<FILL, 4>(P, grid, smem, st);
+        case 5: return launch_hash_k<FILL, 5>(P, grid, smem, st);
+        case 6: return launch_hash_k<FILL, 6>(P, grid, smem, st);
+        case 7: return launch_hash_k<FILL, 7>(P, grid, smem, st);
+        case 8: return launch_hash_k<FILL, 8>(P, grid, smem, st);
+        case 9: return launch_hash_k<FILL, 9>(P, grid, smem, st);
+        default: return launch_hash_k<FILL, 10>(P, grid, smem, st);
+    }
+}
+
+template <int K>
+int launch_partition_k(const HashParams &P, dim3 grid, int64_t *cnt, int64_t *seg, uint2 *pairs,
+                       int64_t n_cnt, cudaStream_t st) {
+    {
+        TraceSpan ts_("hash_partition", st);
+        part_count_kernel<K><<<grid, kPartThreads, 0, st>>>(P, cnt);
+    }
+    PROJ_LAUNCH_CHECK("part_count_kernel");
+    {
+        TraceSpan ts_("hash_partition", st);
+        scan_i64_kernel<<<1, 1024, 0, st>>>(cnt, n_cnt, seg);
+    }
+    PROJ_LAUNCH_CHECK("scan_i64_kernel");
+    {
+        TraceSpan ts_("hash_partition", st);
+        part_scatter_kernel<K><<<grid, kPartThreads, 0, st>>>(P, seg, pairs);
+    }
+    PROJ_LAUNCH_CHECK("part_scatter_kernel");
+    return PROJ_OK;
+}
+
+int launch_partition(const HashParams &P, dim3 grid, int64_t *cnt, int64_t *seg, uint2 *pairs,
+                     int64_t n_cnt, cudaStream_t st) {
+    switch (P.k) {
+        case 9: return launch_partition_k<9>(P, grid, cnt, seg, pairs, n_cnt, st);
+        case 10: return launch_partition_k<10>(P, grid, cnt, seg, pairs, n_cnt, st);
+        default: return launch_partition_k<0>(P, grid, cnt, seg, pairs, n_cnt, st);
+    }
 }
 
 }  // namespace
@@ -652,32 +721,13 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
         int64_t *seg = cnt + n_cnt;
         uint2 *pairs = reinterpret_cast<uint2 *>(seg + n_cnt + 1);
         const dim3 grid((unsigned)P.n_chunks, (unsigned)n_trials);
-        {
-            TraceSpan ts_("hash_partition", st);
-            part_count_kernel<<<grid, kPartThreads, 0, st>>>(P, cnt);
-        }
-        PROJ_LAUNCH_CHECK("part_count_kernel");
-        {
-            TraceSpan ts_("hash_partition", st);
-            scan_i64_kernel<<<1, 1024, 0, st>>>(cnt, n_cnt, seg);
-        }
-        PROJ_LAUNCH_CHECK("scan_i64_kernel");
-        {
-            TraceSpan ts_("hash_partition", st);
-            part_scatter_kernel<<<grid, kPartThreads, 0, st>>>(P, seg, pairs);
-        }
-        PROJ_LAUNCH_CHECK("part_scatter_kernel");
+        PROJ_TRY(launch_partition(P, grid, cnt, seg, pairs, n_cnt, st));
     }
-    PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
-    PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
     if (!reuse) {
         {
             TraceSpan ts_("hash_count", st);
-            hash_kernel<false><<<(unsigned)n_units, kThreads, S1.total, st>>>(P);
+            PROJ_TRY(launch_hash<false>(P, (unsigned)n_units, S1.total, st));
         }
-        PROJ_LAUNCH_CHECK("hash_kernel<count>");
         {
             TraceSpan ts_("hash_scan", st);
             hash_scan_kernel<<<1, 1024, 0, st>>>(P.part_nb, P.part_nm, (int)n_units, cbase, mbase,
@@ -709,9 +759,8 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
     P.pos_out = nullptr;
     {
         TraceSpan ts_("hash_fill", st);
-        hash_kernel<true><<<(unsigned)n_units, kThreads, S2.total, st>>>(P);
+        PROJ_TRY(launch_hash<true>(P, (unsigned)n_units, S2.total, st));
     }
-    PROJ_LAUNCH_CHECK("hash_kernel<fill>");
     return PROJ_OK;
 }
 
@@ -1017,15 +1066,10 @@ extern "C" int trial_hash_noalloc(const uint32_t *packed_dev, const int64_t *seq
         PROJ_CUDA_TRY(cudaMemsetAsync(cand_off_dev, 0, sizeof(int64_t), st));
         return PROJ_OK;
     }
-    PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
-    PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
     {
         TraceSpan ts_("hash_count", st);
-        hash_kernel<false><<<(unsigned)n_units, kThreads, S1.total, st>>>(P);
+        PROJ_TRY(launch_hash<false>(P, (unsigned)n_units, S1.total, st));
     }
-    PROJ_LAUNCH_CHECK("hash_kernel<count>");
     {
         TraceSpan ts_("hash_scan", st);
         hash_scan_kernel<<<1, 1024, 0, st>>>(P.part_nb, P.part_nm, (int)n_units, cbase, mbase,
@@ -1043,9 +1087,8 @@ extern "C" int trial_hash_noalloc(const uint32_t *packed_dev, const int64_t *seq
     P.pos_out = nullptr;
     {
         TraceSpan ts_("hash_fill", st);
-        hash_kernel<true><<<(unsigned)n_units, kThreads, S2.total, st>>>(P);
+        PROJ_TRY(launch_hash<true>(P, (unsigned)n_units, S2.total, st));
     }
-    PROJ_LAUNCH_CHECK("hash_kernel<fill>");
     return PROJ_OK;
 }
 
