@@ -262,6 +262,23 @@ int projection_find_batch(const uint8_t *ascii, const int64_t *seq_off, const in
 
 void projection_result_free(projection_result *r);
 
+/* ---- step 1 for a batch, on the device (Section 5) ---------------------- */
+
+/* Algorithm 2 step 1 ("if not specified") for n instances held on the device:
+ * k = l - d - 1, s = max(3, ceil(2x / 4^k)), m = ceil(log(1 - q) / log B) with
+ * B = P[Binomial(t, p) < s] and p = C(l-d, k) / C(l, k) (Section 5), each only
+ * where the caller's entry is 0 (nonzero entries are kept).  All arrays are
+ * device int32 [n] except x_dev (int64 [n], l-mers of each instance); k, s and
+ * m are read and written in place.  status_dev[i]: 0 OK, -1 invalid instance
+ * (t < 1, l outside 1..32, d outside 0..l-1, k outside 1..l), -2 no finite
+ * trial count (k > l - d, or m above 2^24; m is then 0).  The same formulas as
+ * projection_default_params, evaluated in FP64 on the GPU.  Asynchronous on
+ * `stream`; EINVAL for n < 0, q outside (0, 1) or NULL arrays. */
+int projection_params_batch(int n, const int32_t *t_dev, const int64_t *x_dev,
+                            const int32_t *l_dev, const int32_t *d_dev, int32_t *k_dev,
+                            int32_t *s_dev, int32_t *m_dev, int32_t *status_dev, double q,
+                            void *stream);
+
 /* ---- failure detection --------------------------------------------------- */
 
 /* Self-test of the bounded waits used by the tensor-core kernels: launches a

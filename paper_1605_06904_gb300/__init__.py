@@ -326,6 +326,24 @@ def projection_selftest_wait(timeout_ns: int = 50_000_000, stream=None) -> int:
     return int(lib().projection_selftest_wait(int(timeout_ns), _stream(stream)))
 
 
+def projection_params_batch(t, x, l, d, k=None, s=None, m=None, q=0.95, stream=None):
+    """Algorithm 2 step 1 for a batch on the device (Section 5).  t, l, d, k, s,
+    m: int32 CUDA tensors [n] (k, s, m optional: zeros = derive); x: int64 CUDA
+    tensor [n] of l-mer counts.  Returns (k, s, m, status) as CUDA tensors."""
+    n = int(t.numel())
+    dev = t.device
+    z = lambda: torch.zeros(n, dtype=torch.int32, device=dev)
+    k = (k if k is not None else z()).to(torch.int32).contiguous().clone()
+    s = (s if s is not None else z()).to(torch.int32).contiguous().clone()
+    m = (m if m is not None else z()).to(torch.int32).contiguous().clone()
+    status = z()
+    t, x, l, d = (v.contiguous() for v in (t.to(torch.int32), x.to(torch.int64),
+                                           l.to(torch.int32), d.to(torch.int32)))
+    check(lib().projection_params_batch(n, _ptr(t), _ptr(x), _ptr(l), _ptr(d), _ptr(k), _ptr(s),
+                                        _ptr(m), _ptr(status), float(q), _stream(stream)))
+    return k, s, m, status
+
+
 def projection_hist_peak(k: int, stream=None) -> float:
     """Shared-memory histogram increments per second for 4^k buckets (the
     bucket kernels' roofline denominator)."""
