@@ -67,6 +67,8 @@ def _L():
             lib.orc_theta0.restype = None
             lib.orc_em.argtypes = [P, P, i32, i32, P, P, i64, i32, f64, P, P, P, i32]
             lib.orc_em.restype = i32
+            lib.orc_em_zoops.argtypes = [P, P, i32, i32, P, P, i64, i32, f64, f64, P, P, i32]
+            lib.orc_em_zoops.restype = i32
             lib.orc_sites.argtypes = [P, P, i32, i32, P, P, P]; lib.orc_sites.restype = None
             lib.orc_consensus.argtypes = [P, i32, P]; lib.orc_consensus.restype = None
             lib.orc_score.argtypes = [P, P, i32, i32, P]; lib.orc_score.restype = i32
@@ -265,6 +267,23 @@ def em(codes, seq_off, l, bg, pwm0, iters, beta, want_lse=False, want_trace=Fals
     if want_trace:
         out.append(tr)
     return tuple(out)
+
+
+def em_zoops(codes, seq_off, l, bg, pwm0, iters, beta, gamma, want_trace=False, nthreads=1):
+    """ZOOPS EM (site probability gamma per sequence) from each starting model
+    pwm0[C][l][4]: returns (pwm, ll[, trace])."""
+    codes = _c(codes, np.uint8); seq_off = _c(seq_off, np.int64)
+    pwm = np.array(pwm0, dtype=np.float64, copy=True, order="C").reshape(-1, l, 4)
+    C = pwm.shape[0]
+    t = seq_off.size - 1
+    bg = _c(bg, np.float64)
+    ll = np.empty(C, np.float64)
+    tr = np.empty((C, iters + 1), np.float64) if want_trace else None
+    rc = _L().orc_em_zoops(_p(codes), _p(seq_off), t, l, _p(bg), _p(pwm), C, iters, float(beta),
+                           float(gamma), _p(ll), _p(tr), int(nthreads))
+    if rc != 0:
+        raise ValueError("bad EM arguments")
+    return (pwm, ll, tr) if want_trace else (pwm, ll)
 
 
 def sites(codes, seq_off, l, bg, pwm) -> np.ndarray:

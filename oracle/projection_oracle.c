@@ -27,6 +27,10 @@
  *       during EM; a base absent from the input counts as one occurrence.
  *   R5  EM is the one-occurrence-per-sequence (OOPS) model with a uniform prior
  *       over sites and a pseudocount beta per base in the M-step.
+ *   R15 the zero-or-one-occurrence (ZOOPS) model named in Section 2 is read as
+ *       the standard two-component mixture with a fixed site probability gamma
+ *       per sequence (uniform over its starts) and the MAP M-step whose
+ *       denominator is the expected number of sites plus 4 beta.
  *
  * Parity status: every function below is pinned by a CPU test (worked example
  * of Figures 1, 2 and 4, Philox known-answer vectors, brute-force bucket
@@ -338,19 +342,80 @@ static void em_one(const uint8_t *codes, const int64_t *seq_off, int t, int l, c
     }
 }
 
+/* ZOOPS EM for ONE starting model (zero or one occurrence per sequence, the
+ * second search model of Section 2; reading R15).  A sequence holds one site
+ * with prior probability gamma (fixed), uniform over its n_i - l + 1 starts,
+ * or no site.  E-step, per sequence i with ns_i starts:
+ *     L_i = log[ (1 - gamma) + (gamma / ns_i) sum_j exp r(i,j) ]
+ * (log-likelihood ratio against the all-background model), and the posterior
+ * of a site at j
+ *     z(i,j) = (gamma / ns_i) exp r(i,j) / exp(L_i).
+ * M-step: pwm_p(a) = (sum_{i,j} z(i,j) [x_{i,j+p} = a] + beta)
+ *                    / (sum_{i,j} z(i,j) + 4 beta).
+ * LL = sum_i L_i.  gamma = 1 is the OOPS model (up to rounding).  Same
+ * iteration order as em_one. */
+static double log_add(double a, double b) {
+    double hi = a > b ? a : b, lo = a > b ? b : a;
+    if (hi == -INFINITY) return -INFINITY;
+    return hi + log1p(exp(lo - hi));
+}
+
+static void em_one_zoops(const uint8_t *codes, const int64_t *seq_off, int t, int l,
+                         const double bg[4], double *pwm, int iters, double beta, double gamma,
+                         double *ll, double *trace, double *r) {
+    double W[32][4];
+    const double log_no = gamma < 1.0 ? log1p(-gamma) : -INFINITY;
+    for (int it = 0; it <= iters; ++it) {
+        log_ratio(pwm, bg, l, W);
+        double N[32][4];
+        memset(N, 0, sizeof N);
+        double LL = 0.0, Z = 0.0;
+        for (int i = 0; i < t; ++i) {
+            int64_t ns = seq_scores(codes, seq_off, i, l, W, r);
+            if (ns == 0) continue;
+            double mx = r[0];
+            for (int64_t j = 1; j < ns; ++j) if (r[j] > mx) mx = r[j];
+            double S = 0.0;
+            for (int64_t j = 0; j < ns; ++j) S += exp(r[j] - mx);
+            const double log_site = log(gamma / (double)ns) + mx + log(S);
+            const double L = log_add(log_no, log_site);
+            LL += L;
+            if (it < iters) {
+                for (int64_t j = 0; j < ns; ++j) {
+                    double z = exp(log(gamma / (double)ns) + r[j] - L);
+                    const uint8_t *lmer = codes + seq_off[i] + j;
+                    for (int p = 0; p < l; ++p) N[p][lmer[p]] += z;
+                    Z += z;
+                }
+            }
+        }
+        if (trace) trace[it] = LL;
+        if (it == iters) { *ll = LL; break; }
+        for (int p = 0; p < l; ++p)
+            for (int a = 0; a < 4; ++a) pwm[p * 4 + a] = (N[p][a] + beta) / (Z + 4.0 * beta);
+    }
+}
+
 typedef struct {
     const uint8_t *codes; const int64_t *seq_off; int t, l; const double *bg;
     double *pwm; int64_t C; int iters; double beta; double *ll, *lse, *trace;
     int64_t c_begin, c_end; int64_t max_ns;
+    double gamma;  /* > 0 and < 1: ZOOPS with this site probability; else OOPS */
 } em_job;
 
 static void *em_worker(void *arg) {
     em_job *jb = (em_job *)arg;
     double *r = (double *)malloc(sizeof(double) * (size_t)(jb->max_ns > 0 ? jb->max_ns : 1));
-    for (int64_t c = jb->c_begin; c < jb->c_end; ++c)
-        em_one(jb->codes, jb->seq_off, jb->t, jb->l, jb->bg, jb->pwm + c * jb->l * 4, jb->iters,
-               jb->beta, jb->ll + c, jb->lse ? jb->lse + c * jb->t : NULL,
-               jb->trace ? jb->trace + c * (jb->iters + 1) : NULL, r);
+    for (int64_t c = jb->c_begin; c < jb->c_end; ++c) {
+        if (jb->gamma > 0.0)
+            em_one_zoops(jb->codes, jb->seq_off, jb->t, jb->l, jb->bg, jb->pwm + c * jb->l * 4,
+                         jb->iters, jb->beta, jb->gamma, jb->ll + c,
+                         jb->trace ? jb->trace + c * (jb->iters + 1) : NULL, r);
+        else
+            em_one(jb->codes, jb->seq_off, jb->t, jb->l, jb->bg, jb->pwm + c * jb->l * 4, jb->iters,
+                   jb->beta, jb->ll + c, jb->lse ? jb->lse + c * jb->t : NULL,
+                   jb->trace ? jb->trace + c * (jb->iters + 1) : NULL, r);
+    }
     free(r);
     return NULL;
 }
@@ -358,9 +423,9 @@ static void *em_worker(void *arg) {
 /* EM for C independent starting models pwm[C][l][4] (refined in place).
  * Candidates are independent, so they are split across `nthreads` threads;
  * the arithmetic of each candidate is the same as with one thread. */
-int orc_em(const uint8_t *codes, const int64_t *seq_off, int t, int l, const double bg[4],
-           double *pwm, int64_t C, int iters, double beta, double *ll, double *lse,
-           double *trace, int nthreads) {
+static int em_run(const uint8_t *codes, const int64_t *seq_off, int t, int l, const double bg[4],
+                  double *pwm, int64_t C, int iters, double beta, double gamma, double *ll,
+                  double *lse, double *trace, int nthreads) {
     if (l < 1 || l > 32 || iters < 0 || t < 1) return -1;
     int64_t max_ns = 0;
     for (int i = 0; i < t; ++i) {
@@ -375,7 +440,7 @@ int orc_em(const uint8_t *codes, const int64_t *seq_off, int t, int l, const dou
         em_job *jb = &jobs[w];
         jb->codes = codes; jb->seq_off = seq_off; jb->t = t; jb->l = l; jb->bg = bg;
         jb->pwm = pwm; jb->C = C; jb->iters = iters; jb->beta = beta; jb->ll = ll;
-        jb->lse = lse; jb->trace = trace; jb->max_ns = max_ns;
+        jb->lse = lse; jb->trace = trace; jb->max_ns = max_ns; jb->gamma = gamma;
         jb->c_begin = C * w / nthreads; jb->c_end = C * (w + 1) / nthreads;
     }
     for (int w = 1; w < nthreads; ++w) pthread_create(&th[w], NULL, em_worker, &jobs[w]);
@@ -383,6 +448,20 @@ int orc_em(const uint8_t *codes, const int64_t *seq_off, int t, int l, const dou
     for (int w = 1; w < nthreads; ++w) pthread_join(th[w], NULL);
     free(jobs); free(th);
     return 0;
+}
+
+int orc_em(const uint8_t *codes, const int64_t *seq_off, int t, int l, const double bg[4],
+           double *pwm, int64_t C, int iters, double beta, double *ll, double *lse,
+           double *trace, int nthreads) {
+    return em_run(codes, seq_off, t, l, bg, pwm, C, iters, beta, 0.0, ll, lse, trace, nthreads);
+}
+
+/* ZOOPS EM (em_one_zoops) for C starting models; 0 < gamma <= 1. */
+int orc_em_zoops(const uint8_t *codes, const int64_t *seq_off, int t, int l, const double bg[4],
+                 double *pwm, int64_t C, int iters, double beta, double gamma, double *ll,
+                 double *trace, int nthreads) {
+    if (!(gamma > 0.0 && gamma <= 1.0)) return -1;
+    return em_run(codes, seq_off, t, l, bg, pwm, C, iters, beta, gamma, ll, NULL, trace, nthreads);
 }
 
 /* Predicted sites: for each sequence the first start maximising r(i,j)

@@ -174,3 +174,83 @@ def test_default_params():
     # twice the mean bucket size when that exceeds 3
     k, s, m = O.default_params([5000] * 20, 8, 2, k=4)
     assert s == math.ceil(2 * 20 * (5000 - 8 + 1) / 4 ** 4)
+
+
+# ---------------------------------------------------------------------------
+# ZOOPS (zero or one occurrence per sequence, reading R15)
+# ---------------------------------------------------------------------------
+
+def _mixture_ll_and_posteriors(seqs, pwm, bg, gamma):
+    """Brute force in probability space: for each sequence the mixture
+    P(seq) = (1-gamma) prod_b bg(x_b) + sum_j gamma/ns prod_{b not in site} bg(x_b)
+    prod_p pwm_p(x_{j+p}), its ratio to the all-background probability, and
+    the posterior of each site by Bayes' rule on the joint probabilities."""
+    l = pwm.shape[0]
+    ll, post = 0.0, []
+    for q in seqs:
+        x = [IDX[c] for c in q]
+        ns = len(q) - l + 1
+        p_bg = math.prod(bg[a] for a in x)
+        joint_site = []
+        for j in range(ns):
+            pr = gamma / ns
+            for b, a in enumerate(x):
+                pr *= pwm[b - j, a] if j <= b < j + l else bg[a]
+            joint_site.append(pr)
+        total = (1 - gamma) * p_bg + sum(joint_site)
+        ll += math.log(total / p_bg)
+        post.append([js / total for js in joint_site])
+    return ll, post
+
+
+@pytest.mark.parametrize("gamma", [0.3, 0.8, 1.0])
+def test_zoops_matches_mixture_brute_force(gamma):
+    """Log-likelihood ratio and one M-step of the ZOOPS oracle against the
+    mixture written out in probability space on a tiny input."""
+    rng = np.random.default_rng(11)
+    l, beta = 4, 0.25
+    seqs = ["".join("ACGT"[c] for c in rng.integers(0, 4, n)) for n in (6, 4, 9, 5)]
+    codes, off = _setup(seqs)
+    bg = O.background(codes)
+    pwm0 = _random_pwm(rng, l)
+    want_ll, post = _mixture_ll_and_posteriors(seqs, pwm0, bg, gamma)
+    _, ll0 = O.em_zoops(codes, off, l, bg, pwm0[None], 0, beta, gamma)
+    assert ll0[0] == pytest.approx(want_ll, rel=1e-12, abs=1e-12)
+    cnt = np.zeros((l, 4))
+    ztot = 0.0
+    for q, zq in zip(seqs, post):
+        for j, z in enumerate(zq):
+            ztot += z
+            for p in range(l):
+                cnt[p, IDX[q[j + p]]] += z
+    pwm1, _ = O.em_zoops(codes, off, l, bg, pwm0[None], 1, beta, gamma)
+    assert np.allclose(pwm1[0], (cnt + beta) / (ztot + 4 * beta), rtol=0, atol=1e-13)
+
+
+def test_zoops_with_gamma_one_is_oops():
+    inst = planted_instance(21, 0, 10, 150, 9, 2)
+    codes = O.encode(inst.ascii)
+    bg = O.background(codes)
+    pwm0 = _random_pwm(np.random.default_rng(5), 9)[None]
+    a = O.em(codes, inst.seq_off, 9, bg, pwm0, 4, 0.25)
+    b = O.em_zoops(codes, inst.seq_off, 9, bg, pwm0, 4, 0.25, 1.0)
+    assert np.allclose(a[0], b[0], rtol=0, atol=1e-12)
+    assert b[1][0] == pytest.approx(a[1][0], rel=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_zoops_map_objective_non_decreasing(seed):
+    """EM on the ZOOPS mixture with a Dirichlet(1+beta) prior: LL + beta *
+    sum log theta never decreases; columns sum to one."""
+    inst = planted_instance(200 + seed, 0, 12, 140, 9, 2, zoops_frac=0.5)
+    codes = O.encode(inst.ascii)
+    bg = O.background(codes)
+    pwm = _random_pwm(np.random.default_rng(seed), 9)
+    prev = -np.inf
+    for it in range(10):
+        ll = O.em_zoops(codes, inst.seq_off, 9, bg, pwm[None], 0, 0.25, 0.5)[1][0]
+        obj = ll + 0.25 * np.log(pwm).sum()
+        assert obj >= prev - 1e-9 * max(1.0, abs(prev))
+        prev = obj
+        pwm = O.em_zoops(codes, inst.seq_off, 9, bg, pwm[None], 1, 0.25, 0.5)[0][0]
+        assert np.allclose(pwm.sum(axis=1), 1.0, atol=1e-12)
