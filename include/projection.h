@@ -181,6 +181,20 @@ int em_refine(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
               float pseudocount, int precision, float *theta_out_dev, double *loglik_dev,
               void *stream);
 
+/* The same refinement under the zero-or-one-occurrence model (ZOOPS, the
+ * second search model named in Section 2): a sequence holds one site with
+ * probability site_prob (fixed, 0 < site_prob <= 1), uniform over its starts,
+ * or none.  Per sequence i with ns_i starts the log-likelihood ratio is
+ *     L_i = log[(1 - site_prob) + (site_prob / ns_i) sum_j e^{r(i,j)}],
+ * the posterior of a site at j is (site_prob / ns_i) e^{r(i,j)} / e^{L_i}, and the
+ * M-step is theta_p(a) = (sum z [x = a] + pseudocount) / (sum z + 4 pseudocount).
+ * site_prob = 1 is the OOPS model of em_refine (up to rounding).  Arguments,
+ * layouts and errors as em_refine; EINVAL for site_prob outside (0, 1]. */
+int em_refine_zoops(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
+                    const double *bg_dev, const float *theta0_dev, int64_t C, int em_iters,
+                    float pseudocount, int precision, double site_prob, float *theta_out_dev,
+                    double *loglik_dev, void *stream);
+
 /* ---- step a9: rank and finalise ----------------------------------------- */
 
 /* Picks the best candidate (largest loglik, FP64; a tie goes to the smaller
@@ -244,6 +258,16 @@ int projection_find_packed_top(const uint32_t *packed_dev, const int64_t *seq_of
                                int d, int k, int s, int m, uint64_t seed, int em_iters,
                                float pseudocount, int precision, int64_t top,
                                projection_result *out, void *stream);
+
+/* projection_find_packed_top with the EM of em_refine_zoops (site_prob in
+ * (0, 1]; top = 0 refines every enriched bucket).  Sites are reported as in
+ * the OOPS search: per sequence the first start of highest score under the
+ * winning model (a caller that wants "no site" decisions thresholds the
+ * posterior itself). */
+int projection_find_packed_zoops(const uint32_t *packed_dev, const int64_t *seq_off, int t,
+                                 int l, int d, int k, int s, int m, uint64_t seed, int em_iters,
+                                 float pseudocount, int precision, double site_prob, int64_t top,
+                                 projection_result *out, void *stream);
 
 /* Batched serving: n_inst independent searches in one call.  Instance i owns
  * sequences inst_seq[i] .. inst_seq[i+1]-1 of the linear input (ascii,

@@ -263,6 +263,37 @@ def projection_find_top(ascii, seq_off, l, d, k=0, s=0, m=0, seed=0, em_iters=5,
         lib().projection_result_free(ctypes.byref(r))
 
 
+def em_refine_zoops(packed, seq_off, l, bg, theta0, em_iters, pseudocount, site_prob,
+                    precision=PROJ_EM_FP32, out=None, stream=None):
+    """ZOOPS EM (site probability `site_prob` per sequence) from theta0 [C, l, 4]
+    (float32 CUDA).  Returns (theta [C, l, 4] float32, loglik [C] float64)."""
+    off = _off(seq_off)
+    C = theta0.shape[0]
+    theta0 = theta0.contiguous()
+    th = torch.empty_like(theta0) if out is None else out
+    ll = _dev(max(1, C), torch.float64, theta0.device)
+    check(lib().em_refine_zoops(_ptr(packed), _ptr(off), off.size - 1, l, _ptr(bg), _ptr(theta0),
+                                C, em_iters, float(pseudocount), precision, float(site_prob),
+                                _ptr(th), _ptr(ll), _stream(stream)))
+    return th, ll[:C]
+
+
+def projection_find_packed_zoops(packed, seq_off, l, d, k=0, s=0, m=0, seed=0, em_iters=5,
+                                 pseudocount=0.25, precision=PROJ_EM_FP32, site_prob=0.5, top=0,
+                                 stream=None) -> dict:
+    off = _off(seq_off)
+    r = ProjectionResult()
+    rc = lib().projection_find_packed_zoops(_ptr(packed), _ptr(off), off.size - 1, l, d, k, s, m,
+                                            seed & (2**64 - 1), em_iters, float(pseudocount),
+                                            precision, float(site_prob), int(top), ctypes.byref(r),
+                                            _stream(stream))
+    try:
+        check(rc)
+        return _result_dict(r)
+    finally:
+        lib().projection_result_free(ctypes.byref(r))
+
+
 def projection_find_packed_top(packed, seq_off, l, d, k=0, s=0, m=0, seed=0, em_iters=5,
                                pseudocount=0.25, precision=PROJ_EM_FP32, top=0,
                                stream=None) -> dict:

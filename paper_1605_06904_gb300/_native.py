@@ -49,6 +49,10 @@ SIGNATURES = {
                             P, P, P, P], i32),
     "theta0_build": ([P, P, i32, i32, P, P, i64, f32, P, P], i32),
     "em_refine": ([P, P, i32, i32, P, P, i64, i32, f32, i32, P, P, P], i32),
+    "em_refine_zoops": ([P, P, i32, i32, P, P, i64, i32, f32, i32, ctypes.c_double, P, P, P], i32),
+    "projection_find_packed_zoops": ([P, P, i32, i32, i32, i32, i32, i32, u64, i32, f32, i32,
+                                      ctypes.c_double, i64, ctypes.POINTER(ProjectionResult), P],
+                                     i32),
     "projection_finalize": ([P, P, i32, i32, P, P, P, i64, P, P, P, P, P], i32),
     "projection_find": ([P, P, i32, i32, i32, i32, i32, i32, u64, i32, f32, i32,
                          ctypes.POINTER(ProjectionResult), P], i32),

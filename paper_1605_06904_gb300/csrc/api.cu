@@ -248,6 +248,22 @@ int em_refine(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
                   theta_out_dev, loglik_dev, st);
 }
 
+int em_refine_zoops(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
+                    const double *bg_dev, const float *theta0_dev, int64_t C, int em_iters,
+                    float pseudocount, int precision, double site_prob, float *theta_out_dev,
+                    double *loglik_dev, void *stream) {
+    clear_error();
+    cudaStream_t st = (cudaStream_t)stream;
+    PROJ_REQUIRE(C >= 0, "need C >= 0");
+    PROJ_REQUIRE(site_prob > 0.0 && site_prob <= 1.0, "need 0 < site_prob <= 1");
+    PROJ_REQUIRE(C == 0 || (packed_dev && bg_dev && theta0_dev && theta_out_dev && loglik_dev),
+                 "NULL buffer");
+    Layout L;
+    PROJ_TRY(make_layout(seq_off, t, l, st, L));
+    return run_em(packed_dev, L, bg_dev, theta0_dev, C, em_iters, pseudocount, precision,
+                  theta_out_dev, loglik_dev, st, site_prob);
+}
+
 int projection_finalize(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
                         const double *bg_dev, const float *theta_dev, const double *loglik_dev,
                         int64_t C, int64_t *best_dev, int32_t *sites_dev, uint8_t *consensus_dev,
@@ -265,7 +281,7 @@ int projection_finalize(const uint32_t *packed_dev, const int64_t *seq_off, int 
 
 static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int l, int d, int k,
                      int s, int m, uint64_t seed, int em_iters, float pseudocount, int precision,
-                     int64_t top, projection_result *out, cudaStream_t st) {
+                     int64_t top, projection_result *out, cudaStream_t st, double gamma = 1.0) {
     PROJ_REQUIRE(packed != nullptr, "packed input must not be NULL");
     PROJ_REQUIRE(d >= 0 && d < l, "need 0 <= d < l");
     Layout L;
@@ -345,7 +361,7 @@ static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int 
     double *ll = model.as<double>();
     float *theta = reinterpret_cast<float *>(ll + R);
     PROJ_TRY(launch_theta0(packed, L, r_off, r_members, R, pseudocount, theta, st));
-    PROJ_TRY(run_em(packed, L, bg, theta, R, em_iters, pseudocount, precision, theta, ll, st));
+    PROJ_TRY(run_em(packed, L, bg, theta, R, em_iters, pseudocount, precision, theta, ll, st, gamma));
     PROJ_TRY(launch_finalize(packed, L, bg, theta, ll, R, best, sites, cons, score, st));
 
     int64_t b = -1;
@@ -410,6 +426,24 @@ int projection_find_packed_top(const uint32_t *packed_dev, const int64_t *seq_of
     if (top < 0) { set_error("top must be >= 0"); out->status = PROJ_EINVAL; return PROJ_EINVAL; }
     const int rc = find_impl(packed_dev, seq_off, t, l, d, k, s, m, seed, em_iters, pseudocount,
                              precision, top, out, (cudaStream_t)stream);
+    out->status = rc;
+    return rc;
+}
+
+int projection_find_packed_zoops(const uint32_t *packed_dev, const int64_t *seq_off, int t,
+                                 int l, int d, int k, int s, int m, uint64_t seed, int em_iters,
+                                 float pseudocount, int precision, double site_prob, int64_t top,
+                                 projection_result *out, void *stream) {
+    clear_error();
+    if (!out) { set_error("out must not be NULL"); return PROJ_EINVAL; }
+    result_init(out);
+    if (top < 0 || !(site_prob > 0.0 && site_prob <= 1.0)) {
+        set_error("need top >= 0 and 0 < site_prob <= 1");
+        out->status = PROJ_EINVAL;
+        return PROJ_EINVAL;
+    }
+    const int rc = find_impl(packed_dev, seq_off, t, l, d, k, s, m, seed, em_iters, pseudocount,
+                             precision, top, out, (cudaStream_t)stream, site_prob);
     out->status = rc;
     return rc;
 }
@@ -615,6 +649,7 @@ int projection_find_batch(const uint8_t *ascii, const int64_t *seq_off, const in
         eh[i].seq_off = offs.data() + off_pos[i] + 2 * (t + 1);  // global positions
         ei[i].seq_off = bi[i].seq_off; ei[i].bg = bi[i].bg; ei[i].t = t; ei[i].l = l[i];
         ei[i].cand_begin = H.cand_begin[i];
+        ei[i].gamma = 1.0;  // OOPS
         out[i].n_candidates = H.n_cand[i];
         out[i].n_members = H.n_mem[i];
     }

@@ -177,7 +177,7 @@ int launch_theta0(const uint32_t *packed, const Layout &L, const int64_t *cand_o
 
 int run_em(const uint32_t *packed, const Layout &L, const double *bg, const float *theta0,
            int64_t C, int iters, float beta, int precision, float *theta_out, double *ll,
-           cudaStream_t st);
+           cudaStream_t st, double gamma = 1.0);
 
 int launch_finalize(const uint32_t *packed, const Layout &L, const double *bg,
                     const float *theta, const double *ll, int64_t C, int64_t *best,

@@ -20,7 +20,8 @@
 namespace proj {
 
 int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const float *theta0,
-              int64_t C, int iters, float beta, float *theta_out, double *ll, cudaStream_t st);
+              int64_t C, int iters, float beta, float *theta_out, double *ll, cudaStream_t st,
+              double gamma);
 
 namespace {
 
@@ -77,9 +78,17 @@ struct EmParams {
     const float *theta_in;
     double *part_acc;   // [G][C][4l] normalised counts of this group's sequences
     double *part_ll;    // [G][C]
+    double *part_zs;    // [G][C] expected number of sites (ZOOPS)
     int64_t C;
     int mstep;
+    double gamma;       // site probability per sequence: < 1 ZOOPS, 1 OOPS
 };
+
+// log(e^a + e^b) in FP64 (a may be -inf).
+__device__ __forceinline__ double log_add_d(double a, double b) {
+    const double hi = fmax(a, b), lo = fmin(a, b);
+    return hi == -INFINITY ? -INFINITY : hi + log1p(exp(lo - hi));
+}
 
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float v) {
     const float y = v - comp;
@@ -109,7 +118,7 @@ __global__ void __launch_bounds__(kEmThreads) em_fp32_kernel(const EmParams P) {
         Ws[q * NT + tid] = valid ? logf(P.theta_in[c * L4 + q]) - lbg[q & 3] : 0.f;
         if (valid && P.mstep) tot[q] = 0.0;
     }
-    double ll = 0.0;
+    double ll = 0.0, zs = 0.0;
     const int i0 = (int)((int64_t)P.t * g / P.G), i1 = (int)((int64_t)P.t * (g + 1) / P.G);
     for (int i = i0; i < i1; ++i) {
         const int64_t base = P.seq_off[i];
@@ -154,27 +163,45 @@ __global__ void __launch_bounds__(kEmThreads) em_fp32_kernel(const EmParams P) {
             }
         }
         const double Sd = (double)S - (double)Sc;
-        ll += (double)m + log(Sd) - log((double)ns);
+        double w = 1.0;  // posterior probability that the sequence holds a site
+        if (P.gamma < 1.0) {
+            // ZOOPS: L_i = log[(1 - gamma) + (gamma / ns) sum_j e^r]
+            const double lg = log(P.gamma / (double)ns) + (double)m + log(Sd);
+            const double Li = log_add_d(log1p(-P.gamma), lg);
+            w = exp(lg - Li);
+            ll += Li;
+        } else {
+            ll += (double)m + log(Sd) - log((double)ns);
+        }
+        zs += w;
         if (P.mstep && valid) {
-            const double inv = 1.0 / Sd;
+            const double inv = w / Sd;
             for (int q = 0; q < L4; ++q)
                 tot[q] += ((double)acc[q * NT + tid] - (double)cmp[q * NT + tid]) * inv;
         }
     }
-    if (valid) P.part_ll[(int64_t)g * P.C + c] = ll;
+    if (valid) {
+        P.part_ll[(int64_t)g * P.C + c] = ll;
+        P.part_zs[(int64_t)g * P.C + c] = zs;
+    }
 }
 
 // Sum of the G partial results in group order (fixed, so deterministic), then
 // the M-step theta = (counts + pseudocount) / (t + 4 pseudocount).
 __global__ void em_reduce_kernel(const double *__restrict__ part_acc,
-                                 const double *__restrict__ part_ll, int G, int64_t C, int L4,
-                                 int t, float beta, int mstep, float *__restrict__ theta_out,
-                                 double *__restrict__ ll_out) {
+                                 const double *__restrict__ part_ll,
+                                 const double *__restrict__ part_zs, int zoops, int G, int64_t C,
+                                 int L4, int t, float beta, int mstep,
+                                 float *__restrict__ theta_out, double *__restrict__ ll_out) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (mstep && idx < C * L4) {
-        double s = 0.0;
+        double s = 0.0, sites = (double)t;  // OOPS: one site per sequence
         for (int g = 0; g < G; ++g) s += part_acc[(int64_t)g * C * L4 + idx];
-        theta_out[idx] = (float)((s + (double)beta) / ((double)t + 4.0 * (double)beta));
+        if (zoops) {
+            sites = 0.0;
+            for (int g = 0; g < G; ++g) sites += part_zs[(int64_t)g * C + idx / L4];
+        }
+        theta_out[idx] = (float)((s + (double)beta) / (sites + 4.0 * (double)beta));
     }
     if (idx < C) {
         double s = 0.0;
@@ -435,14 +462,15 @@ int launch_theta0(const uint32_t *packed, const Layout &L, const int64_t *cand_o
 
 int run_em(const uint32_t *packed, const Layout &L, const double *bg, const float *theta0,
            int64_t C, int iters, float beta, int precision, float *theta_out, double *ll,
-           cudaStream_t st) {
+           cudaStream_t st, double gamma) {
     PROJ_REQUIRE(iters >= 0 && iters <= 1000, "em_iters out of range: %d", iters);
     PROJ_REQUIRE(beta > 0.f, "pseudocount must be > 0");
     PROJ_REQUIRE(precision == PROJ_EM_FP32 || precision == PROJ_EM_BF16_SPLIT,
                  "unknown precision %d", precision);
     if (C == 0) return PROJ_OK;
+    PROJ_REQUIRE(gamma > 0.0 && gamma <= 1.0, "site probability must be in (0, 1]");
     if (precision == PROJ_EM_BF16_SPLIT)
-        return run_em_tc(packed, L, bg, theta0, C, iters, beta, theta_out, ll, st);
+        return run_em_tc(packed, L, bg, theta0, C, iters, beta, theta_out, ll, st, gamma);
 
     const int L4 = 4 * L.l;
     // enough (candidate-tile, sequence-group) units to fill every SM a few times
@@ -450,7 +478,7 @@ int run_em(const uint32_t *packed, const Layout &L, const double *bg, const floa
     const int64_t want = (int64_t)sm_count() * 8;
     const int G = (int)std::min<int64_t>(L.t, std::max<int64_t>(1, (want + tiles - 1) / tiles));
     DevBuf part;
-    PROJ_TRY(part.alloc((size_t)G * C * (L4 + 1) * sizeof(double), st));
+    PROJ_TRY(part.alloc((size_t)G * C * (L4 + 2) * sizeof(double), st));
     DevBuf tmp;  // model of the current iteration (theta_out may alias theta0)
     PROJ_TRY(tmp.alloc((size_t)C * L4 * sizeof(float), st));
     PROJ_CUDA_TRY(cudaMemcpyAsync(tmp.as<float>(), theta0, (size_t)C * L4 * sizeof(float),
@@ -466,7 +494,9 @@ int run_em(const uint32_t *packed, const Layout &L, const double *bg, const floa
     P.bg = bg;
     P.C = C;
     P.part_ll = part.as<double>();
-    P.part_acc = part.as<double>() + (size_t)G * C;
+    P.part_zs = part.as<double>() + (size_t)G * C;
+    P.part_acc = part.as<double>() + (size_t)2 * G * C;
+    P.gamma = gamma;
     P.theta_in = tmp.as<float>();
     for (int it = 0; it <= iters; ++it) {
         P.mstep = it < iters;
@@ -480,7 +510,8 @@ int run_em(const uint32_t *packed, const Layout &L, const double *bg, const floa
         {
             TraceSpan ts_("em_reduce", st);
             em_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-                P.part_acc, P.part_ll, G, C, L4, L.t, beta, P.mstep, tmp.as<float>(), ll);
+                P.part_acc, P.part_ll, P.part_zs, gamma < 1.0 ? 1 : 0, G, C, L4, L.t, beta,
+                P.mstep, tmp.as<float>(), ll);
         }
         PROJ_LAUNCH_CHECK("em_reduce_kernel");
     }

@@ -16,6 +16,7 @@ struct EmInst {
     const double *bg;        // [4] its background frequencies
     int t, l;
     int64_t cand_begin;      // index of its first candidate in the candidate arrays
+    double gamma;            // site probability per sequence: < 1 ZOOPS, 1 OOPS
 };
 
 // One unit of EM work: up to 128 candidates of one instance against one

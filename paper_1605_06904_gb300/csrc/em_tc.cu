@@ -65,6 +65,7 @@ struct EmTcParams {
     int stride;             // floats per candidate model (>= 4l of its instance)
     double *part_acc;       // [G][C][stride]; G == 1 when no candidate tile is split
     double *part_ll;        // [G][C]
+    double *part_zs;        // [G][C] expected number of sites (ZOOPS)
     int64_t C;
     int mstep;
     int G;                  // items per candidate tile (consecutive in the item list)
@@ -105,6 +106,12 @@ __device__ __forceinline__ float ex2(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// log(e^a + e^b) in FP64 (a may be -inf).
+__device__ __forceinline__ double log_add(double a, double b) {
+    const double hi = fmax(a, b), lo = fmin(a, b);
+    return hi == -INFINITY ? -INFINITY : hi + log1p(exp(lo - hi));
 }
 
 __device__ __forceinline__ void kahan(float &sum, float &comp, float v) {
@@ -436,7 +443,7 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
             float tot[KH];  // this item's normalised counts of candidate c, columns of this half
 #pragma unroll
             for (int q = 0; q < KH; ++q) tot[q] = 0.f;
-            double ll = 0.0;
+            double ll = 0.0, zs = 0.0;  // zs: expected number of sites (ZOOPS)
             float m = -INFINITY, Ssum = 0.f, Scmp = 0.f;
             bool first = true;
             o_base = o_waited;  // every count MMA of earlier items was waited for
@@ -528,11 +535,22 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                 if (tcur.last()) {
                     const float Sh = Ssum - Scmp;
                     const float Sf = Sh + exchange(Sh);
-                    ll += (double)((m + log2f(Sf)) * 0.69314718f - logf((float)tcur.ns));
+                    float w = 1.f;  // posterior probability that the sequence holds a site
+                    if (in.gamma < 1.0) {
+                        // ZOOPS: L_i = log[(1 - gamma) + (gamma / ns) sum_j e^r]
+                        const double lg = log(in.gamma / (double)tcur.ns) +
+                                          ((double)m + (double)log2f(Sf)) * 0.6931471805599453;
+                        const double Li = log_add(log1p(-in.gamma), lg);
+                        w = (float)exp(lg - Li);
+                        ll += Li;
+                    } else {
+                        ll += (double)((m + log2f(Sf)) * 0.69314718f - logf((float)tcur.ns));
+                    }
+                    zs += (double)w;
                     if (P.mstep) {
                         wait_o((uint32_t)i + 1);
                         tc::fence_after_sync();
-                        const float inv = 1.f / Sf;
+                        const float inv = w / Sf;
 #pragma unroll
                         for (int c8 = 0; c8 < KH; c8 += 8) {
                             float o[8];
@@ -553,7 +571,7 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                 // the item covers every sequence: final values directly
                 if (half == 0) P.ll_out[c] = ll;
                 if (P.mstep) {
-                    const double den = (double)in.t + 4.0 * (double)P.beta;
+                    const double den = (in.gamma < 1.0 ? zs : (double)in.t) + 4.0 * (double)P.beta;
                     float *dst = P.theta_out + c * P.stride + half * KH;
 #pragma unroll
                     for (int q = 0; q < KH; ++q)
@@ -561,7 +579,10 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                             dst[q] = (float)(((double)tot[q] + (double)P.beta) / den);
                 }
             } else if (ok && valid) {
-                if (half == 0) P.part_ll[(int64_t)item.g * P.C + c] = ll;
+                if (half == 0) {
+                    P.part_ll[(int64_t)item.g * P.C + c] = ll;
+                    P.part_zs[(int64_t)item.g * P.C + c] = zs;
+                }
                 if (P.mstep) {
                     double *dst = P.part_acc + ((int64_t)item.g * P.C + c) * P.stride + half * KH;
 #pragma unroll
@@ -584,7 +605,6 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
         if (fold && s_last) {
             __threadfence();
             const int width = P.mstep ? L4 : 0;
-            const double den = (double)in.t + 4.0 * (double)P.beta;
             for (int e = tid; e < item.nc * (width + 1); e += kTcThreads) {
                 const int cc = e / (width + 1), q = e - cc * (width + 1);
                 const int64_t cg = item.c0 + cc;
@@ -592,7 +612,13 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                 if (q < width) {
                     for (int g = 0; g < P.G; ++g)
                         acc += __ldcg(P.part_acc + ((int64_t)g * P.C + cg) * P.stride + q);
-                    P.theta_out[cg * P.stride + q] = (float)((acc + (double)P.beta) / den);
+                    double sites = (double)in.t;  // OOPS: one site per sequence
+                    if (in.gamma < 1.0) {
+                        sites = 0.0;
+                        for (int g = 0; g < P.G; ++g) sites += __ldcg(P.part_zs + (int64_t)g * P.C + cg);
+                    }
+                    P.theta_out[cg * P.stride + q] =
+                        (float)((acc + (double)P.beta) / (sites + 4.0 * (double)P.beta));
                 } else {
                     for (int g = 0; g < P.G; ++g) acc += __ldcg(P.part_ll + (int64_t)g * P.C + cg);
                     P.ll_out[cg] = acc;
@@ -617,7 +643,8 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
 // log-likelihood sum over the G sequence groups, in group order (used when G
 // is above kFoldMaxG).
 __global__ void em_tc_reduce_kernel(const double *__restrict__ part_acc,
-                                    const double *__restrict__ part_ll, int G, int64_t C,
+                                    const double *__restrict__ part_ll,
+                                    const double *__restrict__ part_zs, int G, int64_t C,
                                     int stride, const EmInst *__restrict__ inst, int n_inst,
                                     float beta, int mstep, float *__restrict__ theta_out,
                                     double *__restrict__ ll_out) {
@@ -632,9 +659,13 @@ __global__ void em_tc_reduce_kernel(const double *__restrict__ part_acc,
         if (inst[mid].cand_begin <= (int64_t)c) lo = mid; else hi = mid - 1;
     }
     if (mstep && (int)q < 4 * inst[lo].l) {
-        double s = 0.0;
+        double s = 0.0, sites = (double)inst[lo].t;  // OOPS: one site per sequence
         for (int g = 0; g < G; ++g) s += part_acc[((int64_t)g * C + c) * stride + q];
-        theta_out[idx] = (float)((s + (double)beta) / ((double)inst[lo].t + 4.0 * (double)beta));
+        if (inst[lo].gamma < 1.0) {
+            sites = 0.0;
+            for (int g = 0; g < G; ++g) sites += part_zs[(int64_t)g * C + c];
+        }
+        theta_out[idx] = (float)((s + (double)beta) / (sites + 4.0 * (double)beta));
     }
     if (q == 0) {
         double s = 0.0;
@@ -821,7 +852,7 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
         em_tc_plan(insts, items, G, sched.ctas, sched.waves);
         Gmax = std::max(Gmax, G);
     }
-    PROJ_TRY(run.part.alloc((size_t)Gmax * C * (stride + 1) * sizeof(double), st));
+    PROJ_TRY(run.part.alloc((size_t)Gmax * C * (stride + 2) * sizeof(double), st));
     PROJ_TRY(run.tmp.alloc((size_t)C * stride * sizeof(float), st));
     PROJ_TRY(run.flag.alloc(sizeof(int), st));
     PROJ_CUDA_TRY(cudaMemsetAsync(run.flag.as<int>(), 0, sizeof(int), st));
@@ -852,7 +883,8 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
             EmTcParams P{};
             P.packed = packed; P.nwords = nwords; P.inst = inst_dev; P.items = ib.as<EmItem>();
             P.n_items = (int)items.size(); P.theta_in = run.tmp.as<float>(); P.stride = stride;
-            P.part_ll = run.part.as<double>(); P.part_acc = run.part.as<double>() + (size_t)G * C;
+            P.part_ll = run.part.as<double>(); P.part_zs = run.part.as<double>() + (size_t)G * C;
+            P.part_acc = run.part.as<double>() + (size_t)2 * G * C;
             P.C = C; P.err = run.flag.as<int>(); P.mstep = 1; P.G = G; P.beta = 0.25f;
             P.theta_out = run.tmp.as<float>(); P.ll_out = ll_scratch.as<double>();
             P.tile_done = run.tiles.as<uint32_t>();
@@ -863,7 +895,8 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
             if (G > kFoldMaxG) {  // the separate fold is part of this schedule's cost
                 const int64_t nq = C * stride;
                 em_tc_reduce_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(
-                    P.part_acc, P.part_ll, G, C, stride, inst_dev, (int)insts.size(), P.beta, 1,
+                    P.part_acc, P.part_ll, P.part_zs, G, C, stride, inst_dev, (int)insts.size(),
+                    P.beta, 1,
                     run.tmp.as<float>(), ll_scratch.as<double>());
                 PROJ_LAUNCH_CHECK("em_tc_reduce_kernel");
             }
@@ -909,7 +942,8 @@ int em_tc_enqueue(EmTcRun &run, int iters, float beta, float *theta_out, double 
     P.theta_in = run.tmp.as<float>();
     P.stride = stride;
     P.part_ll = run.part.as<double>();
-    P.part_acc = run.part.as<double>() + (size_t)G * C;
+    P.part_zs = run.part.as<double>() + (size_t)G * C;
+    P.part_acc = run.part.as<double>() + (size_t)2 * G * C;
     P.C = C;
     P.G = G;
     P.beta = beta;
@@ -927,7 +961,8 @@ int em_tc_enqueue(EmTcRun &run, int iters, float beta, float *theta_out, double 
             {
                 TraceSpan ts_("em_reduce", st);
                 em_tc_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-                    P.part_acc, P.part_ll, G, C, stride, run.inst_dev, run.n_inst, beta, P.mstep,
+                    P.part_acc, P.part_ll, P.part_zs, G, C, stride, run.inst_dev, run.n_inst, beta,
+                    P.mstep,
                     run.tmp.as<float>(), ll);
             }
             PROJ_LAUNCH_CHECK("em_tc_reduce_kernel");
@@ -963,7 +998,8 @@ int run_em_tc_batch(const uint32_t *packed, int64_t nwords, const std::vector<Em
 }
 
 int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const float *theta0,
-              int64_t C, int iters, float beta, float *theta_out, double *ll, cudaStream_t st) {
+              int64_t C, int iters, float beta, float *theta_out, double *ll, cudaStream_t st,
+              double gamma) {
     std::vector<EmInstHost> insts(1);
     insts[0].t = L.t;
     insts[0].l = L.l;
@@ -977,6 +1013,7 @@ int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const f
     in.l = L.l;
     in.bg = bg;
     in.cand_begin = 0;
+    in.gamma = gamma;
     DevBuf ib;
     PROJ_TRY(ib.alloc(sizeof(EmInst), st));
     PROJ_CUDA_TRY(cudaMemcpyAsync(ib.as<EmInst>(), &in, sizeof(EmInst), cudaMemcpyHostToDevice, st));
