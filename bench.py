@@ -156,7 +156,8 @@ def peaks():
         return {"hbm_gbs": FALLBACK_HBM_GBS, "bf16_tflops": FALLBACK_BF16_TFLOPS}, "fallback"
 
 
-def em_error_report(P, inst, packed, k, s, seed, iters, beta, dev, n_sample=16, trials=2):
+def em_error_report(P, inst, packed, k, s, seed, iters, beta, dev, n_sample=16, trials=2,
+                    site_prob=None):
     """Errors of both EM precisions against the FP64 oracle from identical
     starting models: theta^0 of the n_sample largest buckets of the first
     `trials` trials, hashed and built by the oracle (inputs of the GPU leg are
@@ -170,13 +171,21 @@ def em_error_report(P, inst, packed, k, s, seed, iters, beta, dev, n_sample=16, 
     sel = O.top_candidates(h["cand_cnt"], n_sample)
     th0 = np.stack([O.theta0(codes, off, inst.l, h["members"][h["cand_off"][c]:h["cand_off"][c + 1]],
                              beta) for c in sel]).astype(np.float32)
-    w_pwm, w_ll = O.em(codes, off, inst.l, O.background(codes), th0.astype(np.float64), iters,
-                       beta, nthreads=os.cpu_count() or 1)
+    if site_prob is None:
+        w_pwm, w_ll = O.em(codes, off, inst.l, O.background(codes), th0.astype(np.float64), iters,
+                           beta, nthreads=os.cpu_count() or 1)
+    else:
+        w_pwm, w_ll = O.em_zoops(codes, off, inst.l, O.background(codes), th0.astype(np.float64),
+                                 iters, beta, site_prob, nthreads=os.cpu_count() or 1)
     bg = P.projection_background(packed, off[-1])
     out = {}
     for name, prec in (("bf16_split", P.PROJ_EM_BF16_SPLIT), ("fp32", P.PROJ_EM_FP32)):
-        g_pwm, g_ll = P.em_refine(packed, off, inst.l, bg, torch.from_numpy(th0).to(dev), iters,
-                                  beta, prec)
+        t0 = torch.from_numpy(th0).to(dev)
+        if site_prob is None:
+            g_pwm, g_ll = P.em_refine(packed, off, inst.l, bg, t0, iters, beta, prec)
+        else:
+            g_pwm, g_ll = P.em_refine_zoops(packed, off, inst.l, bg, t0, iters, beta, site_prob,
+                                            prec)
         g_pwm, g_ll = g_pwm.cpu().numpy(), g_ll.cpu().numpy()
         out[name] = {"pwm_max_abs": float(np.abs(g_pwm - w_pwm).max()),
                      "ll_max_rel": float((np.abs(g_ll - w_ll) /
@@ -387,6 +396,10 @@ def run_top(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step(prec):
+        if args.zoops:
+            return P.projection_find_packed_zoops(packed, off, inst.l, inst.d, k, s, m, seed=seed,
+                                                  em_iters=iters, pseudocount=beta,
+                                                  precision=prec, site_prob=args.zoops, top=top)
         return P.projection_find_packed_top(packed, off, inst.l, inst.d, k, s, m, seed=seed,
                                             em_iters=iters, pseudocount=beta, precision=prec,
                                             top=top)
@@ -426,7 +439,8 @@ def run_top(args):
     scores = x * R * (iters + 1)
 
     errs, n_err = em_error_report(P, inst, packed, k, s, seed, iters, beta, dev,
-                                  n_sample=args.err_sample, trials=1)
+                                  n_sample=args.err_sample, trials=1,
+                                  site_prob=args.zoops or None)
     pk, pk_kind = peaks()
     flops = args.steps * x * R * (iters * 16 * inst.l + 8 * inst.l)
     achieved = flops / (em_ms / 1e3) / 1e12 if em_ms > 0 else None
@@ -436,7 +450,9 @@ def run_top(args):
         "warmup": args.warmup, "ms_per_step": T * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16-split", "data": "synthetic",
         "config": {"workload": f"markov-gc40 zoops(20,5) t=2000 n=500 k=10 s=4 m={m} top=1024 "
-                               "em_iters=10 pseudocount=0.25", "config_index": 5,
+                               "em_iters=10 pseudocount=0.25"
+                               + (f" em_model=zoops(site_prob={args.zoops})" if args.zoops
+                                  else " em_model=oops"), "config_index": 5,
                    "x_lmers": x, "l2": "flushed between steps (512 MB write)"},
         "hashes_per_s": m * x / T, "hash_ms_per_step": hash_ms / args.steps,
         "ms_per_step_by_phase": phases,
@@ -477,6 +493,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-inst", type=int, default=256)
     ap.add_argument("--err-sample", type=int, default=16)
+    ap.add_argument("--zoops", type=float, default=0.0,
+                    help="config 5 only: refine with the ZOOPS EM at this site probability")
     ap.add_argument("--trials", type=int, default=0,
                     help="config 5 only: hash this many trials instead of 500 (profiling)")
     args = ap.parse_args()
