@@ -622,6 +622,20 @@ def main():
                  "avg_launch_ms": hc_ms / max(1, hc_launches),
                  "peak_source": f"projection_hist_peak({k}) measured in this run"}
 
+    # ---- the low-memory all-pairs enrichment on the same trials (no 4^k table):
+    # x^2 key comparisons per trial, against the histogram path's count + fill
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    ap = P.trial_hash_allpairs(packed, off, inst.l, k, s, seed, 0, m, cap_cand=max(1, C),
+                               cap_members=max(1, res["n_members"]) if "n_members" in res else None)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ap_ms = a0.elapsed_time(a1)
+    allpairs = {"ms_for_all_trials": ap_ms, "compares_per_s": m * x * x / (ap_ms / 1e3),
+                "same_candidates": ap["n_candidates"] == C,
+                "hash_ms_histogram_path": P.projection_trace_read("hash")[0] / args.steps}
+
     # ---- end to end through the public API: host ASCII in, result out
     e2e_times = []
     for i in range(max(3, min(args.steps, 10))):
@@ -671,7 +685,8 @@ def main():
                          f"theta0), {iters} EM iters") if errs else None,
         "wall_ms_per_step": wall * 1e3 / args.steps,
         "flush_ms_per_step": float(np.mean(flush_ms)),
-        "roofline": roof, "hash_roofline": hash_roof, "clocks": clk, "e2e": e2e,
+        "roofline": roof, "hash_roofline": hash_roof, "allpairs_enrichment": allpairs,
+        "clocks": clk, "e2e": e2e,
         "gpu_launches": all_launches / max(1, args.steps),
         "cpu_baseline": None,
     }

@@ -286,6 +286,23 @@ int projection_find_batch(const uint8_t *ascii, const int64_t *seq_off, const in
 
 void projection_result_free(projection_result *r);
 
+/* ---- low-memory enrichment by all-pairs comparison ---------------------- */
+
+/* Algorithm 2 steps 2-3 without the 4^k bucket table: per trial every l-mer's
+ * projected k-mer is compared with those of all x l-mers of the trial
+ * (PROJECTION2 of Section 5.2; the pairwise compare of Section 6's
+ * CUDA-PROJECTION), O(x) memory and O(x^2) work per trial.  For inputs where
+ * 4^k counters do not fit but x is small.  Output, capacities, ownership and
+ * errors exactly as trial_hash (no positions or counts outputs); the candidate
+ * list and member lists are identical to trial_hash's.  1 <= k <= min(l, 15),
+ * n_trials <= 65535 and n_trials * x < 2^31 per call; ECAPACITY (with a
+ * message) when a trial has more than 4096 enriched buckets. */
+int trial_hash_allpairs(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l, int k,
+                        int s, uint64_t seed, int64_t trial_begin, int64_t n_trials,
+                        int64_t cap_cand, int64_t cap_members, int32_t *cand_trial_dev,
+                        uint32_t *cand_key_dev, int32_t *cand_cnt_dev, int64_t *cand_off_dev,
+                        int32_t *members_dev, int64_t *totals_dev, void *stream);
+
 /* ---- step 1 for a batch, on the device (Section 5) ---------------------- */
 
 /* Algorithm 2 step 1 ("if not specified") for n instances held on the device:

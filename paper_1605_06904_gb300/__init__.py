@@ -142,6 +142,37 @@ def trial_hash(packed, seq_off, l, k, s, seed, trial_begin, n_trials, positions_
     return out
 
 
+def trial_hash_allpairs(packed, seq_off, l, k, s, seed, trial_begin, n_trials, cap_cand=None,
+                        cap_members=None, stream=None):
+    """trial_hash's output from the low-memory all-pairs mode (no 4^k table;
+    O(x^2) comparisons per trial)."""
+    off = _off(seq_off)
+    t = off.size - 1
+    dev = packed.device
+    x = int(np.sum(np.maximum(np.diff(off) - l + 1, 0)))
+    if cap_members is None:
+        cap_members = max(1, min(x * n_trials, 1 << 26))
+    if cap_cand is None:
+        cap_cand = max(1, cap_members // max(1, s))
+    while True:
+        ct = _dev(cap_cand, torch.int32, dev)
+        ck = _dev(cap_cand, torch.int32, dev)
+        cc = _dev(cap_cand, torch.int32, dev)
+        co = _dev(cap_cand + 1, torch.int64, dev)
+        mem = _dev(cap_members, torch.int32, dev)
+        tot = _dev(2, torch.int64, dev)
+        check(lib().trial_hash_allpairs(_ptr(packed), _ptr(off), t, l, k, s, seed & (2**64 - 1),
+                                        trial_begin, n_trials, cap_cand, cap_members, _ptr(ct),
+                                        _ptr(ck), _ptr(cc), _ptr(co), _ptr(mem), _ptr(tot),
+                                        _stream(stream)))
+        C, M = (int(v) for v in tot.cpu())
+        if C <= cap_cand and M <= cap_members:
+            break
+        cap_cand, cap_members = max(C, 1), max(M, 1)
+    return {"cand_trial": ct[:C], "cand_key": ck[:C], "cand_cnt": cc[:C], "cand_off": co[:C + 1],
+            "members": mem[:M], "n_candidates": C, "n_members": M}
+
+
 def trial_hash_noalloc(packed, seq_off, l, k, s, seed, trial_begin, n_trials, cap_cand,
                        cap_members, positions_in=None, stream=None):
     """trial_hash without device allocation inside the library (scratch in a

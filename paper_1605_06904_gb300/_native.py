@@ -67,6 +67,8 @@ SIGNATURES = {
     "projection_result_free": ([ctypes.POINTER(ProjectionResult)], None),
     "projection_selftest_wait": ([i64, P], i32),
     "projection_hist_peak": ([i32, P, P], i32),
+    "trial_hash_allpairs": ([P, P, i32, i32, i32, i32, u64, i64, i64, i64, i64, P, P, P, P, P, P,
+                             P], i32),
     "projection_params_batch": ([i32, P, P, P, P, P, P, P, P, ctypes.c_double, P], i32),
     "projection_trace_enable": ([i32], i32),
     "projection_trace_read": ([ctypes.c_char_p, P, P], i32),

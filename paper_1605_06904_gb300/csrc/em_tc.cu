@@ -108,12 +108,6 @@ __device__ __forceinline__ float ex2(float x) {
     return y;
 }
 
-// log(e^a + e^b) in FP64 (a may be -inf).
-__device__ __forceinline__ double log_add(double a, double b) {
-    const double hi = fmax(a, b), lo = fmin(a, b);
-    return hi == -INFINITY ? -INFINITY : hi + log1p(exp(lo - hi));
-}
-
 __device__ __forceinline__ void kahan(float &sum, float &comp, float v) {
     const float y = v - comp;
     const float s = sum + y;
@@ -444,6 +438,9 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
 #pragma unroll
             for (int q = 0; q < KH; ++q) tot[q] = 0.f;
             double ll = 0.0, zs = 0.0;  // zs: expected number of sites (ZOOPS)
+            const bool zoops = in.gamma < 1.0;
+            const float log_gamma = zoops ? logf((float)in.gamma) : 0.f;
+            const float log_no = zoops ? log1pf(-(float)in.gamma) : 0.f;
             float m = -INFINITY, Ssum = 0.f, Scmp = 0.f;
             bool first = true;
             o_base = o_waited;  // every count MMA of earlier items was waited for
@@ -536,13 +533,16 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                     const float Sh = Ssum - Scmp;
                     const float Sf = Sh + exchange(Sh);
                     float w = 1.f;  // posterior probability that the sequence holds a site
-                    if (in.gamma < 1.0) {
-                        // ZOOPS: L_i = log[(1 - gamma) + (gamma / ns) sum_j e^r]
-                        const double lg = log(in.gamma / (double)tcur.ns) +
-                                          ((double)m + (double)log2f(Sf)) * 0.6931471805599453;
-                        const double Li = log_add(log1p(-in.gamma), lg);
-                        w = (float)exp(lg - Li);
-                        ll += Li;
+                    if (zoops) {
+                        // ZOOPS: L_i = log[(1 - gamma) + (gamma / ns) sum_j e^r], in FP32
+                        // (FP64 transcendentals are slow here; the sum over sequences
+                        // stays FP64)
+                        const float lg = log_gamma - logf((float)tcur.ns) +
+                                         (m + log2f(Sf)) * 0.69314718f;
+                        const float hi = fmaxf(log_no, lg), lo = fminf(log_no, lg);
+                        const float Li = hi + log1pf(expf(lo - hi));
+                        w = expf(lg - Li);
+                        ll += (double)Li;
                     } else {
                         ll += (double)((m + log2f(Sf)) * 0.69314718f - logf((float)tcur.ns));
                     }
