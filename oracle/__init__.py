@@ -69,6 +69,22 @@ def _L():
             lib.orc_em.restype = i32
             lib.orc_em_zoops.argtypes = [P, P, i32, i32, P, P, i64, i32, f64, f64, P, P, i32]
             lib.orc_em_zoops.restype = i32
+            lib.orc_encode_aa.argtypes = [P, i64, P]
+            lib.orc_encode_aa.restype = i64
+            lib.orc_keys_a.argtypes = [P, P, i32, i32, i32, P, i32, P]
+            lib.orc_keys_a.restype = None
+            lib.orc_background_a.argtypes = [P, i64, i32, P]
+            lib.orc_background_a.restype = None
+            lib.orc_theta0_a.argtypes = [P, P, P, i32, i32, P, i32, f64, i32, P]
+            lib.orc_theta0_a.restype = None
+            lib.orc_em_a.argtypes = [P, P, i32, i32, i32, P, P, i64, i32, f64, P, i32]
+            lib.orc_em_a.restype = i32
+            lib.orc_sites_a.argtypes = [P, P, i32, i32, i32, P, P, P]
+            lib.orc_sites_a.restype = None
+            lib.orc_consensus_a.argtypes = [P, i32, i32, ctypes.c_char_p, ctypes.c_char_p]
+            lib.orc_consensus_a.restype = None
+            lib.orc_score_a.argtypes = [P, P, i32, i32, i32, P]
+            lib.orc_score_a.restype = i32
             lib.orc_sites.argtypes = [P, P, i32, i32, P, P, P]; lib.orc_sites.restype = None
             lib.orc_consensus.argtypes = [P, i32, P]; lib.orc_consensus.restype = None
             lib.orc_score.argtypes = [P, P, i32, i32, P]; lib.orc_score.restype = i32
@@ -360,4 +376,115 @@ def find(ascii_seqs, l, d, k=0, s=0, m=0, seed=0, em_iters=5, beta=0.25, nthread
                    score=score(codes, seq_off, l, st))
     if with_hash:
         res["hash"] = h
+    return res
+
+
+# --------------------------------------------------------------------------
+# Protein alphabet (reading R17): 20 letters ACDEFGHIKLMNPQRSTVWY, codes 0..19
+# --------------------------------------------------------------------------
+
+AA_LETTERS = "ACDEFGHIKLMNPQRSTVWY"
+
+
+def encode_aa(ascii_bytes) -> np.ndarray:
+    a = np.frombuffer(bytes(ascii_bytes), np.uint8)
+    out = np.empty(a.size, np.uint8)
+    bad = _L().orc_encode_aa(_p(a), a.size, _p(out))
+    if bad >= 0:
+        raise ValueError(f"not an amino-acid letter at {bad}")
+    return out
+
+
+def keys_a(codes, seq_off, l, pos, A):
+    codes = _c(codes, np.uint8); seq_off = _c(seq_off, np.int64); pos = _c(pos, np.int32)
+    t = seq_off.size - 1
+    x = int(np.sum(np.maximum(np.diff(seq_off) - l + 1, 0)))
+    out = np.empty(x, np.uint32)
+    _L().orc_keys_a(_p(codes), _p(seq_off), t, l, pos.size, _p(pos), A, _p(out))
+    return out
+
+
+def background_a(codes, A) -> np.ndarray:
+    codes = _c(codes, np.uint8)
+    bg = np.empty(A, np.float64)
+    _L().orc_background_a(_p(codes), codes.size, A, _p(bg))
+    return bg
+
+
+def theta0_a(codes, seq_off, l, members, beta, A) -> np.ndarray:
+    codes = _c(codes, np.uint8); seq_off = _c(seq_off, np.int64)
+    lo = lmer_offsets(seq_off, l)
+    mem = _c(members, np.int32)
+    out = np.empty((l, A), np.float64)
+    _L().orc_theta0_a(_p(codes), _p(seq_off), _p(lo), seq_off.size - 1, l, _p(mem), mem.size,
+                      float(beta), A, _p(out))
+    return out
+
+
+def em_a(codes, seq_off, l, bg, pwm0, iters, beta, A, nthreads=1):
+    """OOPS EM over an alphabet of A letters from pwm0[C][l][A]: (pwm, ll)."""
+    codes = _c(codes, np.uint8); seq_off = _c(seq_off, np.int64)
+    pwm = np.array(pwm0, dtype=np.float64, copy=True, order="C").reshape(-1, l, A)
+    C = pwm.shape[0]
+    bg = _c(bg, np.float64)
+    ll = np.empty(C, np.float64)
+    rc = _L().orc_em_a(_p(codes), _p(seq_off), seq_off.size - 1, l, A, _p(bg), _p(pwm), C, iters,
+                       float(beta), _p(ll), int(nthreads))
+    if rc != 0:
+        raise ValueError("bad EM arguments")
+    return pwm, ll
+
+
+def sites_a(codes, seq_off, l, bg, pwm, A) -> np.ndarray:
+    codes = _c(codes, np.uint8); seq_off = _c(seq_off, np.int64)
+    pwm = _c(pwm, np.float64); bg = _c(bg, np.float64)
+    out = np.empty(seq_off.size - 1, np.int32)
+    _L().orc_sites_a(_p(codes), _p(seq_off), seq_off.size - 1, l, A, _p(bg), _p(pwm), _p(out))
+    return out
+
+
+def consensus_a(pwm, A, letters=AA_LETTERS) -> str:
+    pwm = _c(pwm, np.float64)
+    l = pwm.size // A
+    buf = ctypes.create_string_buffer(l + 1)
+    _L().orc_consensus_a(_p(pwm), l, A, letters.encode(), buf)
+    return buf.value.decode()
+
+
+def score_a(codes, seq_off, l, sites, A) -> int:
+    codes = _c(codes, np.uint8); seq_off = _c(seq_off, np.int64); sites = _c(sites, np.int32)
+    return int(_L().orc_score_a(_p(codes), _p(seq_off), seq_off.size - 1, l, A, _p(sites)))
+
+
+def find_protein(seqs, l, k, s, m, seed, em_iters, beta, nthreads=1):
+    """Algorithm 2 + Section 5.1 over the 20-letter alphabet (keys base 20,
+    enriched buckets by grouping equal keys, OOPS EM on every candidate)."""
+    A = 20
+    codes = encode_aa(b"".join(bytes(q, "ascii") if isinstance(q, str) else bytes(q) for q in seqs))
+    seq_off = np.concatenate([[0], np.cumsum([len(q) for q in seqs])]).astype(np.int64)
+    ct, ck, cc, offs, mems, base = [], [], [], [], [], 0
+    for trial in range(m):
+        kk = keys_a(codes, seq_off, l, positions(seed, trial, l, k), A)
+        a, b, o, mm = enriched(kk, s)
+        ct.append(np.full(a.size, trial, np.int32)); ck.append(a); cc.append(b)
+        offs.append(o[1:] + base); mems.append(mm)
+        base += mm.size
+    cand_off = np.concatenate([np.array([0], np.int64)] + offs).astype(np.int64)
+    members = np.concatenate(mems) if mems else np.zeros(0, np.int32)
+    C = int(cand_off.size - 1)
+    res = {"k": k, "s": s, "m": m, "n_candidates": C,
+           "cand_trial": np.concatenate(ct) if ct else np.zeros(0, np.int32),
+           "cand_key": np.concatenate(ck) if ck else np.zeros(0, np.uint32),
+           "cand_cnt": np.concatenate(cc) if cc else np.zeros(0, np.int32),
+           "cand_off": cand_off, "members": members}
+    if C == 0:
+        return res
+    bg = background_a(codes, A)
+    th0 = np.stack([theta0_a(codes, seq_off, l, members[cand_off[c]:cand_off[c + 1]], beta, A)
+                    for c in range(C)])
+    pwm, ll = em_a(codes, seq_off, l, bg, th0, em_iters, beta, A, nthreads=nthreads)
+    w = rank(ll)
+    st = sites_a(codes, seq_off, l, bg, pwm[w], A)
+    res.update(bg=bg, pwm_all=pwm, ll_all=ll, win=w, pwm=pwm[w], loglik=float(ll[w]),
+               consensus=consensus_a(pwm[w], A), sites=st, score=score_a(codes, seq_off, l, st, A))
     return res

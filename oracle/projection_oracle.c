@@ -514,3 +514,195 @@ int orc_score(const uint8_t *codes, const int64_t *seq_off, int t, int l, const 
     }
     return total;
 }
+
+/* ------------------------------------------------------------------------- */
+/* R17: the protein alphabet.  Section 2 takes Sigma = {A, C, G, T} for DNA and */
+/* |Sigma| = 20 for proteins; read here as the 20 amino-acid letters           */
+/* ACDEFGHIKLMNPQRSTVWY with codes 0..19 in that order (upper or lower case).  */
+/* The functions below are the DNA ones with the alphabet size A as a          */
+/* parameter (keys base A, most significant position first; models A x l).    */
+/* With A = 4 and codes 0..3 they compute exactly what the DNA functions do.   */
+/* ------------------------------------------------------------------------- */
+
+int64_t orc_encode_aa(const uint8_t *ascii, int64_t n, uint8_t *codes) {
+    static const char letters[] = "ACDEFGHIKLMNPQRSTVWY";
+    for (int64_t i = 0; i < n; ++i) {
+        int c = ascii[i];
+        if (c >= 'a' && c <= 'z') c -= 32;
+        int code = -1;
+        for (int a = 0; a < 20; ++a) if (letters[a] == c) { code = a; break; }
+        if (code < 0) return i;
+        codes[i] = (uint8_t)code;
+    }
+    return -1;
+}
+
+void orc_keys_a(const uint8_t *codes, const int64_t *seq_off, int t, int l, int k,
+                const int32_t *pos, int A, uint32_t *keys) {
+    int64_t g = 0;
+    for (int i = 0; i < t; ++i) {
+        int64_t n = seq_off[i + 1] - seq_off[i];
+        for (int64_t j = 0; j + l <= n; ++j) {
+            const uint8_t *lmer = codes + seq_off[i] + j;
+            uint32_t key = 0;
+            for (int q = 0; q < k; ++q) key = key * (uint32_t)A + lmer[pos[q]];
+            keys[g++] = key;
+        }
+    }
+}
+
+void orc_background_a(const uint8_t *codes, int64_t n, int A, double *bg) {
+    int64_t c[32] = {0};
+    for (int64_t b = 0; b < n; ++b) c[codes[b]] += 1;
+    int64_t tot = 0;
+    for (int a = 0; a < A; ++a) { if (c[a] == 0) c[a] = 1; tot += c[a]; }
+    for (int a = 0; a < A; ++a) bg[a] = (double)c[a] / (double)tot;
+}
+
+void orc_theta0_a(const uint8_t *codes, const int64_t *seq_off, const int64_t *lmer_off, int t,
+                  int l, const int32_t *members, int cnt, double beta, int A, double *pwm) {
+    double n[32][32];
+    memset(n, 0, sizeof n);
+    for (int e = 0; e < cnt; ++e) {
+        int i;
+        int64_t j;
+        lmer_locate(lmer_off, t, members[e], &i, &j);
+        const uint8_t *lmer = codes + seq_off[i] + j;
+        for (int p = 0; p < l; ++p) n[p][lmer[p]] += 1.0;
+    }
+    for (int p = 0; p < l; ++p)
+        for (int a = 0; a < A; ++a) pwm[p * A + a] = (n[p][a] + beta) / ((double)cnt + A * beta);
+}
+
+/* OOPS EM (as em_one) over an alphabet of A letters: r(i,j) = sum_p
+ * [log pwm_p(x) - log bg(x)], z = softmax over the starts, LL = sum_i [log
+ * sum_j e^r - log ns_i], pwm_p(a) = (sum z [x = a] + beta) / (t' + A beta). */
+static void em_one_a(const uint8_t *codes, const int64_t *seq_off, int t, int l, int A,
+                     const double *bg, double *pwm, int iters, double beta, double *ll,
+                     double *r) {
+    double W[32][32];
+    int tprime = 0;
+    for (int i = 0; i < t; ++i)
+        if (seq_off[i + 1] - seq_off[i] >= l) ++tprime;
+    for (int it = 0; it <= iters; ++it) {
+        for (int p = 0; p < l; ++p)
+            for (int a = 0; a < A; ++a) W[p][a] = log(pwm[p * A + a]) - log(bg[a]);
+        double N[32][32];
+        memset(N, 0, sizeof N);
+        double LL = 0.0;
+        for (int i = 0; i < t; ++i) {
+            int64_t n = seq_off[i + 1] - seq_off[i];
+            int64_t ns = n >= l ? n - l + 1 : 0;
+            if (ns == 0) continue;
+            for (int64_t j = 0; j < ns; ++j) {
+                const uint8_t *lmer = codes + seq_off[i] + j;
+                double acc = 0.0;
+                for (int p = 0; p < l; ++p) acc += W[p][lmer[p]];
+                r[j] = acc;
+            }
+            double mx = r[0];
+            for (int64_t j = 1; j < ns; ++j) if (r[j] > mx) mx = r[j];
+            double S = 0.0;
+            for (int64_t j = 0; j < ns; ++j) S += exp(r[j] - mx);
+            double L = mx + log(S);
+            LL += L - log((double)ns);
+            if (it < iters) {
+                for (int64_t j = 0; j < ns; ++j) {
+                    double z = exp(r[j] - L);
+                    const uint8_t *lmer = codes + seq_off[i] + j;
+                    for (int p = 0; p < l; ++p) N[p][lmer[p]] += z;
+                }
+            }
+        }
+        if (it == iters) { *ll = LL; break; }
+        for (int p = 0; p < l; ++p)
+            for (int a = 0; a < A; ++a)
+                pwm[p * A + a] = (N[p][a] + beta) / ((double)tprime + A * beta);
+    }
+}
+
+typedef struct {
+    const uint8_t *codes; const int64_t *seq_off; int t, l, A; const double *bg;
+    double *pwm; int iters; double beta; double *ll; int64_t c_begin, c_end, max_ns;
+} em_a_job;
+
+static void *em_a_worker(void *arg) {
+    em_a_job *jb = (em_a_job *)arg;
+    double *r = (double *)malloc(sizeof(double) * (size_t)(jb->max_ns > 0 ? jb->max_ns : 1));
+    for (int64_t c = jb->c_begin; c < jb->c_end; ++c)
+        em_one_a(jb->codes, jb->seq_off, jb->t, jb->l, jb->A, jb->bg,
+                 jb->pwm + c * jb->l * jb->A, jb->iters, jb->beta, jb->ll + c, r);
+    free(r);
+    return NULL;
+}
+
+int orc_em_a(const uint8_t *codes, const int64_t *seq_off, int t, int l, int A, const double *bg,
+             double *pwm, int64_t C, int iters, double beta, double *ll, int nthreads) {
+    if (l < 1 || l > 32 || A < 2 || A > 32 || iters < 0 || t < 1) return -1;
+    int64_t max_ns = 0;
+    for (int i = 0; i < t; ++i) {
+        int64_t n = seq_off[i + 1] - seq_off[i];
+        if (n - l + 1 > max_ns) max_ns = n - l + 1;
+    }
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > C) nthreads = C > 0 ? (int)C : 1;
+    em_a_job *jobs = (em_a_job *)calloc((size_t)nthreads, sizeof(em_a_job));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    for (int w = 0; w < nthreads; ++w) {
+        em_a_job *jb = &jobs[w];
+        jb->codes = codes; jb->seq_off = seq_off; jb->t = t; jb->l = l; jb->A = A; jb->bg = bg;
+        jb->pwm = pwm; jb->iters = iters; jb->beta = beta; jb->ll = ll; jb->max_ns = max_ns;
+        jb->c_begin = C * w / nthreads; jb->c_end = C * (w + 1) / nthreads;
+    }
+    for (int w = 1; w < nthreads; ++w) pthread_create(&th[w], NULL, em_a_worker, &jobs[w]);
+    em_a_worker(&jobs[0]);
+    for (int w = 1; w < nthreads; ++w) pthread_join(th[w], NULL);
+    free(jobs); free(th);
+    return 0;
+}
+
+void orc_sites_a(const uint8_t *codes, const int64_t *seq_off, int t, int l, int A,
+                 const double *bg, const double *pwm, int32_t *sites) {
+    double W[32][32];
+    for (int p = 0; p < l; ++p)
+        for (int a = 0; a < A; ++a) W[p][a] = log(pwm[p * A + a]) - log(bg[a]);
+    for (int i = 0; i < t; ++i) {
+        int64_t n = seq_off[i + 1] - seq_off[i];
+        int64_t ns = n >= l ? n - l + 1 : 0, best = ns > 0 ? 0 : -1;
+        double bv = -INFINITY;
+        for (int64_t j = 0; j < ns; ++j) {
+            const uint8_t *lmer = codes + seq_off[i] + j;
+            double acc = 0.0;
+            for (int p = 0; p < l; ++p) acc += W[p][lmer[p]];
+            if (acc > bv) { bv = acc; best = j; }
+        }
+        sites[i] = (int32_t)best;
+    }
+}
+
+/* Consensus over A letters: per column the letter of largest weight, ties to
+ * the lowest code (R13); `letters` maps codes to characters. */
+void orc_consensus_a(const double *pwm, int l, int A, const char *letters, char *out) {
+    for (int p = 0; p < l; ++p) {
+        int best = 0;
+        for (int a = 1; a < A; ++a) if (pwm[p * A + a] > pwm[p * A + best]) best = a;
+        out[p] = letters[best];
+    }
+    out[l] = 0;
+}
+
+int orc_score_a(const uint8_t *codes, const int64_t *seq_off, int t, int l, int A,
+                const int32_t *sites) {
+    int total = 0;
+    for (int p = 0; p < l; ++p) {
+        int c[32] = {0};
+        for (int i = 0; i < t; ++i) {
+            if (sites[i] < 0) continue;
+            c[codes[seq_off[i] + sites[i] + p]] += 1;
+        }
+        int m = 0;
+        for (int a = 0; a < A; ++a) if (c[a] > m) m = c[a];
+        total += m;
+    }
+    return total;
+}

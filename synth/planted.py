@@ -127,6 +127,36 @@ def planted_instance(seed: int, instance: int, t: int, n, l: int, d: int,
     return Instance(seqs=seqs, l=l, d=d, motif=motif.tobytes().decode(), starts=starts)
 
 
+AA_LETTERS = np.frombuffer(b"ACDEFGHIKLMNPQRSTVWY", dtype=np.uint8)
+
+
+def planted_protein(seed: int, instance: int, t: int, n, l: int, d: int) -> Instance:
+    """Protein counterpart of planted_instance: iid uniform residues over the 20
+    amino-acid letters, a uniform random motif, and in every sequence one
+    occurrence with exactly d distinct positions replaced by one of the 19
+    other letters (uniform), at a uniform start."""
+    st = _Stream(seed, instance)
+    lens = [int(n)] * t if np.isscalar(n) else [int(v) for v in n]
+    motif = AA_LETTERS[st.below(20, l)].copy()
+    seqs, starts = [], np.full(t, -1, np.int64)
+    for i in range(t):
+        s = AA_LETTERS[st.below(20, lens[i])]
+        if lens[i] >= l:
+            occ = motif.copy()
+            perm = np.arange(l)
+            for q in range(d):
+                j = q + st.below(l - q)
+                perm[q], perm[j] = perm[j], perm[q]
+            for p in perm[:d]:
+                others = AA_LETTERS[AA_LETTERS != occ[p]]
+                occ[p] = others[st.below(19)]
+            a = st.below(lens[i] - l + 1)
+            s[a:a + l] = occ
+            starts[i] = a
+        seqs.append(s.tobytes())
+    return Instance(seqs=seqs, l=l, d=d, motif=motif.tobytes().decode(), starts=starts)
+
+
 # The five workloads: sizes and parameters of the planted challenge problems.
 CONFIGS = {
     1: dict(name="planted(11,2) t=20 n=600", t=20, n=600, l=11, d=2, k=7, s=4, m=100,
