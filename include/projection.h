@@ -303,6 +303,26 @@ int trial_hash_allpairs(const uint32_t *packed_dev, const int64_t *seq_off, int 
                         uint32_t *cand_key_dev, int32_t *cand_cnt_dev, int64_t *cand_off_dev,
                         int32_t *members_dev, int64_t *totals_dev, void *stream);
 
+/* ---- the protein alphabet (Section 2, |Sigma| = 20) ---------------------- */
+
+/* Algorithm 2 with Section 5.1's OOPS EM over the 20 amino-acid letters
+ * ACDEFGHIKLMNPQRSTVWY (codes 0..19, either case; any other character returns
+ * PROJ_EBADCHAR with its index in the message).  Host ASCII sequences in
+ * linear form (ascii[seq_off[t]], seq_off[t+1], every length >= l, 1 <= l <=
+ * 32).  k, s and m are required (the Section 5 formulas are stated for DNA):
+ * 1 <= k <= min(l, 6) (keys base 20 = the projected residues read
+ * most-significant first), s >= 1, 1 <= m <= 65535; trials draw their
+ * positions as in trial_hash.  Enriched buckets come from the all-pairs
+ * comparison (trial_hash_allpairs' scheme, ECAPACITY above 4096 enriched
+ * buckets per trial; m * x < 2^31).  theta^0 and em_iters OOPS iterations:
+ * scores and exponentials in FP32, M-step counts in 64-bit fixed point (2^-40),
+ * log-likelihoods in FP64 (results do not depend on thread scheduling);
+ * ranking, sites and Score as projection_find.  out->pwm holds [l][20] floats; out->win_key is
+ * the base-20 key.  Copies in, computes, copies out, synchronises `stream`. */
+int projection_find_protein(const uint8_t *ascii, const int64_t *seq_off, int t, int l, int k,
+                            int s, int m, uint64_t seed, int em_iters, float pseudocount,
+                            projection_result *out, void *stream);
+
 /* ---- step 1 for a batch, on the device (Section 5) ---------------------- */
 
 /* Algorithm 2 step 1 ("if not specified") for n instances held on the device:

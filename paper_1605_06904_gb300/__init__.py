@@ -19,9 +19,10 @@ __all__ = ["projection_packed_words", "projection_default_params", "projection_p
            "projection_background", "projection_positions", "trial_hash",
            "trial_hash_noalloc", "theta0_build",
            "em_refine", "projection_finalize", "projection_find", "projection_find_packed",
-           "projection_find_batch", "projection_find_top", "projection_find_packed_top",
+           "projection_find_batch", "projection_find_top", "projection_find_protein", "projection_find_packed_top",
            "projection_trace_enable", "projection_trace_read", "projection_selftest_wait",
-           "ProjectionError",
+           "projection_hist_peak", "projection_params_batch", "em_refine_zoops",
+           "projection_find_packed_zoops", "trial_hash_allpairs", "ProjectionError",
            "PROJ_EM_FP32", "PROJ_EM_BF16_SPLIT", "seq_offsets"]
 
 
@@ -243,14 +244,14 @@ def projection_finalize(packed, seq_off, l, bg, theta, loglik, stream=None):
             "consensus": bytes(cons.cpu().numpy()).decode(), "score": int(score.item())}
 
 
-def _result_dict(r: ProjectionResult) -> dict:
+def _result_dict(r: ProjectionResult, alphabet: int = 4) -> dict:
     l, t = r.l, r.t
     out = {"status": r.status, "t": t, "l": l, "k": r.k, "s": r.s, "m": r.m,
            "n_candidates": r.n_candidates, "n_members": r.n_members, "win_index": r.win_index,
            "win_trial": r.win_trial, "win_key": r.win_key, "loglik": r.loglik,
            "score": r.score, "n_refined": r.n_refined}
     if r.pwm:
-        out["pwm"] = np.ctypeslib.as_array(r.pwm, shape=(l * 4,)).reshape(l, 4).copy()
+        out["pwm"] = np.ctypeslib.as_array(r.pwm, shape=(l * alphabet,)).reshape(l, alphabet).copy()
         out["sites"] = np.ctypeslib.as_array(r.sites, shape=(t,)).copy()
         out["consensus"] = r.consensus.decode()
     return out
@@ -290,6 +291,23 @@ def projection_find_top(ascii, seq_off, l, d, k=0, s=0, m=0, seed=0, em_iters=5,
     try:
         check(rc)
         return _result_dict(r)
+    finally:
+        lib().projection_result_free(ctypes.byref(r))
+
+
+def projection_find_protein(ascii, seq_off, l, k, s, m, seed=0, em_iters=5, pseudocount=0.25,
+                            stream=None) -> dict:
+    """Algorithm 2 + OOPS EM over the 20 amino-acid letters from HOST ASCII
+    sequences in linear form; the result's "pwm" is [l, 20]."""
+    off = _off(seq_off)
+    ascii = np.ascontiguousarray(np.asarray(ascii, np.uint8))
+    r = ProjectionResult()
+    rc = lib().projection_find_protein(_ptr(ascii), _ptr(off), off.size - 1, l, k, s, m,
+                                       seed & (2**64 - 1), em_iters, float(pseudocount),
+                                       ctypes.byref(r), _stream(stream))
+    try:
+        check(rc)
+        return _result_dict(r, 20)
     finally:
         lib().projection_result_free(ctypes.byref(r))
 

@@ -52,6 +52,29 @@ __global__ void __launch_bounds__(kApThreads) ap_keys_kernel(
     keys[(int64_t)trial_local * x + g] = ap_key(window64(packed, nwords, b0), pos, k);
 }
 
+// Keys over the 20-letter protein alphabet: byte codes 0..19, base 20, the
+// first projected position most significant.
+__global__ void __launch_bounds__(kApThreads) ap_keys_aa_kernel(
+    const uint8_t *__restrict__ codes, const int32_t *__restrict__ seq_off,
+    const int32_t *__restrict__ lmer_off, int t, int l, int k, int x, uint64_t seed,
+    int64_t trial_begin, uint32_t *__restrict__ keys) {
+    __shared__ int s_pos[16];
+    const int trial_local = blockIdx.y;
+    if (threadIdx.x == 0) draw_positions(seed, (uint64_t)(trial_begin + trial_local), l, k, s_pos);
+    __syncthreads();
+    const int g = blockIdx.x * kApThreads + threadIdx.x;
+    if (g >= x) return;
+    int lo = 0, hi = t - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(lmer_off + mid) <= g) lo = mid; else hi = mid - 1;
+    }
+    const uint8_t *lmer = codes + __ldg(seq_off + lo) + (g - __ldg(lmer_off + lo));
+    uint32_t key = 0u;
+    for (int q = 0; q < k; ++q) key = key * 20u + (uint32_t)lmer[s_pos[q]];
+    keys[(int64_t)trial_local * x + g] = key;
+}
+
 // The comparison of l-mer g's projected k-mer with those of all x l-mers of
 // its trial, taken through shared memory one tile at a time.
 __global__ void __launch_bounds__(kApThreads) ap_compare_kernel(const uint32_t *__restrict__ keys,
@@ -262,32 +285,20 @@ __global__ void ap_members_kernel(const int32_t *__restrict__ cnt, const int32_t
 
 using namespace proj;
 
-extern "C" int trial_hash_allpairs(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
-                                   int k, int s, uint64_t seed, int64_t trial_begin,
-                                   int64_t n_trials, int64_t cap_cand, int64_t cap_members,
-                                   int32_t *cand_trial_dev, uint32_t *cand_key_dev,
-                                   int32_t *cand_cnt_dev, int64_t *cand_off_dev,
-                                   int32_t *members_dev, int64_t *totals_dev, void *stream) {
-    clear_error();
-    cudaStream_t st = (cudaStream_t)stream;
-    PROJ_REQUIRE(packed_dev != nullptr && totals_dev != nullptr && cand_off_dev != nullptr,
-                 "packed_dev, cand_off_dev and totals_dev must not be NULL");
-    PROJ_REQUIRE(k >= 1 && k <= 15 && k <= l, "need 1 <= k <= min(l, 15)");
-    PROJ_REQUIRE(s >= 1, "need s >= 1");
-    PROJ_REQUIRE(trial_begin >= 0 && n_trials >= 0 && n_trials <= 65535,
-                 "need 0 <= n_trials <= 65535 per call");
-    PROJ_REQUIRE(cap_cand >= 0 && cap_members >= 0, "capacities must be >= 0");
-    PROJ_REQUIRE(cap_cand == 0 || (cand_trial_dev && cand_key_dev && cand_cnt_dev),
-                 "candidate buffers must not be NULL");
-    PROJ_REQUIRE(cap_members == 0 || members_dev, "members_dev must not be NULL");
-    Layout L;
-    PROJ_TRY(make_layout(seq_off, t, l, st, L));
+namespace proj {
+
+int run_allpairs(const uint32_t *packed, const uint8_t *codes, int alphabet, const Layout &L,
+                 int k, int s, uint64_t seed, int64_t trial_begin, int64_t n_trials,
+                 int64_t cap_cand, int64_t cap_members, int32_t *cand_trial_dev,
+                 uint32_t *cand_key_dev, int32_t *cand_cnt_dev, int64_t *cand_off_dev,
+                 int32_t *members_dev, int64_t *totals_dev, cudaStream_t st) {
     if (n_trials == 0) {
         PROJ_CUDA_TRY(cudaMemsetAsync(totals_dev, 0, 2 * sizeof(int64_t), st));
         PROJ_CUDA_TRY(cudaMemsetAsync(cand_off_dev, 0, sizeof(int64_t), st));
         return PROJ_OK;
     }
     const int64_t T = n_trials, x = L.x;
+    const int t = L.t, l = L.l;
     PROJ_REQUIRE(T * x < ((int64_t)1 << 31), "n_trials * x must stay below 2^31 per call");
     DevBuf scratch;
     const size_t per = (size_t)T * x;
@@ -312,9 +323,13 @@ extern "C" int trial_hash_allpairs(const uint32_t *packed_dev, const int64_t *se
     const dim3 grid_x((unsigned)((x + kApThreads - 1) / kApThreads), (unsigned)T);
     {
         TraceSpan ts_("allpairs", st);
-        ap_keys_kernel<<<grid_x, kApThreads, 0, st>>>(packed_dev, L.nwords, L.seq_off_dev(),
-                                                      L.lmer_off_dev(), t, l, k, (int)x, seed,
-                                                      trial_begin, keys);
+        if (alphabet == 20)
+            ap_keys_aa_kernel<<<grid_x, kApThreads, 0, st>>>(codes, L.seq_off_dev(), L.lmer_off_dev(),
+                                                             t, l, k, (int)x, seed, trial_begin, keys);
+        else
+            ap_keys_kernel<<<grid_x, kApThreads, 0, st>>>(packed, L.nwords, L.seq_off_dev(),
+                                                          L.lmer_off_dev(), t, l, k, (int)x, seed,
+                                                          trial_begin, keys);
     }
     PROJ_LAUNCH_CHECK("ap_keys_kernel");
     {
@@ -355,4 +370,31 @@ extern "C" int trial_hash_allpairs(const uint32_t *packed_dev, const int64_t *se
     }
     PROJ_LAUNCH_CHECK("ap_members_kernel");
     return PROJ_OK;
+}
+
+}  // namespace proj
+
+extern "C" int trial_hash_allpairs(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
+                                   int k, int s, uint64_t seed, int64_t trial_begin,
+                                   int64_t n_trials, int64_t cap_cand, int64_t cap_members,
+                                   int32_t *cand_trial_dev, uint32_t *cand_key_dev,
+                                   int32_t *cand_cnt_dev, int64_t *cand_off_dev,
+                                   int32_t *members_dev, int64_t *totals_dev, void *stream) {
+    clear_error();
+    cudaStream_t st = (cudaStream_t)stream;
+    PROJ_REQUIRE(packed_dev != nullptr && totals_dev != nullptr && cand_off_dev != nullptr,
+                 "packed_dev, cand_off_dev and totals_dev must not be NULL");
+    PROJ_REQUIRE(k >= 1 && k <= 15 && k <= l, "need 1 <= k <= min(l, 15)");
+    PROJ_REQUIRE(s >= 1, "need s >= 1");
+    PROJ_REQUIRE(trial_begin >= 0 && n_trials >= 0 && n_trials <= 65535,
+                 "need 0 <= n_trials <= 65535 per call");
+    PROJ_REQUIRE(cap_cand >= 0 && cap_members >= 0, "capacities must be >= 0");
+    PROJ_REQUIRE(cap_cand == 0 || (cand_trial_dev && cand_key_dev && cand_cnt_dev),
+                 "candidate buffers must not be NULL");
+    PROJ_REQUIRE(cap_members == 0 || members_dev, "members_dev must not be NULL");
+    Layout L;
+    PROJ_TRY(make_layout(seq_off, t, l, st, L));
+    return run_allpairs(packed_dev, nullptr, 4, L, k, s, seed, trial_begin, n_trials, cap_cand,
+                        cap_members, cand_trial_dev, cand_key_dev, cand_cnt_dev, cand_off_dev,
+                        members_dev, totals_dev, st);
 }

@@ -172,6 +172,14 @@ int launch_finalize_batch(const uint32_t *packed, int64_t nwords, const BatchIns
 int launch_background_batch(const uint32_t *packed, const int64_t *base_range, int n_inst,
                             double *bg, cudaStream_t st);
 
+// All-pairs enrichment (csrc/allpairs.cu) for DNA (alphabet 4, packed input)
+// or proteins (alphabet 20, byte codes).
+int run_allpairs(const uint32_t *packed, const uint8_t *codes, int alphabet, const Layout &L,
+                 int k, int s, uint64_t seed, int64_t trial_begin, int64_t n_trials,
+                 int64_t cap_cand, int64_t cap_members, int32_t *cand_trial_dev,
+                 uint32_t *cand_key_dev, int32_t *cand_cnt_dev, int64_t *cand_off_dev,
+                 int32_t *members_dev, int64_t *totals_dev, cudaStream_t st);
+
 int launch_theta0(const uint32_t *packed, const Layout &L, const int64_t *cand_off,
                   const int32_t *members, int64_t C, float beta, float *theta0, cudaStream_t st);
 
