@@ -20,9 +20,11 @@
 //      the product carries ~16 mantissa bits of W);
 //   3. thread i reads row i of S, keeps a running maximum and a compensated
 //      running sum of 2^(S - max) for its candidate, rescales its row of O when
-//      the maximum grows, and writes P = 2^(S - max) as BF16 hi + lo parts;
+//      the maximum grows, and writes P = 2^(S - max) as BF16 hi + lo parts over
+//      its own columns of S in tensor memory;
 //   4. one thread issues O += P_hi X + P_lo X (M=128, N=16*ceil(4l/16), K=64)
-//      with X read in MN-major form from the same shared-memory tile.
+//      with P read from tensor memory and X in MN-major form from the same
+//      shared-memory tile.
 // The steps of consecutive tiles overlap (two score buffers in tensor memory,
 // a ring of three one-hot tiles): the score MMA of tile i+1 and the count MMA
 // of tile i-1 run on the tensor core while the CUDA cores work on tile i.
@@ -88,16 +90,14 @@ struct TcLayout {
     static constexpr int W_BYTES = 128 * KP * 2;   // each of W_hi, W_lo
     static constexpr int X_BYTES = kNT * KP * 2;   // one one-hot tile
     static constexpr int NX = 3;                   // ring of one-hot tiles
-    static constexpr int P_BYTES = 128 * kNT * 2;  // each of P_hi, P_lo
     static constexpr int OFF_WHI = 0;
     static constexpr int OFF_WLO = OFF_WHI + W_BYTES;
     static constexpr int OFF_X = OFF_WLO + W_BYTES;
-    static constexpr int OFF_PHI = OFF_X + NX * X_BYTES;
-    static constexpr int OFF_PLO = OFF_PHI + P_BYTES;
     static constexpr int SEQ_WORDS = 2048;  // staged packed words of an item (32K bases)
-    static constexpr int OFF_SEQ = OFF_PLO + P_BYTES;
+    static constexpr int OFF_SEQ = OFF_X + NX * X_BYTES;
     static constexpr int TOTAL = OFF_SEQ + SEQ_WORDS * 4;
-    // two score buffers S[2] (kNT columns each) and the count accumulator O (KP)
+    // two score buffers S[2] (kNT columns each; P = 2^(S - m) as BF16 hi + lo
+    // replaces S in place) and the count accumulator O (KP)
     static constexpr uint32_t TMEM_COLS = 256;
     static_assert(2 * kNT + KP <= 256, "tensor-memory budget");
 };
@@ -226,10 +226,12 @@ __device__ __forceinline__ float max_half(const float (&v)[32], int nv) {
 //   issuer: S(0), S(1); then per j: [P(j) written] O (+)= P X(j);
 //           [X(j+2) built, S buffer of j read] S(j+2) = W X(j+2)^T
 //   softmax, per j: [S(j) ready] read S(j), release its buffer; P = 2^(S-m);
-//           [count MMA of j-1 done] write P(j); build X(j+2) into the slot of
-//           tile j-1; at a sequence end [count MMA of j done] read O.
-// Two score buffers in tensor memory, one P buffer and a ring of three one-hot
-// tiles in shared memory.
+//           write P(j) over S(j); [count MMA of j-1 done] build X(j+2) into
+//           the slot of tile j-1; at a sequence end [count MMA of j done] read O.
+// Two score buffers in tensor memory (each holding S(j), then P(j)) and a ring
+// of three one-hot tiles in shared memory.  S(j+2) overwrites P(j) only after
+// the count MMA that reads P(j): tcgen05.mma operations issued by one thread
+// execute in issue order.
 //
 // Reference maximum: P = 2^(S - m) with m = max(exact maximum of the
 // sequence's first tile, top - 100), top = sum_p max_a W the highest score the
@@ -255,7 +257,6 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
     const int quad = warp & 3, half = (warp >> 2) & 1;
     const int row = 32 * quad + lane;
     uint8_t *sWhi = smem + LY::OFF_WHI, *sWlo = smem + LY::OFF_WLO, *sX = smem + LY::OFF_X;
-    uint8_t *sPhi = smem + LY::OFF_PHI, *sPlo = smem + LY::OFF_PLO;
     uint32_t *sSeq = reinterpret_cast<uint32_t *>(smem + LY::OFF_SEQ);
 
     if (tid == 0) {
@@ -386,8 +387,6 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                 const uint64_t dWlo = tc::sdesc(tc::smem_addr(sWlo), 128, KP * 16);
                 const uint64_t dXk = tc::sdesc(tc::smem_addr(sX), 128, KP * 16);   // K-major
                 const uint64_t dXmn = tc::sdesc(tc::smem_addr(sX), KP * 16, 128);  // MN-major
-                const uint64_t dPhi = tc::sdesc(tc::smem_addr(sPhi), 128, NT * 16);
-                const uint64_t dPlo = tc::sdesc(tc::smem_addr(sPlo), 128, NT * 16);
                 auto issue_scores = [&](uint32_t d, uint32_t slot) {
                     const uint64_t dx = dXk + slot * kXSlot;
 #pragma unroll
@@ -412,12 +411,17 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                         tc::fence_after_sync();
                         const uint64_t dx = dXmn + (uint32_t)(j % 3) * kXSlot;
                         const uint32_t acc0 = ti.j0 > 0 ? 1u : 0u;  // O restarts with a sequence
+                        // P(j) in score buffer j&1: l-mers 16s..16s+15 at columns
+                        // 32(s/2) + 8(s%2) (hi) and 16 further (lo)
+                        const uint32_t tP = tm + NT * (uint32_t)(j & 1);
 #pragma unroll
                         for (int s = 0; s < NT / 16; ++s)
-                            tc::mma_bf16(tO, dPhi + 16 * s, dx + 2 * KP * s, idesc_o, s > 0 ? 1u : acc0);
+                            tc::mma_bf16_ts(tO, tP + 32 * (s >> 1) + 8 * (s & 1), dx + 2 * KP * s,
+                                            idesc_o, s > 0 ? 1u : acc0);
 #pragma unroll
                         for (int s = 0; s < NT / 16; ++s)
-                            tc::mma_bf16(tO, dPlo + 16 * s, dx + 2 * KP * s, idesc_o, 1u);
+                            tc::mma_bf16_ts(tO, tP + 32 * (s >> 1) + 16 + 8 * (s & 1),
+                                            dx + 2 * KP * s, idesc_o, 1u);
                         tc::mma_commit(&mbO);
                     }
                     if (j + 2 < n && ok) {
@@ -499,24 +503,28 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                 if (i + 2 < n) tc::mbar_arrive(&mbSfree[b]);  // the issuer may overwrite S(i)
 
                 if (P.mstep) {
-                    wait_o((uint32_t)i);  // the count MMA of tile i-1 has read P and X(i-1)
+                    // P over this thread's own score columns: hi of its 32 l-mers in
+                    // the first 16, lo in the last 16 (the count MMA of tile i-2,
+                    // which read the buffer's previous P, completed before S(i))
 #pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        uint32_t hi[4], lo[4];
+                    for (int g = 0; g < 2; ++g) {
+                        uint32_t hi[8], lo[8];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const float a0 = v[8 * g + 2 * q], a1 = v[8 * g + 2 * q + 1];
+                        for (int q = 0; q < 8; ++q) {
+                            const float a0 = v[16 * g + 2 * q], a1 = v[16 * g + 2 * q + 1];
                             const uint32_t h = pack_bf16(a0, a1);
                             hi[q] = h;
                             lo[q] = pack_bf16(a0 - __uint_as_float(h << 16),
                                               a1 - __uint_as_float(h & 0xFFFF0000u));
                         }
-                        *reinterpret_cast<uint4 *>(sPhi + tc::kmajor_off(row, 32 * half + 8 * g, NT)) =
-                            make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                        *reinterpret_cast<uint4 *>(sPlo + tc::kmajor_off(row, 32 * half + 8 * g, NT)) =
-                            make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                        tc::tmem_st8u(tS + 8 * g, hi);
+                        tc::tmem_st8u(tS + 16 + 8 * g, lo);
                     }
-                    tc::fence_async_smem();
+                    tc::tmem_wait_st();
+                    // count MMA i-1 complete (it read X(i-1), whose slot is rebuilt
+                    // below) before count MMA i can be issued: the parity waits on
+                    // mbO never fall two phases behind
+                    wait_o((uint32_t)i);
                     tc::fence_before_sync();
                     tc::mbar_arrive(&mbPfull);
                 }
