@@ -65,7 +65,7 @@ struct EmTcParams {
     int n_items;
     const float *theta_in;  // [C][stride]
     int stride;             // floats per candidate model (>= 4l of its instance)
-    double *part_acc;       // [G][C][stride]; G == 1 when no candidate tile is split
+    float *part_acc;        // [G][C][stride]; G == 1 when no candidate tile is split
     double *part_ll;        // [G][C]
     double *part_zs;        // [G][C] expected number of sites (ZOOPS)
     int64_t C;
@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
     __shared__ uint32_t tmem_slot;
     __shared__ float sh_x[2][2][kTcRows];  // [slot][half][row] values exchanged by a row's two threads
     __shared__ bool s_last;
+    __shared__ float s_inv[kTcRows];  // 1 / (sites + 4 pseudocount) per candidate of a fold
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool issuer = warp == kSoftThreads / 32;
     const int quad = warp & 3, half = (warp >> 2) & 1;
@@ -579,12 +580,13 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                 // the item covers every sequence: final values directly
                 if (half == 0) P.ll_out[c] = ll;
                 if (P.mstep) {
-                    const double den = (in.gamma < 1.0 ? zs : (double)in.t) + 4.0 * (double)P.beta;
+                    // FP32 (the counts are FP32 sums; FP64 is a narrow pipe here)
+                    const float inv =
+                        1.f / (float)((in.gamma < 1.0 ? zs : (double)in.t) + 4.0 * (double)P.beta);
                     float *dst = P.theta_out + c * P.stride + half * KH;
 #pragma unroll
                     for (int q = 0; q < KH; ++q)
-                        if (half * KH + q < L4)
-                            dst[q] = (float)(((double)tot[q] + (double)P.beta) / den);
+                        if (half * KH + q < L4) dst[q] = (tot[q] + P.beta) * inv;
                 }
             } else if (ok && valid) {
                 if (half == 0) {
@@ -592,10 +594,10 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                     P.part_zs[(int64_t)item.g * P.C + c] = zs;
                 }
                 if (P.mstep) {
-                    double *dst = P.part_acc + ((int64_t)item.g * P.C + c) * P.stride + half * KH;
+                    float *dst = P.part_acc + ((int64_t)item.g * P.C + c) * P.stride + half * KH;
 #pragma unroll
                     for (int q = 0; q < KH; ++q)
-                        if (half * KH + q < L4) dst[q] = (double)tot[q];
+                        if (half * KH + q < L4) dst[q] = tot[q];
                 }
             }
         }
@@ -612,22 +614,27 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
         }
         if (fold && s_last) {
             __threadfence();
+            if (P.mstep && tid < item.nc) {
+                double sites = (double)in.t;  // OOPS: one site per sequence
+                if (in.gamma < 1.0) {
+                    sites = 0.0;
+                    for (int g = 0; g < P.G; ++g)
+                        sites += __ldcg(P.part_zs + (int64_t)g * P.C + item.c0 + tid);
+                }
+                s_inv[tid] = 1.f / (float)(sites + 4.0 * (double)P.beta);
+            }
+            __syncthreads();
             const int width = P.mstep ? L4 : 0;
             for (int e = tid; e < item.nc * (width + 1); e += kTcThreads) {
                 const int cc = e / (width + 1), q = e - cc * (width + 1);
                 const int64_t cg = item.c0 + cc;
-                double acc = 0.0;
                 if (q < width) {
+                    float acc = 0.f;
                     for (int g = 0; g < P.G; ++g)
                         acc += __ldcg(P.part_acc + ((int64_t)g * P.C + cg) * P.stride + q);
-                    double sites = (double)in.t;  // OOPS: one site per sequence
-                    if (in.gamma < 1.0) {
-                        sites = 0.0;
-                        for (int g = 0; g < P.G; ++g) sites += __ldcg(P.part_zs + (int64_t)g * P.C + cg);
-                    }
-                    P.theta_out[cg * P.stride + q] =
-                        (float)((acc + (double)P.beta) / (sites + 4.0 * (double)P.beta));
+                    P.theta_out[cg * P.stride + q] = (acc + P.beta) * s_inv[cc];
                 } else {
+                    double acc = 0.0;
                     for (int g = 0; g < P.G; ++g) acc += __ldcg(P.part_ll + (int64_t)g * P.C + cg);
                     P.ll_out[cg] = acc;
                 }
@@ -650,7 +657,7 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
 // M-step theta = (sum_g counts + pseudocount) / (t + 4 pseudocount) and the
 // log-likelihood sum over the G sequence groups, in group order (used when G
 // is above kFoldMaxG).
-__global__ void em_tc_reduce_kernel(const double *__restrict__ part_acc,
+__global__ void em_tc_reduce_kernel(const float *__restrict__ part_acc,
                                     const double *__restrict__ part_ll,
                                     const double *__restrict__ part_zs, int G, int64_t C,
                                     int stride, const EmInst *__restrict__ inst, int n_inst,
@@ -667,13 +674,14 @@ __global__ void em_tc_reduce_kernel(const double *__restrict__ part_acc,
         if (inst[mid].cand_begin <= (int64_t)c) lo = mid; else hi = mid - 1;
     }
     if (mstep && (int)q < 4 * inst[lo].l) {
-        double s = 0.0, sites = (double)inst[lo].t;  // OOPS: one site per sequence
+        float s = 0.f;
+        double sites = (double)inst[lo].t;  // OOPS: one site per sequence
         for (int g = 0; g < G; ++g) s += part_acc[((int64_t)g * C + c) * stride + q];
         if (inst[lo].gamma < 1.0) {
             sites = 0.0;
             for (int g = 0; g < G; ++g) sites += part_zs[(int64_t)g * C + c];
         }
-        theta_out[idx] = (float)((s + (double)beta) / (sites + 4.0 * (double)beta));
+        theta_out[idx] = (s + beta) / (float)(sites + 4.0 * (double)beta);
     }
     if (q == 0) {
         double s = 0.0;
@@ -860,7 +868,8 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
         em_tc_plan(insts, items, G, sched.ctas, sched.waves);
         Gmax = std::max(Gmax, G);
     }
-    PROJ_TRY(run.part.alloc((size_t)Gmax * C * (stride + 2) * sizeof(double), st));
+    // part_ll, part_zs [G][C] double, then part_acc [G][C][stride] float
+    PROJ_TRY(run.part.alloc((size_t)Gmax * C * (2 * sizeof(double) + stride * sizeof(float)), st));
     PROJ_TRY(run.tmp.alloc((size_t)C * stride * sizeof(float), st));
     PROJ_TRY(run.flag.alloc(sizeof(int), st));
     PROJ_CUDA_TRY(cudaMemsetAsync(run.flag.as<int>(), 0, sizeof(int), st));
@@ -892,7 +901,7 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
             P.packed = packed; P.nwords = nwords; P.inst = inst_dev; P.items = ib.as<EmItem>();
             P.n_items = (int)items.size(); P.theta_in = run.tmp.as<float>(); P.stride = stride;
             P.part_ll = run.part.as<double>(); P.part_zs = run.part.as<double>() + (size_t)G * C;
-            P.part_acc = run.part.as<double>() + (size_t)2 * G * C;
+            P.part_acc = reinterpret_cast<float *>(run.part.as<double>() + (size_t)2 * G * C);
             P.C = C; P.err = run.flag.as<int>(); P.mstep = 1; P.G = G; P.beta = 0.25f;
             P.theta_out = run.tmp.as<float>(); P.ll_out = ll_scratch.as<double>();
             P.tile_done = run.tiles.as<uint32_t>();
@@ -951,7 +960,7 @@ int em_tc_enqueue(EmTcRun &run, int iters, float beta, float *theta_out, double 
     P.stride = stride;
     P.part_ll = run.part.as<double>();
     P.part_zs = run.part.as<double>() + (size_t)G * C;
-    P.part_acc = run.part.as<double>() + (size_t)2 * G * C;
+    P.part_acc = reinterpret_cast<float *>(run.part.as<double>() + (size_t)2 * G * C);
     P.C = C;
     P.G = G;
     P.beta = beta;

@@ -43,13 +43,30 @@ __global__ void pack_kernel(const uint8_t *__restrict__ ascii, int64_t total,
     }
 }
 
+// Block-wide sums of three per-thread counts (warp shuffles, then warp order);
+// the result is valid in thread 0.  blockDim.x is a multiple of 32.
+__device__ __forceinline__ void block_sum3(unsigned long long &a, unsigned long long &b,
+                                           unsigned long long &c) {
+    __shared__ unsigned long long part[32][3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) { part[warp][0] = a; part[warp][1] = b; part[warp][2] = c; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = b = c = 0ull;
+        for (int w = 0; w < nw; ++w) { a += part[w][0]; b += part[w][1]; c += part[w][2]; }
+    }
+}
+
 // Base counts by popcount over packed words (single CTA; the input is a few
-// hundred KB at most for the workloads in scope).
+// MB at most for the workloads in scope).
 __global__ void background_kernel(const uint32_t *__restrict__ packed, int64_t total,
                                   double *__restrict__ bg) {
-    __shared__ unsigned long long cnt[4];
-    if (threadIdx.x < 4) cnt[threadIdx.x] = 0ull;
-    __syncthreads();
     unsigned long long c1 = 0, c2 = 0, c3 = 0;  // C, T, G (A = rest)
     const int64_t nw = (total + 15) >> 4;
     for (int64_t w = threadIdx.x; w < nw; w += blockDim.x) {
@@ -61,13 +78,10 @@ __global__ void background_kernel(const uint32_t *__restrict__ packed, int64_t t
         c2 += __popc(hi & ~lo);
         c3 += __popc(lo & hi);
     }
-    atomicAdd(&cnt[1], c1);
-    atomicAdd(&cnt[2], c2);
-    atomicAdd(&cnt[3], c3);
-    __syncthreads();
+    block_sum3(c1, c2, c3);
     if (threadIdx.x == 0) {
         unsigned long long c[4];
-        c[1] = cnt[1]; c[2] = cnt[2]; c[3] = cnt[3];
+        c[1] = c1; c[2] = c2; c[3] = c3;
         c[0] = (unsigned long long)total - c[1] - c[2] - c[3];
         unsigned long long tot = 0;
         for (int a = 0; a < 4; ++a) { if (c[a] == 0) c[a] = 1; tot += c[a]; }
@@ -80,9 +94,6 @@ __global__ void background_kernel(const uint32_t *__restrict__ packed, int64_t t
 __global__ void background_batch_kernel(const uint32_t *__restrict__ packed,
                                         const int64_t *__restrict__ base_range,
                                         double *__restrict__ bg) {
-    __shared__ unsigned long long cnt[4];
-    if (threadIdx.x < 4) cnt[threadIdx.x] = 0ull;
-    __syncthreads();
     const int64_t b0 = base_range[2 * blockIdx.x], b1 = base_range[2 * blockIdx.x + 1];
     unsigned long long c1 = 0, c2 = 0, c3 = 0;
     for (int64_t w = (b0 >> 4) + threadIdx.x; w <= ((b1 - 1) >> 4); w += blockDim.x) {
@@ -97,13 +108,10 @@ __global__ void background_batch_kernel(const uint32_t *__restrict__ packed,
         c2 += __popc(hi2 & ~lo2);
         c3 += __popc(lo2 & hi2);
     }
-    atomicAdd(&cnt[1], c1);
-    atomicAdd(&cnt[2], c2);
-    atomicAdd(&cnt[3], c3);
-    __syncthreads();
+    block_sum3(c1, c2, c3);
     if (threadIdx.x == 0) {
         unsigned long long c[4];
-        c[1] = cnt[1]; c[2] = cnt[2]; c[3] = cnt[3];
+        c[1] = c1; c[2] = c2; c[3] = c3;
         c[0] = (unsigned long long)(b1 - b0) - c[1] - c[2] - c[3];
         unsigned long long tot = 0;
         for (int a = 0; a < 4; ++a) { if (c[a] == 0) c[a] = 1; tot += c[a]; }

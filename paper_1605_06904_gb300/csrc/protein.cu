@@ -39,14 +39,14 @@ __global__ void aa_pack_kernel(const uint8_t *__restrict__ ascii, int64_t n,
 // 0-order residue frequencies (an absent residue counts once, as for DNA).
 __global__ void aa_background_kernel(const uint8_t *__restrict__ codes, int64_t n,
                                      double *__restrict__ bg) {
-    __shared__ unsigned long long cnt[kAA];
-    if (threadIdx.x < kAA) cnt[threadIdx.x] = 0ull;
+    __shared__ unsigned int cnt[kAA];  // inputs hold < 2^31 residues
+    if (threadIdx.x < kAA) cnt[threadIdx.x] = 0u;
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&cnt[codes[i]], 1ull);
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&cnt[codes[i]], 1u);
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long tot = 0;
-        for (int a = 0; a < kAA; ++a) { if (cnt[a] == 0) cnt[a] = 1; tot += cnt[a]; }
+        for (int a = 0; a < kAA; ++a) { if (cnt[a] == 0u) cnt[a] = 1u; tot += cnt[a]; }
         for (int a = 0; a < kAA; ++a) bg[a] = (double)cnt[a] / (double)tot;
     }
 }
