@@ -279,6 +279,48 @@ int projection_finalize(const uint32_t *packed_dev, const int64_t *seq_off, int 
                            consensus_dev, score_dev, st);
 }
 
+// The winner's model, log-likelihood and (trial, key) gathered on the device so
+// that the search's results come back in one copy.  sel (may be NULL) maps a
+// refined candidate to its index in the full list.
+__global__ void winner_kernel(const int64_t *__restrict__ best, const int64_t *__restrict__ sel,
+                              const float *__restrict__ theta, int L4,
+                              const double *__restrict__ ll, const int32_t *__restrict__ cand_trial,
+                              const uint32_t *__restrict__ cand_key, int64_t *__restrict__ win,
+                              double *__restrict__ ll_w, int32_t *__restrict__ trial_w,
+                              uint32_t *__restrict__ key_w, float *__restrict__ pwm_w) {
+    const int64_t b = *best;
+    const int tid = threadIdx.x;
+    if (b < 0) {
+        if (tid == 0) {
+            *win = -1;
+            *ll_w = -INFINITY;
+            *trial_w = -1;
+            *key_w = 0u;
+        }
+        for (int q = tid; q < L4; q += blockDim.x) pwm_w[q] = 0.f;
+        return;
+    }
+    const int64_t bo = sel ? sel[b] : b;
+    if (tid == 0) {
+        *win = bo;
+        *ll_w = ll[b];
+        *trial_w = cand_trial[bo];
+        *key_w = cand_key[bo];
+    }
+    for (int q = tid; q < L4; q += blockDim.x) pwm_w[q] = theta[b * L4 + q];
+}
+
+// Fixed head of a search's small device buffer (read back in one copy); the
+// sites [t], the winner's model [4l] and the consensus [l] follow it.
+struct SearchHead {
+    double bg[4];
+    int64_t totals[2];
+    int64_t best, win;
+    double ll;
+    int32_t score, err, trial;
+    uint32_t key;
+};
+
 static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int l, int d, int k,
                      int s, int m, uint64_t seed, int em_iters, float pseudocount, int precision,
                      int64_t top, projection_result *out, cudaStream_t st, double gamma = 1.0) {
@@ -295,15 +337,18 @@ static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int 
     PROJ_REQUIRE(s >= 1 && m >= 1, "need s >= 1 and m >= 1");
     out->t = t; out->l = l; out->k = k; out->s = s; out->m = m;
 
-    DevBuf small;  // bg[4] | totals[2] | best | score | sites[t] | consensus[l]
-    const size_t small_bytes = 4 * 8 + 2 * 8 + 8 + 8 + (size_t)t * 4 + (size_t)l + 16;
-    PROJ_TRY(small.alloc(small_bytes, st));
-    double *bg = small.as<double>();
-    int64_t *totals = reinterpret_cast<int64_t *>(bg + 4);
-    int64_t *best = totals + 2;
-    int32_t *score = reinterpret_cast<int32_t *>(best + 1);
-    int32_t *sites = score + 2;
-    uint8_t *cons = reinterpret_cast<uint8_t *>(sites + t);
+    DevBuf small;  // SearchHead | sites[t] | pwm[4l] | consensus[l]
+    const size_t small_bytes = sizeof(SearchHead) + (size_t)t * 4 + (size_t)16 * l + (size_t)l;
+    PROJ_TRY(small.alloc(small_bytes + 16, st));
+    PROJ_CUDA_TRY(cudaMemsetAsync(small.as<void>(), 0, sizeof(SearchHead), st));
+    SearchHead *head = small.as<SearchHead>();
+    double *bg = head->bg;
+    int64_t *totals = head->totals;
+    int64_t *best = &head->best;
+    int32_t *score = &head->score;
+    int32_t *sites = reinterpret_cast<int32_t *>(head + 1);
+    float *pwm_w = reinterpret_cast<float *>(sites + t);
+    uint8_t *cons = reinterpret_cast<uint8_t *>(pwm_w + 4 * l);
     PROJ_TRY(launch_background(packed, L.total, bg, st));
 
     // pass sizes: count first, then size the candidate list exactly
@@ -361,14 +406,30 @@ static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int 
     double *ll = model.as<double>();
     float *theta = reinterpret_cast<float *>(ll + R);
     PROJ_TRY(launch_theta0(packed, L, r_off, r_members, R, pseudocount, theta, st));
-    PROJ_TRY(run_em(packed, L, bg, theta, R, em_iters, pseudocount, precision, theta, ll, st, gamma));
+    PROJ_TRY(run_em(packed, L, bg, theta, R, em_iters, pseudocount, precision, theta, ll, st, gamma,
+                    &head->err));
     PROJ_TRY(launch_finalize(packed, L, bg, theta, ll, R, best, sites, cons, score, st));
+    DevBuf sel_dev;  // refined candidate -> index in the full list (top selection only)
+    if (!sel.empty()) {
+        PROJ_TRY(sel_dev.alloc(sel.size() * sizeof(int64_t), st));
+        PROJ_CUDA_TRY(cudaMemcpyAsync(sel_dev.as<int64_t>(), sel.data(), sel.size() * sizeof(int64_t),
+                                      cudaMemcpyHostToDevice, st));
+    }
+    winner_kernel<<<1, 128, 0, st>>>(best, sel.empty() ? nullptr : sel_dev.as<int64_t>(), theta,
+                                     4 * l, ll, ho.cand_trial, ho.cand_key, &head->win, &head->ll,
+                                     &head->trial, &head->key, pwm_w);
+    PROJ_LAUNCH_CHECK("winner_kernel");
 
-    int64_t b = -1;
-    PROJ_CUDA_TRY(cudaMemcpyAsync(&b, best, sizeof b, cudaMemcpyDeviceToHost, st));
+    std::vector<uint8_t> res(small_bytes);
+    PROJ_CUDA_TRY(cudaMemcpyAsync(res.data(), small.as<void>(), small_bytes, cudaMemcpyDeviceToHost, st));
     PROJ_CUDA_TRY(cudaStreamSynchronize(st));
-    const int64_t b_orig = (b >= 0 && !sel.empty()) ? sel[b] : b;  // index in the full list
-    out->win_index = b_orig;
+    SearchHead h;
+    memcpy(&h, res.data(), sizeof h);
+    if (h.err) {
+        set_error("a bounded wait for tensor-core completion expired in em_tc_kernel");
+        return PROJ_ETIMEOUT;
+    }
+    out->win_index = h.win;
     out->pwm = (float *)calloc((size_t)4 * l, sizeof(float));
     out->consensus = (char *)calloc((size_t)l + 1, 1);
     out->sites = (int32_t *)calloc((size_t)t, sizeof(int32_t));
@@ -376,19 +437,15 @@ static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int 
         set_error("host allocation failed");
         return PROJ_ENOMEM;
     }
-    PROJ_CUDA_TRY(cudaMemcpyAsync(out->sites, sites, (size_t)t * 4, cudaMemcpyDeviceToHost, st));
-    PROJ_CUDA_TRY(cudaMemcpyAsync(out->consensus, cons, (size_t)l, cudaMemcpyDeviceToHost, st));
-    PROJ_CUDA_TRY(cudaMemcpyAsync(&out->score, score, 4, cudaMemcpyDeviceToHost, st));
-    if (b >= 0) {
-        PROJ_CUDA_TRY(cudaMemcpyAsync(out->pwm, theta + b * 4 * l, (size_t)4 * l * sizeof(float),
-                                      cudaMemcpyDeviceToHost, st));
-        PROJ_CUDA_TRY(cudaMemcpyAsync(&out->loglik, ll + b, 8, cudaMemcpyDeviceToHost, st));
-        PROJ_CUDA_TRY(cudaMemcpyAsync(&out->win_trial, ho.cand_trial + b_orig, 4, cudaMemcpyDeviceToHost, st));
-        PROJ_CUDA_TRY(cudaMemcpyAsync(&out->win_key, ho.cand_key + b_orig, 4, cudaMemcpyDeviceToHost, st));
-    }
-    PROJ_CUDA_TRY(cudaStreamSynchronize(st));
+    memcpy(out->sites, res.data() + sizeof(SearchHead), (size_t)t * 4);
+    memcpy(out->pwm, res.data() + sizeof(SearchHead) + (size_t)t * 4, (size_t)16 * l);
+    memcpy(out->consensus, res.data() + sizeof(SearchHead) + (size_t)t * 4 + (size_t)16 * l, (size_t)l);
+    out->score = h.score;
+    out->loglik = h.ll;
+    out->win_trial = h.trial;
+    out->win_key = h.key;
     out->consensus[l] = 0;
-    if (b < 0) {
+    if (h.win < 0) {
         out->loglik = -INFINITY;
         out->win_trial = -1;
         out->win_key = 0;

@@ -183,9 +183,12 @@ int run_allpairs(const uint32_t *packed, const uint8_t *codes, int alphabet, con
 int launch_theta0(const uint32_t *packed, const Layout &L, const int64_t *cand_off,
                   const int32_t *members, int64_t C, float beta, float *theta0, cudaStream_t st);
 
+// err_dev: when not NULL, the tensor-core path's timeout flag (int, nonzero =
+// PROJ_ETIMEOUT) is copied there on the stream and not checked here, so the
+// caller can read it with its results instead of synchronising in between.
 int run_em(const uint32_t *packed, const Layout &L, const double *bg, const float *theta0,
            int64_t C, int iters, float beta, int precision, float *theta_out, double *ll,
-           cudaStream_t st, double gamma = 1.0);
+           cudaStream_t st, double gamma = 1.0, int *err_dev = nullptr);
 
 int launch_finalize(const uint32_t *packed, const Layout &L, const double *bg,
                     const float *theta, const double *ll, int64_t C, int64_t *best,

@@ -21,7 +21,7 @@ namespace proj {
 
 int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const float *theta0,
               int64_t C, int iters, float beta, float *theta_out, double *ll, cudaStream_t st,
-              double gamma);
+              double gamma, int *err_dev);
 
 namespace {
 
@@ -462,7 +462,7 @@ int launch_theta0(const uint32_t *packed, const Layout &L, const int64_t *cand_o
 
 int run_em(const uint32_t *packed, const Layout &L, const double *bg, const float *theta0,
            int64_t C, int iters, float beta, int precision, float *theta_out, double *ll,
-           cudaStream_t st, double gamma) {
+           cudaStream_t st, double gamma, int *err_dev) {
     PROJ_REQUIRE(iters >= 0 && iters <= 1000, "em_iters out of range: %d", iters);
     PROJ_REQUIRE(beta > 0.f, "pseudocount must be > 0");
     PROJ_REQUIRE(precision == PROJ_EM_FP32 || precision == PROJ_EM_BF16_SPLIT,
@@ -470,7 +470,7 @@ int run_em(const uint32_t *packed, const Layout &L, const double *bg, const floa
     if (C == 0) return PROJ_OK;
     PROJ_REQUIRE(gamma > 0.0 && gamma <= 1.0, "site probability must be in (0, 1]");
     if (precision == PROJ_EM_BF16_SPLIT)
-        return run_em_tc(packed, L, bg, theta0, C, iters, beta, theta_out, ll, st, gamma);
+        return run_em_tc(packed, L, bg, theta0, C, iters, beta, theta_out, ll, st, gamma, err_dev);
 
     const int L4 = 4 * L.l;
     // enough (candidate-tile, sequence-group) units to fill every SM a few times

@@ -58,12 +58,15 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
                   EmTcRun &run, cudaStream_t st);
 int em_tc_enqueue(EmTcRun &run, int iters, float beta, float *theta_out, double *ll,
                   cudaStream_t st);
-int em_tc_finish(EmTcRun &run, cudaStream_t st);
+// Checks the launches' timeout flag (synchronises), or with err_dev copies it
+// there on the stream for the caller to check later.
+int em_tc_finish(EmTcRun &run, cudaStream_t st, int *err_dev = nullptr);
 
 // Runs iters EM iterations + a final E-step for the candidates of all
 // instances (models theta0[C][stride], stride >= 4l of each instance).
 int run_em_tc_batch(const uint32_t *packed, int64_t nwords, const std::vector<EmInstHost> &insts,
                     const EmInst *inst_dev, const float *theta0, int64_t C, int stride, int iters,
-                    float beta, float *theta_out, double *ll, cudaStream_t st);
+                    float beta, float *theta_out, double *ll, cudaStream_t st,
+                    int *err_dev = nullptr);
 
 }  // namespace proj

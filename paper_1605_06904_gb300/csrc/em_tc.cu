@@ -990,8 +990,13 @@ int em_tc_enqueue(EmTcRun &run, int iters, float beta, float *theta_out, double 
     return PROJ_OK;
 }
 
-int em_tc_finish(EmTcRun &run, cudaStream_t st) {
+int em_tc_finish(EmTcRun &run, cudaStream_t st, int *err_dev) {
     if (run.C == 0) return PROJ_OK;
+    if (err_dev) {
+        PROJ_CUDA_TRY(cudaMemcpyAsync(err_dev, run.flag.as<int>(), sizeof(int),
+                                      cudaMemcpyDeviceToDevice, st));
+        return PROJ_OK;
+    }
     int err = 0;
     PROJ_CUDA_TRY(cudaMemcpyAsync(&err, run.flag.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
     PROJ_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1004,19 +1009,19 @@ int em_tc_finish(EmTcRun &run, cudaStream_t st) {
 
 int run_em_tc_batch(const uint32_t *packed, int64_t nwords, const std::vector<EmInstHost> &insts,
                     const EmInst *inst_dev, const float *theta0, int64_t C, int stride, int iters,
-                    float beta, float *theta_out, double *ll, cudaStream_t st) {
+                    float beta, float *theta_out, double *ll, cudaStream_t st, int *err_dev) {
     EmTcRun run;
     if (C == 0) return PROJ_OK;
     PROJ_TRY(em_tc_prepare(packed, nwords, insts, inst_dev, theta0, C, stride, run, st));
     PROJ_TRY(run_as_graph(kGraphEm, st, [&](cudaStream_t cs) {
         return em_tc_enqueue(run, iters, beta, theta_out, ll, cs);
     }));
-    return em_tc_finish(run, st);
+    return em_tc_finish(run, st, err_dev);
 }
 
 int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const float *theta0,
               int64_t C, int iters, float beta, float *theta_out, double *ll, cudaStream_t st,
-              double gamma) {
+              double gamma, int *err_dev) {
     std::vector<EmInstHost> insts(1);
     insts[0].t = L.t;
     insts[0].l = L.l;
@@ -1035,7 +1040,7 @@ int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const f
     PROJ_TRY(ib.alloc(sizeof(EmInst), st));
     PROJ_CUDA_TRY(cudaMemcpyAsync(ib.as<EmInst>(), &in, sizeof(EmInst), cudaMemcpyHostToDevice, st));
     return run_em_tc_batch(packed, L.nwords, insts, ib.as<EmInst>(), theta0, C, 4 * L.l, iters,
-                           beta, theta_out, ll, st);
+                           beta, theta_out, ll, st, err_dev);
 }
 
 }  // namespace proj
