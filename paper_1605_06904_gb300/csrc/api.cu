@@ -323,7 +323,10 @@ struct SearchHead {
 
 static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int l, int d, int k,
                      int s, int m, uint64_t seed, int em_iters, float pseudocount, int precision,
-                     int64_t top, projection_result *out, cudaStream_t st, double gamma = 1.0) {
+                     int64_t top, projection_result *out, cudaStream_t st, double gamma = 1.0,
+                     const int64_t *bad_dev = nullptr, const uint8_t *ascii = nullptr) {
+    // bad_dev: the pack kernel's first non-ACGT index (or -1), checked at the
+    // first synchronisation of the search
     PROJ_REQUIRE(packed != nullptr, "packed input must not be NULL");
     PROJ_REQUIRE(d >= 0 && d < l, "need 0 <= d < l");
     Layout L;
@@ -361,9 +364,16 @@ static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int 
     probe.cand_off = off0.as<int64_t>();
     probe.count_only = true;
     PROJ_TRY(run_trial_hash(packed, L, k, s, seed, 0, m, nullptr, probe, st));
-    int64_t tot_h[2];
+    int64_t tot_h[2], bad_h = -1;
     PROJ_CUDA_TRY(cudaMemcpyAsync(tot_h, totals, sizeof tot_h, cudaMemcpyDeviceToHost, st));
+    if (bad_dev)
+        PROJ_CUDA_TRY(cudaMemcpyAsync(&bad_h, bad_dev, sizeof bad_h, cudaMemcpyDeviceToHost, st));
     PROJ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (bad_h >= 0) {
+        set_error("character %d at index %lld is not A/C/G/T", ascii ? (int)ascii[bad_h] : -1,
+                  (long long)bad_h);
+        return PROJ_EBADCHAR;
+    }
     const int64_t C = tot_h[0], M = tot_h[1];
     out->n_candidates = C;
     out->n_members = M;
@@ -527,16 +537,8 @@ static int find_host(const uint8_t *ascii, const int64_t *seq_off, int t, int l,
     if (e != cudaSuccess) { set_error("H2D copy failed: %s", cudaGetErrorString(e)); return fail(PROJ_ECUDA); }
     rc = launch_pack(ascii_dev, total, packed, bad, st);
     if (rc) return fail(rc);
-    int64_t bad_h = -1;
-    e = cudaMemcpyAsync(&bad_h, bad, 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) { set_error("D2H copy failed: %s", cudaGetErrorString(e)); return fail(PROJ_ECUDA); }
-    if (bad_h >= 0) {
-        set_error("character %d at index %lld is not A/C/G/T", (int)ascii[bad_h], (long long)bad_h);
-        return fail(PROJ_EBADCHAR);
-    }
     rc = find_impl(packed, seq_off, t, l, d, k, s, m, seed, em_iters, pseudocount, precision, top,
-                   out, st);
+                   out, st, 1.0, bad, ascii);
     out->status = rc;
     return rc;
 }

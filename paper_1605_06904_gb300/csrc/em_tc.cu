@@ -442,7 +442,9 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
             float tot[KH];  // this item's normalised counts of candidate c, columns of this half
 #pragma unroll
             for (int q = 0; q < KH; ++q) tot[q] = 0.f;
-            double ll = 0.0, zs = 0.0;  // zs: expected number of sites (ZOOPS)
+            // per-sequence log-likelihoods and (ZOOPS) expected site counts, summed
+            // in compensated FP32 (the FP64 pipe is narrow on this part)
+            float ll_s = 0.f, ll_c = 0.f, zs_s = 0.f, zs_c = 0.f;
             const bool zoops = in.gamma < 1.0;
             const float log_gamma = zoops ? logf((float)in.gamma) : 0.f;
             const float log_no = zoops ? log1pf(-(float)in.gamma) : 0.f;
@@ -551,11 +553,11 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                         const float hi = fmaxf(log_no, lg), lo = fminf(log_no, lg);
                         const float Li = hi + log1pf(expf(lo - hi));
                         w = expf(lg - Li);
-                        ll += (double)Li;
+                        kahan(ll_s, ll_c, Li);
                     } else {
-                        ll += (double)((m + log2f(Sf)) * 0.69314718f - logf((float)tcur.ns));
+                        kahan(ll_s, ll_c, (m + log2f(Sf)) * 0.69314718f - logf((float)tcur.ns));
                     }
-                    zs += (double)w;
+                    kahan(zs_s, zs_c, w);
                     if (P.mstep) {
                         wait_o((uint32_t)i + 1);
                         tc::fence_after_sync();
@@ -576,6 +578,7 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                 }
                 tcur.advance(in, item.seq_hi);
             }
+            const double ll = (double)ll_s - (double)ll_c, zs = (double)zs_s - (double)zs_c;
             if (ok && valid && P.G == 1) {
                 // the item covers every sequence: final values directly
                 if (half == 0) P.ll_out[c] = ll;
