@@ -85,7 +85,7 @@ __global__ void aa_theta0_kernel(const uint8_t *__restrict__ codes,
 // One OOPS EM iteration (E-step + optional M-step) for one candidate per CTA.
 // Warps take sequences in turn, lanes take l-mers: pass A gives every lane a
 // running (max, sum) of e^r in FP32 (r = sum_p W[p][x], W = log theta - log
-// bg), merged across lanes in FP64 into L_i = log sum_j e^{r(i,j)}; pass B
+// bg), merged across lanes into L_i = log sum_j e^{r(i,j)}; pass B
 // recomputes r and adds z = e^{r - L_i} to the counts of the l letters of its
 // l-mer.  Counts are fixed point in units of 2^-31: a warp sums its current
 // sequence with 32-bit integer atomics (a sequence's z sum to 1, so every
@@ -93,7 +93,9 @@ __global__ void aa_theta0_kernel(const uint8_t *__restrict__ codes,
 // totals.  Integer sums do not depend on the order of the additions, and the
 // per-warp log-likelihoods are summed in warp order, so results are
 // deterministic.  The M-step writes theta = (counts + beta) / (t + 20 beta)
-// (Section 5.1) directly.
+// (Section 5.1) directly.  Transcendentals and divisions are FP32 (the FP64
+// pipe of this part runs 2 lanes per clock per SM); the per-sequence terms
+// are summed in FP64.
 constexpr int kAaEmThreads = 256;
 constexpr int kAaEmWarps = kAaEmThreads / 32;
 constexpr float kFix = 2147483648.f;  // 2^31
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(kAaEmThreads) aa_em_kernel(
     const int64_t c = blockIdx.x;
     unsigned int *a32 = seq_acc[warp];
     for (int q = tid; q < L20; q += kAaEmThreads) {
-        W[q] = logf(theta_in[c * L20 + q]) - (float)log(bg[q % kAA]);
+        W[q] = logf(theta_in[c * L20 + q]) - logf((float)bg[q % kAA]);
         acc[q] = 0ull;
     }
     for (int q = lane; q < L20; q += 32) a32[q] = 0u;
@@ -134,12 +136,12 @@ __global__ void __launch_bounds__(kAaEmThreads) aa_em_kernel(
         float M = m;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) M = fmaxf(M, __shfl_xor_sync(0xffffffffu, M, o));
-        double Sd = S > 0.f ? (double)S * exp((double)m - (double)M) : 0.0;
+        float Sf = S > 0.f ? S * expf(m - M) : 0.f;  // lane sums relative to the warp maximum
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) Sd += __shfl_xor_sync(0xffffffffu, Sd, o);
-        ll += (double)M + log(Sd) - log((double)ns);
+        for (int o = 16; o > 0; o >>= 1) Sf += __shfl_xor_sync(0xffffffffu, Sf, o);
+        ll += (double)(M + logf(Sf) - logf((float)ns));
         if (mstep) {
-            const float scale = (float)(1.0 / Sd) * kFix;
+            const float scale = kFix / Sf;
             for (int j = lane; j < ns; j += 32) {
                 float r = 0.f;
                 for (int p = 0; p < l; ++p) r += W[p * kAA + seq[j + p]];
@@ -165,9 +167,9 @@ __global__ void __launch_bounds__(kAaEmThreads) aa_em_kernel(
         ll_out[c] = tot;
     }
     if (mstep) {
-        const double den = (double)t + (double)kAA * (double)beta;
+        const float inv = 1.f / ((float)t + (float)kAA * beta);
         for (int q = tid; q < L20; q += kAaEmThreads)
-            theta_out[c * L20 + q] = (float)(((double)acc[q] / (double)kFix + (double)beta) / den);
+            theta_out[c * L20 + q] = ((float)acc[q] * (1.f / kFix) + beta) * inv;
     }
 }
 
