@@ -28,6 +28,14 @@ struct EmItem {
     int seq_lo, seq_hi;
     int g;           // sequence group, selects the partial-result slot
     int n_tiles;     // tiles of 64 l-mers over the item's sequences
+    int64_t tile0;   // index of its first tile in the run's one-hot tile array
+};
+
+// One sequence as the one-hot tile builder sees it.
+struct XSeq {
+    int64_t base;    // first base in the packed input
+    int64_t tile;    // index of its first tile
+    int ns, l;       // l-mers, motif length
 };
 
 // Host-side summary used to plan the items.
@@ -52,6 +60,7 @@ struct EmTcRun {
     int64_t C = 0;
     int stride = 0, n_inst = 0, kp = 16, G = 1, ctas = 3, n_items = 0;
     DevBuf part, tmp, flag, items, tiles;
+    DevBuf xt, xseq;  // one-hot tiles [n_x_tiles][64][kp] BF16 (K-major core layout), their sequences
 };
 int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmInstHost> &insts,
                   const EmInst *inst_dev, const float *theta0, int64_t C, int stride,

@@ -13,8 +13,9 @@
 // memory) takes items in turn from the list (persistent over the list when the
 // grid is smaller than it), so one launch serves one motif search or a batch of
 // many instances of different t, n and l.  Per tile of 64 l-mers of a sequence:
-//   1. the CTA writes the one-hot tile X [64 x 4l] to shared memory (from the
-//      item's packed words, staged in shared memory);
+//   1. one thread copies the one-hot tile X [64 x 4l] into shared memory with a
+//      bulk asynchronous copy (the tiles depend only on the sequences and are
+//      built once per EM run, in the MMA operand layout, by em_xtiles_kernel);
 //   2. one thread issues S = W_hi X^T + W_lo X^T (M=128, N=64, K=16*ceil(4l/16),
 //      FP32 accumulation in tensor memory; W split into BF16 hi + lo parts so
 //      the product carries ~16 mantissa bits of W);
@@ -76,6 +77,7 @@ struct EmTcParams {
                             // rewritten only after every item reading them is done)
     double *ll_out;         // [C]
     uint32_t *tile_done;    // [n_items / G] finished items per tile, 0 between launches
+    const uint8_t *xt;      // one-hot tiles of every sequence, X_BYTES each
     int *err;
 };
 
@@ -93,9 +95,7 @@ struct TcLayout {
     static constexpr int OFF_WHI = 0;
     static constexpr int OFF_WLO = OFF_WHI + W_BYTES;
     static constexpr int OFF_X = OFF_WLO + W_BYTES;
-    static constexpr int SEQ_WORDS = 2048;  // staged packed words of an item (32K bases)
-    static constexpr int OFF_SEQ = OFF_X + NX * X_BYTES;
-    static constexpr int TOTAL = OFF_SEQ + SEQ_WORDS * 4;
+    static constexpr int TOTAL = OFF_X + NX * X_BYTES;
     // two score buffers S[2] (kNT columns each; P = 2^(S - m) as BF16 hi + lo
     // replaces S in place) and the count accumulator O (KP)
     static constexpr uint32_t TMEM_COLS = 256;
@@ -146,39 +146,41 @@ struct TileIt {
     }
 };
 
-// One-hot tile X[j][p*4+a] = [x_{j0+j+p} = a] of the l-mers of tile `t`:
-// thread (row j, part) writes every fourth 16-byte chunk (two positions each,
-// BF16 1.0 = 0x3F80 in the slot of the base's code) of row j, from one 64-bit
-// window of the packed sequence (staged words when `staged`).
-template <int KP>
-__device__ __forceinline__ void build_x(uint8_t *sX, const TileIt &t, int l, const uint32_t *sSeq,
-                                        int nw_st, int64_t w_first, bool staged,
-                                        const uint32_t *packed, int64_t nwords, int tid) {
-    static_assert(kSoftThreads == 4 * kNT, "four threads per row");
-    constexpr int kChunks = KP / 8;
-    const int j = tid % kNT, part = tid / kNT;
-    if (part >= kChunks) return;
-    const bool row_ok = j < t.ns - t.j0;
-    uint64_t win = 0;
-    if (row_ok) {
-        const int64_t b0 = t.base + t.j0 + j;
-        win = staged ? window64(sSeq, nw_st, b0 - (w_first << 4)) : window64(packed, nwords, b0);
-    }
-#pragma unroll
-    for (int kb = part; kb < kChunks; kb += 4) {
-        uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
-        const int p0 = 2 * kb, p1 = 2 * kb + 1;
-        if (row_ok && p0 < l) {
-            const uint32_t code = (uint32_t)(win >> (2 * p0)) & 3u;
-            const uint32_t v = 0x3F80u << (16 * (code & 1u));
-            if (code >> 1) w1 = v; else w0 = v;
+// One-hot tiles X[j][p*4+a] = [x_{j0+j+p} = a] of every sequence, in the
+// K-major core-matrix layout the MMAs read (KP columns, rows past the
+// sequence's last l-mer zero), one CTA per sequence: thread (row j, part)
+// writes every fourth 16-byte chunk (two positions each, BF16 1.0 = 0x3F80 in
+// the slot of the base's code) of row j, from one 64-bit window of the packed
+// sequence.
+__global__ void __launch_bounds__(256) em_xtiles_kernel(const uint32_t *__restrict__ packed,
+                                                        int64_t nwords,
+                                                        const XSeq *__restrict__ seqs, int kp,
+                                                        uint8_t *__restrict__ xt) {
+    const XSeq sq = seqs[blockIdx.x];
+    const int j = threadIdx.x % kNT, part = threadIdx.x / kNT;
+    const int chunks = kp / 8;
+    const size_t xbytes = (size_t)kNT * kp * 2;
+    const int ntiles = (sq.ns + kNT - 1) / kNT;
+    for (int tt = 0; tt < ntiles; ++tt) {
+        uint8_t *dst = xt + (size_t)(sq.tile + tt) * xbytes;
+        const int r = tt * kNT + j;
+        const bool row_ok = r < sq.ns;
+        const uint64_t win = row_ok ? window64(packed, nwords, sq.base + r) : 0ull;
+        for (int kb = part; kb < chunks; kb += 4) {
+            uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
+            const int p0 = 2 * kb, p1 = 2 * kb + 1;
+            if (row_ok && p0 < sq.l) {
+                const uint32_t code = (uint32_t)(win >> (2 * p0)) & 3u;
+                const uint32_t v = 0x3F80u << (16 * (code & 1u));
+                if (code >> 1) w1 = v; else w0 = v;
+            }
+            if (row_ok && p1 < sq.l) {
+                const uint32_t code = (uint32_t)(win >> (2 * p1)) & 3u;
+                const uint32_t v = 0x3F80u << (16 * (code & 1u));
+                if (code >> 1) w3 = v; else w2 = v;
+            }
+            *reinterpret_cast<uint4 *>(dst + tc::kmajor_off(j, 8 * kb, kp)) = make_uint4(w0, w1, w2, w3);
         }
-        if (row_ok && p1 < l) {
-            const uint32_t code = (uint32_t)(win >> (2 * p1)) & 3u;
-            const uint32_t v = 0x3F80u << (16 * (code & 1u));
-            if (code >> 1) w3 = v; else w2 = v;
-        }
-        *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(j, 8 * kb, KP)) = make_uint4(w0, w1, w2, w3);
     }
 }
 
@@ -258,14 +260,13 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
     const int quad = warp & 3, half = (warp >> 2) & 1;
     const int row = 32 * quad + lane;
     uint8_t *sWhi = smem + LY::OFF_WHI, *sWlo = smem + LY::OFF_WLO, *sX = smem + LY::OFF_X;
-    uint32_t *sSeq = reinterpret_cast<uint32_t *>(smem + LY::OFF_SEQ);
 
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&mbSfull[b], 1);
             tc::mbar_init(&mbSfree[b], kSoftThreads);
         }
-        for (int s = 0; s < LY::NX; ++s) tc::mbar_init(&mbXfull[s], kSoftThreads);
+        for (int s = 0; s < LY::NX; ++s) tc::mbar_init(&mbXfull[s], 1);  // + the copy's bytes
         tc::mbar_init(&mbPfull, kSoftThreads);
         tc::mbar_init(&mbO, 1);
         tc::mbar_init(&mbEnd, 1);
@@ -288,6 +289,15 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
     uint32_t phSfull = 0u, phSfree = 0u, phX = 0u, phP = 0u;
     uint32_t o_waited = 0, o_base = 0;  // count MMAs of this CTA known complete / before this item
     uint32_t xcnt = 0;                  // exchanges done (slot = xcnt & 1)
+    uint32_t xcopies[LY::NX] = {0u, 0u, 0u};  // one-hot tile copies issued per slot (thread 0)
+    // thread 0: one-hot tile j of the item into ring slot j % 3
+    auto copy_x = [&](int64_t tile, int j) {
+        const int slot = j % LY::NX;
+        tc::mbar_arrive_expect_tx(&mbXfull[slot], (uint32_t)LY::X_BYTES);
+        tc::bulk_g2s(sX + slot * LY::X_BYTES, P.xt + tile * LY::X_BYTES, (uint32_t)LY::X_BYTES,
+                     &mbXfull[slot]);
+        ++xcopies[slot];
+    };
     bool ok = true, abort = false;
 
     auto wait_o = [&](uint32_t target) {  // first `target` count MMAs of the item complete
@@ -314,12 +324,12 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
         const int64_t c = item.c0 + row;
         const bool valid = row < item.nc;
         const int n = item.n_tiles;
-        const int64_t b_lo = in.seq_off[item.seq_lo], b_hi = in.seq_off[item.seq_hi];
-        const int64_t w_first = b_lo >> 4;
-        const int nw_st = (int)(((b_hi + 15) >> 4) - w_first) + 2;
-        const bool staged = nw_st <= LY::SEQ_WORDS;
 
         __syncthreads();  // the previous item's MMAs and reads are complete
+        if (tid == 0) {  // the first two one-hot tiles (every slot is free)
+            copy_x(item.tile0, 0);
+            if (n > 1) copy_x(item.tile0 + 1, 1);
+        }
         float span = 0.f;   // sum over this thread's positions of max_a W - min_a W
         float wmax = 0.f;   // sum over this thread's positions of max_a W
         if (!issuer) {
@@ -355,9 +365,6 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                 *reinterpret_cast<uint4 *>(sWlo + tc::kmajor_off(row, k8, KP)) =
                     make_uint4(lo[0], lo[1], lo[2], lo[3]);
             }
-            if (staged)
-                for (int w = tid; w < nw_st; w += kSoftThreads)
-                    sSeq[w] = (w_first + w) < P.nwords ? __ldg(P.packed + w_first + w) : 0u;
         }
         // per row: highest possible score and score range (both halves)
         float row_span = 0.f, row_top = 0.f;
@@ -366,19 +373,8 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
             row_top = wmax + exchange(wmax);
         }
         const bool careful = __syncthreads_or(row_span > 200.f);
-        TileIt tb;
-        tb.start(in, item.seq_lo, item.seq_hi);
-        if (!issuer) {
-            build_x<KP>(sX, tb, l, sSeq, nw_st, w_first, staged, P.packed, P.nwords, tid);
-            tb.advance(in, item.seq_hi);
-            if (n > 1) {
-                build_x<KP>(sX + LY::X_BYTES, tb, l, sSeq, nw_st, w_first, staged, P.packed,
-                            P.nwords, tid);
-                tb.advance(in, item.seq_hi);
-            }
-            tc::fence_async_smem();
-        }
-        __syncthreads();  // W and the first two one-hot tiles are visible to the issuer
+        if (!issuer) tc::fence_async_smem();
+        __syncthreads();  // W is visible to the issuer (the one-hot tiles arrive on mbXfull)
 
         if (issuer) {
             if (lane == 0) {
@@ -397,9 +393,15 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                     for (int s = 0; s < KP / 16; ++s)
                         if (s < kq) tc::mma_bf16(d, dWlo + 16 * s, dx + 16 * s, IDESC_S, 1u);
                 };
+                ok = tc::mbar_wait(&mbXfull[0], phX & 1u, kWaitNs);
+                phX ^= 1u;
+                tc::fence_after_sync();
                 issue_scores(tm, 0);
                 tc::mma_commit(&mbSfull[0]);
-                if (n > 1) {
+                if (n > 1 && ok) {
+                    ok = tc::mbar_wait(&mbXfull[1], (phX >> 1) & 1u, kWaitNs);
+                    phX ^= 2u;
+                    tc::fence_after_sync();
                     issue_scores(tm + NT, 1);
                     tc::mma_commit(&mbSfull[1]);
                 }
@@ -532,13 +534,7 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                     tc::mbar_arrive(&mbPfull);
                 }
                 // one-hot tile of i+2 into the slot of tile i-1 (its MMAs are complete)
-                if (i + 2 < n) {
-                    build_x<KP>(sX + ((i + 2) % 3) * LY::X_BYTES, tb, l, sSeq, nw_st, w_first,
-                                staged, P.packed, P.nwords, tid);
-                    tb.advance(in, item.seq_hi);
-                    tc::fence_async_smem();
-                    tc::mbar_arrive(&mbXfull[(i + 2) % 3]);
-                }
+                if (i + 2 < n && tid == 0 && ok) copy_x(item.tile0 + i + 2, i + 2);
                 first = false;
                 if (tcur.last()) {
                     const float Sh = Ssum - Scmp;
@@ -646,6 +642,10 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
         }
     }
     if (abort && tid == 0) atomicExch(P.err, 1);
+    // every one-hot tile copy this CTA issued has landed (bounded) before it exits
+    if (tid == 0)
+        for (int s = 0; s < LY::NX; ++s)
+            if (xcopies[s] > 0u) tc::mbar_wait(&mbXfull[s], (xcopies[s] - 1u) & 1u, kWaitNs);
     // every MMA this CTA issued has completed (bounded) before its memory is freed
     if (issuer && lane == 0) tc::mma_commit(&mbEnd);
     tc::mbar_wait(&mbEnd, 0u, kWaitNs);
@@ -798,8 +798,12 @@ int em_tc_plan(const std::vector<EmInstHost> &insts, std::vector<EmItem> &items,
     if (tiles > 0 && tiles < slots)
         G = (int)std::min<int64_t>(std::max(1, tmin), std::max<int64_t>(1, waves * slots / tiles));
     items.clear();
+    int64_t tb = 0;  // one-hot tiles of the earlier instances
     for (size_t ii = 0; ii < insts.size(); ++ii) {
         const EmInstHost &h = insts[ii];
+        std::vector<int64_t> pre(h.t + 1, 0);  // tiles of the instance's first q sequences
+        for (int q = 0; q < h.t; ++q)
+            pre[q + 1] = pre[q] + (h.seq_off[q + 1] - h.seq_off[q] - h.l + 1 + kNT - 1) / kNT;
         for (int64_t c0 = 0; c0 < h.C; c0 += kTcRows)
             for (int g = 0; g < G; ++g) {
                 EmItem it;
@@ -809,11 +813,11 @@ int em_tc_plan(const std::vector<EmInstHost> &insts, std::vector<EmItem> &items,
                 it.seq_lo = (int)((int64_t)h.t * g / G);
                 it.seq_hi = (int)((int64_t)h.t * (g + 1) / G);
                 it.g = g;
-                it.n_tiles = 0;
-                for (int q = it.seq_lo; q < it.seq_hi; ++q)
-                    it.n_tiles += (h.seq_off[q + 1] - h.seq_off[q] - h.l + 1 + 63) / 64;
+                it.n_tiles = (int)(pre[it.seq_hi] - pre[it.seq_lo]);
+                it.tile0 = tb + pre[it.seq_lo];
                 items.push_back(it);
             }
+        tb += pre[h.t];
     }
     return kp;
 }
@@ -882,6 +886,33 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
     PROJ_CUDA_TRY(cudaMemsetAsync(run.tiles.as<uint32_t>(), 0,
                                   (size_t)std::max<int64_t>(1, n_tiles) * sizeof(uint32_t), st));
 
+    // the one-hot tiles of every sequence, built once for all iterations
+    {
+        std::vector<XSeq> xs;
+        int64_t nx = 0;
+        for (const EmInstHost &h : insts)
+            for (int q = 0; q < h.t; ++q) {
+                XSeq v;
+                v.base = h.seq_off[q];
+                v.tile = nx;
+                v.ns = h.seq_off[q + 1] - h.seq_off[q] - h.l + 1;
+                v.l = h.l;
+                xs.push_back(v);
+                nx += (v.ns + kNT - 1) / kNT;
+            }
+        const size_t xbytes = (size_t)kNT * kp * 2;
+        PROJ_TRY(run.xt.alloc(std::max<int64_t>(1, nx) * xbytes, st));
+        PROJ_TRY(run.xseq.alloc(xs.size() * sizeof(XSeq), st));
+        PROJ_CUDA_TRY(cudaMemcpyAsync(run.xseq.as<XSeq>(), xs.data(), xs.size() * sizeof(XSeq),
+                                      cudaMemcpyHostToDevice, st));
+        {
+            TraceSpan ts_("em_xtiles", st);
+            em_xtiles_kernel<<<(unsigned)xs.size(), 256, 0, st>>>(packed, nwords, run.xseq.as<XSeq>(),
+                                                                  kp, run.xt.as<uint8_t>());
+        }
+        PROJ_LAUNCH_CHECK("em_xtiles_kernel");
+    }
+
     if (tune) {
         // time one M-step launch per schedule on this data (the model copy it
         // updates in place is restored before the real iterations)
@@ -908,6 +939,7 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
             P.C = C; P.err = run.flag.as<int>(); P.mstep = 1; P.G = G; P.beta = 0.25f;
             P.theta_out = run.tmp.as<float>(); P.ll_out = ll_scratch.as<double>();
             P.tile_done = run.tiles.as<uint32_t>();
+            P.xt = run.xt.as<uint8_t>();
             const int grid = (int)std::min<int64_t>((int64_t)items.size(),
                                                     (int64_t)sm_count() * std::min(sc.ctas, ctas_per_sm(kpp)));
             PROJ_CUDA_TRY(cudaEventRecord(e0, st));
@@ -970,6 +1002,7 @@ int em_tc_enqueue(EmTcRun &run, int iters, float beta, float *theta_out, double 
     P.theta_out = run.tmp.as<float>();  // in place
     P.ll_out = ll;
     P.tile_done = run.tiles.as<uint32_t>();
+    P.xt = run.xt.as<uint8_t>();
     P.err = run.flag.as<int>();
     const int grid = (int)std::min<int64_t>((int64_t)run.n_items,
                                             (int64_t)sm_count() * std::min(run.ctas, ctas_per_sm(run.kp)));
