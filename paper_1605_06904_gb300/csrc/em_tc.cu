@@ -185,23 +185,30 @@ __global__ void __launch_bounds__(256) em_xtiles_kernel(const uint32_t *__restri
 }
 
 // 2^(v - m) for the nv valid entries of a half tile, 0 elsewhere; returns
-// their sum (tree order).
+// their sum (tree order).  The subtractions and the sum use the packed
+// two-wide FP32 adds (each lane rounded as a scalar add).
 __device__ __forceinline__ float exp_half(float (&v)[32], float m, int nv) {
-    if (nv == 32) {
+    const float2 mm = make_float2(-m, -m);
 #pragma unroll
-        for (int q = 0; q < 32; ++q) v[q] = ex2(v[q] - m);
-    } else {
-#pragma unroll
-        for (int q = 0; q < 32; ++q) v[q] = q < nv ? ex2(v[q] - m) : 0.f;
+    for (int q = 0; q < 32; q += 2) {
+        const float2 d = __fadd2_rn(make_float2(v[q], v[q + 1]), mm);
+        v[q] = ex2(d.x);
+        v[q + 1] = ex2(d.y);
     }
-    float part[16];
+    if (nv < 32) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) part[q] = v[q] + v[q + 16];
+        for (int q = 0; q < 32; ++q) v[q] = q < nv ? v[q] : 0.f;
+    }
+    float2 part[8];
 #pragma unroll
-    for (int w = 8; w >= 1; w >>= 1)
+    for (int q = 0; q < 8; ++q)
+        part[q] = __fadd2_rn(make_float2(v[2 * q], v[2 * q + 1]),
+                             make_float2(v[2 * q + 16], v[2 * q + 17]));
 #pragma unroll
-        for (int q = 0; q < w; ++q) part[q] += part[q + w];
-    return part[0];
+    for (int w = 4; w >= 1; w >>= 1)
+#pragma unroll
+        for (int q = 0; q < w; ++q) part[q] = __fadd2_rn(part[q], part[q + w]);
+    return part[0].x + part[0].y;
 }
 
 __device__ __forceinline__ float max_half(const float (&v)[32], int nv) {
@@ -519,8 +526,10 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                             const float a0 = v[16 * g + 2 * q], a1 = v[16 * g + 2 * q + 1];
                             const uint32_t h = pack_bf16(a0, a1);
                             hi[q] = h;
-                            lo[q] = pack_bf16(a0 - __uint_as_float(h << 16),
-                                              a1 - __uint_as_float(h & 0xFFFF0000u));
+                            const float2 r = __fadd2_rn(
+                                make_float2(a0, a1), make_float2(-__uint_as_float(h << 16),
+                                                                 -__uint_as_float(h & 0xFFFF0000u)));
+                            lo[q] = pack_bf16(r.x, r.y);
                         }
                         tc::tmem_st8u(tS + 8 * g, hi);
                         tc::tmem_st8u(tS + 16 + 8 * g, lo);
