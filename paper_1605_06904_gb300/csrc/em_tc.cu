@@ -438,8 +438,12 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                         const uint32_t xs = (uint32_t)((j + 2) % 3), b = (uint32_t)(j & 1);
                         ok = tc::mbar_wait(&mbXfull[xs], (phX >> xs) & 1u, kWaitNs);
                         phX ^= 1u << xs;
-                        if (ok) ok = tc::mbar_wait(&mbSfree[b], (phSfree >> b) & 1u, kWaitNs);
-                        phSfree ^= 1u << b;
+                        // an M-step's count MMA j, issued above after P(j) was written
+                        // (so after S(j) was read), precedes this MMA: no release needed
+                        if (!P.mstep) {
+                            if (ok) ok = tc::mbar_wait(&mbSfree[b], (phSfree >> b) & 1u, kWaitNs);
+                            phSfree ^= 1u << b;
+                        }
                         tc::fence_after_sync();
                         issue_scores(tm + NT * b, xs);
                         tc::mma_commit(&mbSfull[b]);
@@ -512,7 +516,7 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                 }
                 kahan(Ssum, Scmp, add);
                 tc::fence_before_sync();
-                if (i + 2 < n) tc::mbar_arrive(&mbSfree[b]);  // the issuer may overwrite S(i)
+                if (i + 2 < n && !P.mstep) tc::mbar_arrive(&mbSfree[b]);  // the issuer may overwrite S(i)
 
                 if (P.mstep) {
                     // P over this thread's own score columns: hi of its 32 l-mers in
