@@ -27,7 +27,7 @@
 //      with P read from tensor memory and X in MN-major form from the same
 //      shared-memory tile.
 // The steps of consecutive tiles overlap (two score buffers in tensor memory,
-// a ring of three one-hot tiles): the score MMA of tile i+1 and the count MMA
+// a ring of four one-hot tiles): the score MMA of tile i+1 and the count MMA
 // of tile i-1 run on the tensor core while the CUDA cores work on tile i.
 // At the end of a sequence O / sum is added to the candidate's counts and
 // max + log2(sum) to its log-likelihood.  Scores are kept in log2 units
@@ -91,7 +91,7 @@ template <int KP>
 struct TcLayout {
     static constexpr int W_BYTES = 128 * KP * 2;   // each of W_hi, W_lo
     static constexpr int X_BYTES = kNT * KP * 2;   // one one-hot tile
-    static constexpr int NX = 3;                   // ring of one-hot tiles
+    static constexpr int NX = 4;                   // ring of one-hot tiles
     static constexpr int OFF_WHI = 0;
     static constexpr int OFF_WLO = OFF_WHI + W_BYTES;
     static constexpr int OFF_X = OFF_WLO + W_BYTES;
@@ -233,12 +233,13 @@ __device__ __forceinline__ float max_half(const float (&v)[32], int nv) {
 //
 // Pipeline over the tiles j = 0 .. n-1 of an item, linked by mbarriers:
 //   issuer: S(0), S(1); then per j: [P(j) written] O (+)= P X(j);
-//           [X(j+2) built, S buffer of j read] S(j+2) = W X(j+2)^T
+//           [X(j+2) landed, (E-step only) S buffer of j read] S(j+2) = W X(j+2)^T
 //   softmax, per j: [S(j) ready] read S(j), release its buffer; P = 2^(S-m);
-//           write P(j) over S(j); [count MMA of j-1 done] build X(j+2) into
-//           the slot of tile j-1; at a sequence end [count MMA of j done] read O.
+//           write P(j) over S(j); [count MMA of j-1 done] one thread starts the
+//           copy of X(j+3) into the slot of tile j-1; at a sequence end [count
+//           MMA of j done] read O.
 // Two score buffers in tensor memory (each holding S(j), then P(j)) and a ring
-// of three one-hot tiles in shared memory.  S(j+2) overwrites P(j) only after
+// of four one-hot tiles in shared memory.  S(j+2) overwrites P(j) only after
 // the count MMA that reads P(j): tcgen05.mma operations issued by one thread
 // execute in issue order.
 //
@@ -296,8 +297,8 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
     uint32_t phSfull = 0u, phSfree = 0u, phX = 0u, phP = 0u;
     uint32_t o_waited = 0, o_base = 0;  // count MMAs of this CTA known complete / before this item
     uint32_t xcnt = 0;                  // exchanges done (slot = xcnt & 1)
-    uint32_t xcopies[LY::NX] = {0u, 0u, 0u};  // one-hot tile copies issued per slot (thread 0)
-    // thread 0: one-hot tile j of the item into ring slot j % 3
+    uint32_t xcopies[LY::NX] = {0u, 0u, 0u, 0u};  // one-hot tile copies issued per slot (thread 0)
+    // thread 0: one-hot tile j of the item into ring slot j % NX
     auto copy_x = [&](int64_t tile, int j) {
         const int slot = j % LY::NX;
         tc::mbar_arrive_expect_tx(&mbXfull[slot], (uint32_t)LY::X_BYTES);
@@ -333,10 +334,8 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
         const int n = item.n_tiles;
 
         __syncthreads();  // the previous item's MMAs and reads are complete
-        if (tid == 0) {  // the first two one-hot tiles (every slot is free)
-            copy_x(item.tile0, 0);
-            if (n > 1) copy_x(item.tile0 + 1, 1);
-        }
+        if (tid == 0)  // the first NX - 1 one-hot tiles (every slot is free)
+            for (int j = 0; j < LY::NX - 1 && j < n; ++j) copy_x(item.tile0 + j, j);
         float span = 0.f;   // sum over this thread's positions of max_a W - min_a W
         float wmax = 0.f;   // sum over this thread's positions of max_a W
         if (!issuer) {
@@ -419,7 +418,7 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                         ok = tc::mbar_wait(&mbPfull, phP, kWaitNs);
                         phP ^= 1u;
                         tc::fence_after_sync();
-                        const uint64_t dx = dXmn + (uint32_t)(j % 3) * kXSlot;
+                        const uint64_t dx = dXmn + (uint32_t)(j % LY::NX) * kXSlot;
                         const uint32_t acc0 = ti.j0 > 0 ? 1u : 0u;  // O restarts with a sequence
                         // P(j) in score buffer j&1: l-mers 16s..16s+15 at columns
                         // 32(s/2) + 8(s%2) (hi) and 16 further (lo)
@@ -435,7 +434,7 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                         tc::mma_commit(&mbO);
                     }
                     if (j + 2 < n && ok) {
-                        const uint32_t xs = (uint32_t)((j + 2) % 3), b = (uint32_t)(j & 1);
+                        const uint32_t xs = (uint32_t)((j + 2) % LY::NX), b = (uint32_t)(j & 1);
                         ok = tc::mbar_wait(&mbXfull[xs], (phX >> xs) & 1u, kWaitNs);
                         phX ^= 1u << xs;
                         // an M-step's count MMA j, issued above after P(j) was written
@@ -546,8 +545,9 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                     tc::fence_before_sync();
                     tc::mbar_arrive(&mbPfull);
                 }
-                // one-hot tile of i+2 into the slot of tile i-1 (its MMAs are complete)
-                if (i + 2 < n && tid == 0 && ok) copy_x(item.tile0 + i + 2, i + 2);
+                // one-hot tile of i+3 into the slot of tile i-1 (its MMAs are complete)
+                if (i + LY::NX - 1 < n && tid == 0 && ok)
+                    copy_x(item.tile0 + i + LY::NX - 1, i + LY::NX - 1);
                 first = false;
                 if (tcur.last()) {
                     const float Sh = Ssum - Scmp;
