@@ -462,6 +462,21 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
             const float log_no = zoops ? log1pf(-(float)in.gamma) : 0.f;
             float m = -INFINITY, Ssum = 0.f, Scmp = 0.f;
             bool first = true;
+            // a finished sequence's O is added to tot (scaled by o_inv) during the
+            // next tile, before that tile's count MMA restarts O, so the wait for
+            // the sequence's last count MMA overlaps the next tile's softmax
+            bool o_pend = false;
+            float o_inv = 0.f;
+            auto read_o = [&]() {
+#pragma unroll
+                for (int c8 = 0; c8 < KH; c8 += 8) {
+                    float o[8];
+                    tc::tmem_ld8(tO + lane_base + half * KH + c8, o);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) tot[c8 + q] += o[q] * o_inv;
+                }
+                o_pend = false;
+            };
             o_base = o_waited;  // every count MMA of earlier items was waited for
             TileIt tcur;
             tcur.start(in, item.seq_lo, item.seq_hi);
@@ -542,6 +557,10 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                     // below) before count MMA i can be issued: the parity waits on
                     // mbO never fall two phases behind
                     wait_o((uint32_t)i);
+                    if (o_pend) {  // the previous sequence ended with tile i-1
+                        tc::fence_after_sync();
+                        read_o();
+                    }
                     tc::fence_before_sync();
                     tc::mbar_arrive(&mbPfull);
                 }
@@ -555,8 +574,7 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                     float w = 1.f;  // posterior probability that the sequence holds a site
                     if (zoops) {
                         // ZOOPS: L_i = log[(1 - gamma) + (gamma / ns) sum_j e^r], in FP32
-                        // (FP64 transcendentals are slow here; the sum over sequences
-                        // stays FP64)
+                        // (FP64 transcendentals are slow here)
                         const float lg = log_gamma - logf((float)tcur.ns) +
                                          (m + log2f(Sf)) * 0.69314718f;
                         const float hi = fmaxf(log_no, lg), lo = fminf(log_no, lg);
@@ -568,17 +586,8 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                     }
                     kahan(zs_s, zs_c, w);
                     if (P.mstep) {
-                        wait_o((uint32_t)i + 1);
-                        tc::fence_after_sync();
-                        const float inv = w / Sf;
-#pragma unroll
-                        for (int c8 = 0; c8 < KH; c8 += 8) {
-                            float o[8];
-                            tc::tmem_ld8(tO + lane_base + half * KH + c8, o);
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) tot[c8 + q] += o[q] * inv;
-                        }
-                        tc::fence_before_sync();
+                        o_pend = true;  // read during the next tile or after the loop
+                        o_inv = w / Sf;
                     }
                     m = -INFINITY;
                     Ssum = 0.f;
@@ -586,6 +595,12 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                     first = true;
                 }
                 tcur.advance(in, item.seq_hi);
+            }
+            if (o_pend) {  // the item's last sequence
+                wait_o((uint32_t)n);
+                tc::fence_after_sync();
+                read_o();
+                tc::fence_before_sync();
             }
             const double ll = (double)ll_s - (double)ll_c, zs = (double)zs_s - (double)zs_c;
             if (ok && valid && P.G == 1) {
