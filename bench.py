@@ -481,6 +481,19 @@ def run_top(args):
 # GPU leg
 # ---------------------------------------------------------------------------
 
+def exp_bound(P, flops, exps, tensor_peak_tflops, em_ms):
+    """The EM kernel's two ceilings side by side: tensor time (algorithmic FLOPs
+    at the tensor peak) and exponential time (one exp2 per score at the exp2
+    rate measured now), and which of them binds."""
+    rate = P.projection_ex2_peak()
+    t_tensor = flops / (tensor_peak_tflops * 1e12) * 1e3
+    t_exp = exps / rate * 1e3
+    return {"ex2_per_s": rate, "tensor_ms": t_tensor, "exp_ms": t_exp,
+            "binding": "tensor" if t_tensor >= t_exp else "exp",
+            "frac_of_binding": max(t_tensor, t_exp) / em_ms if em_ms > 0 else None,
+            "peak_source": "projection_ex2_peak() measured in this run"}
+
+
 def protein_measure(P, stream, flush, reps=5):
     """The 20-letter search on a planted protein (15,4) input: t=20 sequences of
     600 residues, k=4 (base-20 keys), s=3, m=40 trials, 5 EM iterations.  Device
@@ -652,7 +665,8 @@ def main():
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "kernel": "em_tc_kernel", "launches": em_launches,
                 "avg_launch_ms": em_ms / max(1, em_launches),
-                "peak_source": f"bf16_tflops_sustained ({pk_kind})"}
+                "peak_source": f"bf16_tflops_sustained ({pk_kind})",
+                "exp_bound": exp_bound(P, flops, args.steps * x * C * (iters + 1), peak, em_ms)}
 
     # ---- the bucket-counting kernel against the shared-memory histogram rate
     hist_peak = P.projection_hist_peak(k)

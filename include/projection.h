@@ -361,6 +361,12 @@ int projection_selftest_wait(int64_t timeout_ns, void *stream);
  * Synchronises `stream`. */
 int projection_hist_peak(int k, double *updates_per_s, void *stream);
 
+/* The GPU's exp2 rate (ex2.approx, the EM kernels' one exponential per score)
+ * measured with independent dependency chains on every SM: *ex2_per_s =
+ * exponentials per second (best of 3 timed launches after a warm-up).
+ * Synchronises `stream`. */
+int projection_ex2_peak(double *ex2_per_s, void *stream);
+
 /* ---- tracing (CUDA-event timers per kernel) ----------------------------- */
 
 /* on != 0: start recording a CUDA event pair around every kernel the library

@@ -21,7 +21,7 @@ __all__ = ["projection_packed_words", "projection_default_params", "projection_p
            "em_refine", "projection_finalize", "projection_find", "projection_find_packed",
            "projection_find_batch", "projection_find_top", "projection_find_protein", "projection_find_packed_top",
            "projection_trace_enable", "projection_trace_read", "projection_selftest_wait",
-           "projection_hist_peak", "projection_params_batch", "em_refine_zoops",
+           "projection_hist_peak", "projection_ex2_peak", "projection_params_batch", "em_refine_zoops",
            "projection_find_packed_zoops", "trial_hash_allpairs", "ProjectionError",
            "PROJ_EM_FP32", "PROJ_EM_BF16_SPLIT", "seq_offsets"]
 
@@ -429,6 +429,14 @@ def projection_hist_peak(k: int, stream=None) -> float:
     bucket kernels' roofline denominator)."""
     out = ctypes.c_double(0.0)
     check(lib().projection_hist_peak(int(k), ctypes.byref(out), _stream(stream)))
+    return float(out.value)
+
+
+def projection_ex2_peak(stream=None) -> float:
+    """exp2 (ex2.approx) evaluations per second on this GPU (the EM kernels'
+    exponential roofline denominator)."""
+    out = ctypes.c_double(0.0)
+    check(lib().projection_ex2_peak(ctypes.byref(out), _stream(stream)))
     return float(out.value)
 
 

@@ -53,6 +53,7 @@ SIGNATURES = {
     "projection_find_packed_zoops": ([P, P, i32, i32, i32, i32, i32, i32, u64, i32, f32, i32,
                                       ctypes.c_double, i64, ctypes.POINTER(ProjectionResult), P],
                                      i32),
+    "projection_ex2_peak": ([P, P], i32),
     "projection_find_protein": ([P, P, i32, i32, i32, i32, i32, u64, i32, f32,
                                  ctypes.POINTER(ProjectionResult), P], i32),
     "projection_finalize": ([P, P, i32, i32, P, P, P, i64, P, P, P, P, P], i32),

@@ -243,15 +243,15 @@ __device__ __forceinline__ float max_half(const float (&v)[32], int nv) {
 // the count MMA that reads P(j): tcgen05.mma operations issued by one thread
 // execute in issue order.
 //
-// Reference maximum: P = 2^(S - m) with m = max(exact maximum of the
-// sequence's first tile, top - 100), top = sum_p max_a W the highest score the
-// row can reach.  Every P of the sequence is then <= 2^100, and when the row's
-// score range sum_p (max_a W - min_a W) is <= 200 the sequence's largest P is
-// >= 2^-100, so nothing overflows or leaves the normal FP32 range that
-// matters.  Rows with a wider range (careful mode, CTA-wide) use the exact
-// first-tile maximum and the two threads of a row compare every tile: if a
-// half-tile sum exceeds 2^64 (or is not finite) m is raised to the tile's
-// exact maximum, the row's sums and O are rescaled and the tile recomputed.
+// Reference maximum: P = 2^(S - m) with m = top - 100, top = sum_p max_a W the
+// highest score the row can reach.  When the row's score range sum_p (max_a W
+// - min_a W) is <= 200 every score lies in [top - 200, top], so every P is in
+// [2^-100, 2^100]: nothing overflows or leaves the normal FP32 (and BF16)
+// range.  Rows with a wider range (careful mode, CTA-wide) use the exact
+// maximum of each sequence's first tile and the two threads of a row compare
+// every tile: if a half-tile sum exceeds 2^64 (or is not finite) m is raised to
+// the tile's exact maximum, the row's sums and O are rescaled and the tile
+// recomputed.
 template <int KP>
 __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(const EmTcParams P) {
     using LY = TcLayout<KP>;
@@ -493,11 +493,14 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                 float v[32];
                 tc::tmem_ld32(tS, v);
                 if (first) {
-                    // the first tile's maximum, raised to at least top - 100 so that
-                    // no later score of the sequence (<= top) gives P above 2^100
-                    const float mh = max_half(v, nv);
-                    m = fmaxf(mh, exchange(mh));
-                    if (!careful) m = fmaxf(m, row_top - 100.f);
+                    if (careful) {  // the first tile's exact maximum
+                        const float mh = max_half(v, nv);
+                        m = fmaxf(mh, exchange(mh));
+                    } else {
+                        // every score of the row lies in [top - 200, top], so
+                        // P = 2^(S - m) stays within [2^-100, 2^100]
+                        m = row_top - 100.f;
+                    }
                 }
                 const float s0 = Ssum, c0s = Scmp;
                 float add = exp_half(v, m, nv);
@@ -1108,6 +1111,58 @@ int run_em_tc(const uint32_t *packed, const Layout &L, const double *bg, const f
 }
 
 }  // namespace proj
+
+// ---------------------------------------------------------------------------
+// projection_ex2_peak: the exp2 rate (MUFU ex2.approx) the EM kernel's one
+// exponential per score is measured against.  Every thread runs eight
+// independent chains x <- 2^-x (values stay in [0.5, 1]).
+// ---------------------------------------------------------------------------
+namespace proj {
+namespace {
+
+__global__ void __launch_bounds__(512) ex2_peak_kernel(int iters, float *sink) {
+    float x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = 0.125f * (float)q + 1e-3f * (float)(threadIdx.x & 7);
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = ex2(-x[q]);
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc += x[q];
+    if (acc == 12345.f) sink[blockIdx.x] = acc;  // keeps the work; never true
+}
+
+}  // namespace
+}  // namespace proj
+
+extern "C" int projection_ex2_peak(double *ex2_per_s, void *stream) {
+    using namespace proj;
+    clear_error();
+    PROJ_REQUIRE(ex2_per_s != nullptr, "ex2_per_s must not be NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = sm_count() * 4, threads = 512, iters = 4096;
+    DevBuf sink;
+    PROJ_TRY(sink.alloc((size_t)grid * 4, st));
+    cudaEvent_t e0, e1;
+    PROJ_CUDA_TRY(cudaEventCreate(&e0));
+    PROJ_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {  // first launch warms up; keep the fastest
+        PROJ_CUDA_TRY(cudaEventRecord(e0, st));
+        ex2_peak_kernel<<<grid, threads, 0, st>>>(iters, sink.as<float>());
+        PROJ_CUDA_TRY(cudaEventRecord(e1, st));
+        PROJ_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PROJ_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    PROJ_LAUNCH_CHECK("ex2_peak_kernel");
+    *ex2_per_s = (double)grid * threads * iters * 8 / (best * 1e-3);
+    return PROJ_OK;
+}
 
 // ---------------------------------------------------------------------------
 // projection_selftest_wait: exercises the bounded wait of the tensor-core

@@ -1,7 +1,6 @@
-"""The measurement helper behind the bucket kernels' roofline: the
-shared-memory histogram rate must be a plausible positive rate for every k the
-bucket kernels support, and no slower for small histograms than for large
-ones by more than the expected bank-conflict spread."""
+"""The measurement helpers behind the rooflines: the shared-memory histogram
+rate must be a plausible positive rate for every k the bucket kernels support,
+and the exp2 rate a plausible number of exponentials per clock and SM."""
 import pytest
 import torch
 
@@ -26,3 +25,9 @@ def test_hist_peak_is_plausible(P, k):
 def test_hist_peak_rejects_bad_k(P):
     with pytest.raises(P.ProjectionError):
         P.projection_hist_peak(11)
+
+
+def test_ex2_peak_is_plausible(P):
+    r = P.projection_ex2_peak()
+    # 152 SMs x ~2 GHz: between 1 and 128 exponentials per clock per SM
+    assert 3e11 < r < 4e13, r
