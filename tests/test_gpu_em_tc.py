@@ -112,3 +112,46 @@ def test_find_bf16_split_recovers_the_oracle_motif(P, cfg):
                              prm["m"], seed=1000 + cfg, em_iters=prm["em_iters"],
                              pseudocount=prm["beta"], precision=P.PROJ_EM_FP32)
     assert fp32["consensus"] == got["consensus"] and np.array_equal(fp32["sites"], got["sites"])
+
+
+def _peaked_models(rng, inst, n_peaked, n_flat, hi=0.997):
+    """n_peaked models putting `hi` on one base per column (the bases of
+    planted-motif-like l-mers), then n_flat models near uniform."""
+    l = inst.l
+    th = np.empty((n_peaked + n_flat, l, 4), np.float64)
+    motif = O.encode(inst.motif.encode())
+    for c in range(n_peaked):
+        word = motif.copy()
+        flip = rng.choice(l, size=int(rng.integers(0, 4)), replace=False)
+        word[flip] = rng.integers(0, 4, flip.size)
+        th[c] = (1.0 - hi) / 3.0
+        th[c, np.arange(l), word] = hi
+    th[n_peaked:] = rng.dirichlet(np.full(4, 20.0), size=(n_flat, l))
+    return th.astype(np.float32)
+
+
+def test_em_bf16_split_careful_rows(P):
+    """Rows whose score range sum_p (max_a W - min_a W) exceeds 200 (log2 units)
+    switch their CTA to careful mode: exact first-tile maxima and a per-tile
+    overflow check with rescaling.  Peaked models (0.997 / 0.001 per column,
+    l = 24: range ~240) exercise it; the second candidate tile holds only flat
+    models and stays in fast mode in the same launch.  Measured errors: PWM
+    2.5e-6, LL 5.8e-5 relative (E-step only); the LL tolerance is doubled over
+    the planted-workload one for a ~3x margin (the BF16-split score error bound
+    2^-16 sum_p |W_p| grows with the range).  A wrong rescale would be off by
+    powers of two or non-finite."""
+    inst = planted_instance(21, 0, 20, 400, 24, 4)
+    rng = np.random.default_rng(5)
+    th0 = _peaked_models(rng, inst, 100, 60)
+    codes = O.encode(inst.ascii)
+    packed = upload(P, inst.ascii)
+    bg = P.projection_background(packed, inst.seq_off[-1])
+    for iters in (0, 4):
+        pwm, ll = P.em_refine(packed, inst.seq_off, inst.l, bg, torch.from_numpy(th0).cuda(), iters,
+                              0.25, P.PROJ_EM_BF16_SPLIT)
+        w_pwm, w_ll = O.em(codes, inst.seq_off, inst.l, O.background(codes),
+                           th0.astype(np.float64), iters, 0.25, nthreads=16)
+        pwm, ll = pwm.cpu().numpy(), ll.cpu().numpy()
+        assert np.all(np.isfinite(pwm)) and np.all(np.isfinite(ll))
+        assert np.max(np.abs(pwm - w_pwm)) <= PWM_TOL_BF16
+        assert np.all(np.abs(ll - w_ll) <= ll_tol(w_ll, inst.t, 2 * LL_REL_BF16))
