@@ -312,9 +312,10 @@ int trial_hash_allpairs(const uint32_t *packed_dev, const int64_t *seq_off, int 
  * 32).  k, s and m are required (the Section 5 formulas are stated for DNA):
  * 1 <= k <= min(l, 6) (keys base 20 = the projected residues read
  * most-significant first), s >= 1, 1 <= m <= 65535; trials draw their
- * positions as in trial_hash.  Enriched buckets come from the all-pairs
- * comparison (trial_hash_allpairs' scheme, ECAPACITY above 4096 enriched
- * buckets per trial; m * x < 2^31).  theta^0 and em_iters OOPS iterations:
+ * positions as in trial_hash.  Enriched buckets come from a per-trial sort
+ * of (key, l-mer) pairs in shared memory when x <= 16384, else from the
+ * all-pairs comparison (trial_hash_allpairs' scheme, ECAPACITY above 4096
+ * enriched buckets per trial); m * x < 2^31.  theta^0 and em_iters OOPS iterations:
  * scores and exponentials in FP32, M-step counts in 64-bit fixed point (2^-40),
  * log-likelihoods in FP64 (results do not depend on thread scheduling);
  * ranking, sites and Score as projection_find.  out->pwm holds [l][20] floats; out->win_key is

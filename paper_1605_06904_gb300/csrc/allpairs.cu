@@ -11,6 +11,10 @@
 //                      compacted, sorted by key, member offsets
 //   ap_scan_kernel     offsets of every trial's candidates and members
 //   ap_write_kernel    candidate table; ap_members_kernel member lists
+// The protein search (20-letter keys) takes a sort path instead when a trial's
+// l-mers fit one CTA's shared memory (x <= 16384): se_sort_kernel sorts the
+// trial's (key, l-mer) pairs (bitonic, O(x log^2 x)) and counts its enriched
+// runs, se_write_kernel writes the same candidate table and member lists.
 #include <algorithm>
 
 #include "common.cuh"
@@ -280,6 +284,128 @@ __global__ void ap_members_kernel(const int32_t *__restrict__ cnt, const int32_t
     if (p < cap_members) members[p] = g;
 }
 
+constexpr int kSortMax = 16384;  // l-mers per trial the sort path holds in shared memory
+
+// Block-wide exclusive scan of two counters (1024 threads); also returns totals.
+__device__ __forceinline__ void se_scan2(int a, int b, int &ea, int &eb, int &ta, int &tb) {
+    __shared__ int s_a[32], s_b[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ua = __shfl_up_sync(0xffffffffu, ia, o), ub = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) { ia += ua; ib += ub; }
+    }
+    if (lane == 31) { s_a[warp] = ia; s_b[warp] = ib; }
+    __syncthreads();
+    if (warp == 0) {
+        int va = s_a[lane], vb = s_b[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ua = __shfl_up_sync(0xffffffffu, va, o), ub = __shfl_up_sync(0xffffffffu, vb, o);
+            if (lane >= o) { va += ua; vb += ub; }
+        }
+        s_a[lane] = va;
+        s_b[lane] = vb;
+    }
+    __syncthreads();
+    const int pa = warp > 0 ? s_a[warp - 1] : 0, pb = warp > 0 ? s_b[warp - 1] : 0;
+    ea = pa + ia - a;
+    eb = pb + ib - b;
+    ta = s_a[31];
+    tb = s_b[31];
+    __syncthreads();
+}
+
+// One CTA per trial: (key << 32 | l-mer) pairs sorted ascending in shared
+// memory (p2 = the power of two >= x; padding sorts last), written to
+// sorted[trial][x]; nb / nm = the trial's runs of >= s equal keys and their
+// l-mers.
+__global__ void __launch_bounds__(1024) se_sort_kernel(const uint32_t *__restrict__ keys, int x,
+                                                       int p2, int s,
+                                                       unsigned long long *__restrict__ sorted,
+                                                       int32_t *__restrict__ nb,
+                                                       int32_t *__restrict__ nm) {
+    extern __shared__ unsigned long long kv[];
+    const int tr = blockIdx.x, tid = threadIdx.x;
+    const uint32_t *kt = keys + (int64_t)tr * x;
+    for (int i = tid; i < p2; i += 1024)
+        kv[i] = i < x ? ((unsigned long long)kt[i] << 32) | (unsigned)i : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= p2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < p2; i += 1024) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a = kv[i], b = kv[ixj];
+                    if ((a > b) == ((i & k) == 0)) {
+                        kv[i] = b;
+                        kv[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    int lnb = 0, lnm = 0;
+    for (int i = tid; i < x; i += 1024) {
+        const uint32_t key = (uint32_t)(kv[i] >> 32);
+        if (i > 0 && (uint32_t)(kv[i - 1] >> 32) == key) continue;  // not a run start
+        int len = 1;
+        while (i + len < x && (uint32_t)(kv[i + len] >> 32) == key) ++len;
+        if (len >= s) { ++lnb; lnm += len; }
+    }
+    int ea, eb, ta, tb;
+    se_scan2(lnb, lnm, ea, eb, ta, tb);
+    if (tid == 0) { nb[tr] = ta; nm[tr] = tb; }
+    for (int i = tid; i < x; i += 1024) sorted[(int64_t)tr * x + i] = kv[i];
+}
+
+// One CTA per trial: the enriched runs of its sorted pairs in key order ->
+// candidate table rows at cbase[trial] and member lists at mbase[trial] (ids
+// ascending within a run, as the pairs are sorted by (key, l-mer)).
+__global__ void __launch_bounds__(1024) se_write_kernel(
+    const unsigned long long *__restrict__ sorted, int x, int s, const int64_t *__restrict__ cbase,
+    const int64_t *__restrict__ mbase, int64_t trial_begin, int64_t cap_cand,
+    int64_t cap_members, int32_t *__restrict__ cand_trial, uint32_t *__restrict__ cand_key,
+    int32_t *__restrict__ cand_cnt, int64_t *__restrict__ cand_off,
+    int32_t *__restrict__ members) {
+    const int tr = blockIdx.x, tid = threadIdx.x;
+    const unsigned long long *kt = sorted + (int64_t)tr * x;
+    const int chunk = (x + 1023) / 1024;
+    const int c0 = min(tid * chunk, x), c1 = min(c0 + chunk, x);
+    auto run_len = [&](int i, uint32_t key) {
+        int len = 1;
+        while (i + len < x && (uint32_t)(kt[i + len] >> 32) == key) ++len;
+        return len;
+    };
+    int cnt = 0, msum = 0;
+    for (int i = c0; i < c1; ++i) {
+        const uint32_t key = (uint32_t)(kt[i] >> 32);
+        if (i > 0 && (uint32_t)(kt[i - 1] >> 32) == key) continue;
+        const int len = run_len(i, key);
+        if (len >= s) { ++cnt; msum += len; }
+    }
+    int rb, rm, ta, tb;
+    se_scan2(cnt, msum, rb, rm, ta, tb);
+    for (int i = c0; i < c1; ++i) {
+        const uint32_t key = (uint32_t)(kt[i] >> 32);
+        if (i > 0 && (uint32_t)(kt[i - 1] >> 32) == key) continue;
+        const int len = run_len(i, key);
+        if (len < s) continue;
+        const int64_t ci = cbase[tr] + rb, off = mbase[tr] + rm;
+        if (ci < cap_cand) {
+            cand_trial[ci] = (int32_t)(trial_begin + tr);
+            cand_key[ci] = key;
+            cand_cnt[ci] = len;
+            cand_off[ci] = off;
+        }
+        for (int q = 0; q < len; ++q)
+            if (off + q < cap_members) members[off + q] = (int32_t)(kt[i + q] & 0xFFFFFFFFu);
+        ++rb;
+        rm += len;
+    }
+}
+
 }  // namespace
 }  // namespace proj
 
@@ -332,6 +458,34 @@ int run_allpairs(const uint32_t *packed, const uint8_t *codes, int alphabet, con
                                                           trial_begin, keys);
     }
     PROJ_LAUNCH_CHECK("ap_keys_kernel");
+    if (alphabet == 20 && x <= kSortMax) {  // sort path
+        int p2 = 2;
+        while (p2 < x) p2 <<= 1;
+        unsigned long long *sorted = reinterpret_cast<unsigned long long *>(lead_off);
+        const size_t smem = (size_t)p2 * 8;
+        PROJ_CUDA_TRY(cudaFuncSetAttribute(se_sort_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        {
+            TraceSpan ts_("enrich_sort", st);
+            se_sort_kernel<<<(unsigned)T, 1024, smem, st>>>(keys, (int)x, p2, s, sorted, nb, nm);
+        }
+        PROJ_LAUNCH_CHECK("se_sort_kernel");
+        {
+            TraceSpan ts_("enrich_sort", st);
+            ap_scan_kernel<<<1, 1024, 0, st>>>(nb, nm, (int)T, cbase, mbase, totals_dev, cap_cand,
+                                               cand_off_dev);
+        }
+        PROJ_LAUNCH_CHECK("ap_scan_kernel");
+        {
+            TraceSpan ts_("enrich_sort", st);
+            se_write_kernel<<<(unsigned)T, 1024, 0, st>>>(sorted, (int)x, s, cbase, mbase,
+                                                          trial_begin, cap_cand, cap_members,
+                                                          cand_trial_dev, cand_key_dev, cand_cnt_dev,
+                                                          cand_off_dev, members_dev);
+        }
+        PROJ_LAUNCH_CHECK("se_write_kernel");
+        return PROJ_OK;
+    }
     {
         TraceSpan ts_("allpairs", st);
         ap_compare_kernel<<<grid_x, kApThreads, 0, st>>>(keys, (int)x, cnt, rank, lead);

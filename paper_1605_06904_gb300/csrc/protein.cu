@@ -1,8 +1,9 @@
 // The motif search over the 20-letter protein alphabet (Section 2: |Sigma| = 20
 // for proteins; letters ACDEFGHIKLMNPQRSTVWY with codes 0..19).  Residues are
 // kept one per byte; keys are base 20, so 20^k buckets leave no room for a
-// histogram and the enriched buckets come from the all-pairs comparison
-// (csrc/allpairs.cu, k <= 6).  theta^0 and OOPS EM (Section 5.1) score in
+// histogram and the enriched buckets come from a per-trial sort of (key,
+// l-mer) pairs in shared memory, or the all-pairs comparison beyond 16,384
+// l-mers (csrc/allpairs.cu, k <= 6).  theta^0 and OOPS EM (Section 5.1) score in
 // FP32 over 20l weights per model; ranking and sites are FP64, as for DNA.
 #include <math.h>
 #include <stdlib.h>
@@ -332,9 +333,9 @@ int protein_impl(const uint8_t *ascii, const int64_t *seq_off, int t, int l, int
     }
     PROJ_LAUNCH_CHECK("aa_background_kernel");
 
-    // enriched buckets in one pass: a trial has at most min(4096, x / s)
-    // candidates and its members are distinct l-mers
-    const int64_t cap_c = m * std::min<int64_t>(4096, L.x / s), cap_m = m * L.x;
+    // enriched buckets in one pass: a trial has at most x / s candidates and
+    // its members are distinct l-mers
+    const int64_t cap_c = m * std::max<int64_t>(1, L.x / s), cap_m = m * L.x;
     DevBuf cand;
     PROJ_TRY(cand.alloc((size_t)cap_c * 12 + (size_t)(cap_c + 1) * 8 + (size_t)cap_m * 4 + 64, st));
     int64_t *cand_off = cand.as<int64_t>();
