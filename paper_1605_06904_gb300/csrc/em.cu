@@ -312,9 +312,10 @@ __device__ __forceinline__ void finalize_body(
     }
 }
 
-// Sites of the winner over many CTAs (one warp per sequence): FP64 scoring of
-// every l-mer is slow on one SM when t * n is large.
-__global__ void __launch_bounds__(256) sites_kernel(
+// Sites of the winner, one CTA (one warp) per sequence: the FP64 scoring of
+// every l-mer is spread over as many SMs as there are sequences (the FP64
+// pipe of this part is narrow).
+__global__ void __launch_bounds__(32) sites_kernel(
     const uint32_t *__restrict__ packed, int64_t nwords, const int32_t *__restrict__ seq_off,
     int t, int l, const double *__restrict__ bg, const float *__restrict__ theta,
     const int64_t *__restrict__ best, int32_t *__restrict__ sites) {
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(256) sites_kernel(
         return;
     }
     const float *th = theta + b * (int64_t)(4 * l);
-    if (tid < 4 * l) W[tid] = log((double)th[tid]) - log(bg[tid & 3]);
+    for (int q = tid; q < 4 * l; q += blockDim.x) W[q] = log((double)th[q]) - log(bg[q & 3]);
     __syncthreads();
     if (i >= t) return;
     const int64_t base = seq_off[i];
@@ -562,8 +563,8 @@ int launch_finalize(const uint32_t *packed, const Layout &L, const double *bg,
     PROJ_LAUNCH_CHECK("finalize_kernel");
     {
         TraceSpan ts_("finalize", st);
-        sites_kernel<<<(unsigned)((L.t + 7) / 8), 256, 0, st>>>(packed, L.nwords, L.seq_off_dev(),
-                                                                L.t, L.l, bg, theta, best, sites);
+        sites_kernel<<<(unsigned)L.t, 32, 0, st>>>(packed, L.nwords, L.seq_off_dev(), L.t, L.l, bg,
+                                                    theta, best, sites);
     }
     PROJ_LAUNCH_CHECK("sites_kernel");
     {

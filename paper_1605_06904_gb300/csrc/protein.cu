@@ -226,7 +226,8 @@ __global__ void __launch_bounds__(1024) aa_rank_kernel(const double *__restrict_
     }
 }
 
-// Sites of the winner: per sequence the first start of highest FP64 score.
+// Sites of the winner: per sequence the first start of highest FP64 score (one
+// CTA of one warp per sequence, spreading the FP64 work over the SMs).
 __global__ void __launch_bounds__(256) aa_sites_kernel(const uint8_t *__restrict__ codes,
                                                        const int32_t *__restrict__ seq_off, int t,
                                                        int l, const double *__restrict__ bg,
@@ -384,7 +385,7 @@ int protein_impl(const uint8_t *ascii, const int64_t *seq_off, int t, int l, int
     PROJ_LAUNCH_CHECK("aa_rank_kernel");
     {
         TraceSpan ts_("finalize", st);
-        aa_sites_kernel<<<(unsigned)((t + 7) / 8), 256, 0, st>>>(codes, L.seq_off_dev(), t, l, bg,
+        aa_sites_kernel<<<(unsigned)t, 32, 0, st>>>(codes, L.seq_off_dev(), t, l, bg,
                                                                 theta, best, sites);
     }
     PROJ_LAUNCH_CHECK("aa_sites_kernel");
