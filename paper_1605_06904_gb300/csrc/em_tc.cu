@@ -9,7 +9,7 @@
 // one-hot keys and values: per sequence a softmax over the starts j.
 //
 // Work is a list of items, each = (instance, up to 128 candidates of it, a
-// range of its sequences); a CTA (128 threads = the 128 lanes of tensor
+// range of its sequences); a CTA (128 candidate rows = the 128 lanes of tensor
 // memory) takes items in turn from the list (persistent over the list when the
 // grid is smaller than it), so one launch serves one motif search or a batch of
 // many instances of different t, n and l.  Per tile of 64 l-mers of a sequence:
@@ -19,19 +19,20 @@
 //   2. one thread issues S = W_hi X^T + W_lo X^T (M=128, N=64, K=16*ceil(4l/16),
 //      FP32 accumulation in tensor memory; W split into BF16 hi + lo parts so
 //      the product carries ~16 mantissa bits of W);
-//   3. thread i reads row i of S, keeps a running maximum and a compensated
-//      running sum of 2^(S - max) for its candidate, rescales its row of O when
-//      the maximum grows, and writes P = 2^(S - max) as BF16 hi + lo parts over
-//      its own columns of S in tensor memory;
+//   3. the two threads of row i read its scores S, add 2^(S - m) to a
+//      compensated running sum for the candidate (m a reference maximum, see
+//      below) and write P = 2^(S - m) as BF16 hi + lo parts over their own
+//      columns of S in tensor memory;
 //   4. one thread issues O += P_hi X + P_lo X (M=128, N=16*ceil(4l/16), K=64)
 //      with P read from tensor memory and X in MN-major form from the same
 //      shared-memory tile.
 // The steps of consecutive tiles overlap (two score buffers in tensor memory,
 // a ring of four one-hot tiles): the score MMA of tile i+1 and the count MMA
 // of tile i-1 run on the tensor core while the CUDA cores work on tile i.
-// At the end of a sequence O / sum is added to the candidate's counts and
-// max + log2(sum) to its log-likelihood.  Scores are kept in log2 units
-// (W = log2 theta - log2 bg) so the exponentials are exp2.
+// At the end of a sequence m + log2(sum) goes to the candidate's
+// log-likelihood and O / sum to its counts (O read during the next tile).
+// Scores are kept in log2 units (W = log2 theta - log2 bg) so the
+// exponentials are exp2.
 //
 // Every wait on an MMA completion is bounded; when a bound expires the CTA
 // stops, records the failure in a device flag (returned as PROJ_ETIMEOUT) and
@@ -226,18 +227,18 @@ __device__ __forceinline__ float max_half(const float (&v)[32], int nv) {
 // The CTA has 288 threads.  Warps 0-7 compute the softmax: warps w and w + 4
 // share the tensor-memory lanes 32*(w%4) .. +31 (candidate rows), warp w
 // taking the first 32 l-mers of each tile and warp w + 4 the last 32; the two
-// threads of a row keep one reference maximum m (agreed through shared memory
-// at the first tile of a sequence), their own compensated sums, and each reads
-// and accumulates half of the row's count columns.  Warp 8 issues the MMAs
-// (one elected thread), so issuing never stalls the softmax warps.
+// threads of a row share one reference maximum m, keep their own compensated
+// sums (added together through shared memory at a sequence end), and each
+// reads and accumulates half of the row's count columns.  Warp 8 issues the
+// MMAs (one elected thread), so issuing never stalls the softmax warps.
 //
 // Pipeline over the tiles j = 0 .. n-1 of an item, linked by mbarriers:
 //   issuer: S(0), S(1); then per j: [P(j) written] O (+)= P X(j);
 //           [X(j+2) landed, (E-step only) S buffer of j read] S(j+2) = W X(j+2)^T
-//   softmax, per j: [S(j) ready] read S(j), release its buffer; P = 2^(S-m);
-//           write P(j) over S(j); [count MMA of j-1 done] one thread starts the
-//           copy of X(j+3) into the slot of tile j-1; at a sequence end [count
-//           MMA of j done] read O.
+//   softmax, per j: [S(j) ready] read S(j), (E-step only) release its buffer;
+//           P = 2^(S-m); write P(j) over S(j); [count MMA of j-1 done] read the
+//           O of a sequence that ended with tile j-1, announce P(j); one thread
+//           starts the copy of X(j+3) into the slot of tile j-1.
 // Two score buffers in tensor memory (each holding S(j), then P(j)) and a ring
 // of four one-hot tiles in shared memory.  S(j+2) overwrites P(j) only after
 // the count MMA that reads P(j): tcgen05.mma operations issued by one thread
