@@ -125,7 +125,7 @@ def test_worked_example_bucket(P, fig1):
 
 
 @pytest.mark.parametrize("cfg,trials", [(1, (0, 100)), (2, (0, 172)), (3, (0, 150)),
-                                        (3, (1850, 150))])
+                                        (3, (1850, 150)), (5, (0, 3)), (5, (497, 3))])
 def test_hash_configs_bit_exact(P, cfg, trials):
     inst = instance_for_config(cfg)
     prm = inst.params
