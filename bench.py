@@ -752,6 +752,12 @@ def main():
         line["cpu_baseline"] = {"value": scores_step / tt, "unit": UNIT, "cores": det["threads"],
                                 "kind": "oracle", "sample": sample_text(det, m),
                                 "seconds_per_step_extrapolated": tt}
+        # the same oracle on one core (a smaller EM sample, same extrapolation)
+        tt1, det1 = oracle_step(inst, k, s, m, seed, iters, beta,
+                                max_sample=max(1, args.ref_sample // 16), nthreads=1)
+        line["cpu_baseline"]["single_thread"] = {
+            "value": scores_step / tt1, "unit": UNIT, "cores": 1, "sample": sample_text(det1, m),
+            "seconds_per_step_extrapolated": tt1}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
