@@ -54,6 +54,7 @@ def _check(got, want, inst):
     (9, 9, 64, 6, 1, 2, 2, 5, 2, 0.5),         # short sequences, many small buckets
     (10, 6, 40, 8, 1, 6, 2, 20, 4, 0.1),       # k = 6, the largest base-20 key
     (15, 30, 600, 12, 3, 4, 3, 10, 3, 0.25),   # x = 17,670 > 16,384: all-pairs enrichment
+    (16, 1, 300, 32, 6, 1, 1, 3, 2, 0.25),     # one sequence, l = 32, k = 1, s = 1
 ])
 def test_protein_search_matches_oracle(native_lib, case):
     seed, t, n, l, d, k, s, m, iters, beta = case
