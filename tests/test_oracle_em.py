@@ -254,3 +254,63 @@ def test_zoops_map_objective_non_decreasing(seed):
         prev = obj
         pwm = O.em_zoops(codes, inst.seq_off, 9, bg, pwm[None], 1, 0.25, 0.5)[0][0]
         assert np.allclose(pwm.sum(axis=1), 1.0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Column 0 of theta (Section 5.1, Figure 4): the background model, and the
+# ranking rule.  Values are counted by hand from the strings, not recomputed
+# by a second implementation.
+# --------------------------------------------------------------------------
+
+def test_background_hand_counted_dna():
+    """0-order base frequencies in code order A, C, T, G (Section 6's codes);
+    a base that never occurs is counted once (reading R7)."""
+    # A 2, C 3, T 1, G absent -> 1: total 7
+    assert np.array_equal(O.background(O.encode(b"AACCCT")),
+                          np.array([2 / 7, 3 / 7, 1 / 7, 1 / 7]))
+    # every base present, lower case accepted: A 1, C 1, T 2, G 2 of 6
+    assert np.array_equal(O.background(O.encode(b"acgttg")),
+                          np.array([1 / 6, 1 / 6, 2 / 6, 2 / 6]))
+    # only G: G 5, the three absent bases once each, total 8
+    assert np.array_equal(O.background(O.encode(b"GGGGG")),
+                          np.array([1 / 8, 1 / 8, 1 / 8, 5 / 8]))
+    # the worked example of Figure 1 is near-uniform, as the 0.25 of Figure 4
+    # assumes: every base between 0.2 and 0.3
+    from conftest import golden_lines
+    bg = O.background(O.encode("".join(golden_lines("fig1_sequences.txt")).encode()))
+    assert bg.sum() == pytest.approx(1.0, abs=1e-15)
+    assert np.all((bg > 0.2) & (bg < 0.3))
+
+
+def test_background_hand_counted_protein():
+    """The same rule over the 20 letters ACDEFGHIKLMNPQRSTVWY (codes 0..19)."""
+    bg = O.background_a(O.encode_aa(b"WWWY"), 20)
+    want = np.full(20, 1 / 22)  # 18 absent letters once each + W 3 + Y 1 = 22
+    want[18] = 3 / 22  # W
+    want[19] = 1 / 22  # Y
+    assert np.array_equal(bg, want)
+    bg = O.background_a(O.encode_aa(b"AACD" + b"ACDEFGHIKLMNPQRSTVWY"), 20)
+    want = np.full(20, 1 / 24)
+    want[0] = 3 / 24  # A: 2 + 1
+    want[1] = 2 / 24  # C
+    want[2] = 2 / 24  # D
+    assert np.array_equal(bg, want)
+
+
+def test_rank_ties_go_to_the_first_candidate():
+    """Ranking (Section 5.1, reading R12): the largest LL wins; among equal LLs
+    the candidate earlier in (trial, key) order."""
+    assert O.rank(np.array([1.0, 3.0, 3.0, 2.0])) == 1
+    assert O.rank(np.array([-5.0, -5.0])) == 0
+    assert O.rank(np.array([2.0, 1.0, 7.5, 7.5, 7.5])) == 2
+    assert O.rank(np.array([-np.inf, 0.0])) == 1
+    assert O.rank(np.array([])) == -1
+
+
+def test_top_candidates_order():
+    """The serving-scale cap keeps the largest buckets; equal sizes keep
+    (trial, key) order."""
+    cnt = np.array([4, 7, 5, 7, 4, 9])
+    assert list(O.top_candidates(cnt, 3)) == [5, 1, 3]
+    assert list(O.top_candidates(cnt, 5)) == [5, 1, 3, 2, 0]
+    assert list(O.top_candidates(cnt, 10)) == [5, 1, 3, 2, 0, 4]
