@@ -135,14 +135,20 @@ int trial_hash(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
  * is allocated: the scratch lives in one fixed array of
  * PROJ_NOALLOC_SCRATCH_BYTES inside the library, held by every GPU that loads
  * the library until the process exits.  Needs
- *   8 (t+1) + 16 n_units + 8 cap_members   bytes (each part rounded up to 256),
- * n_units = n_trials * ceil(4^k / 32768) (a single part when 4^k <= 32768, or
- * when 4^k <= 65536 and x <= 65535); a request above the limit returns
- * PROJ_ECAPACITY with a message and launches nothing.  All calls share the
- * array: calls whose device work overlaps (other streams, other threads) race
- * and must be serialised by the caller.  The first call on each device looks
- * up the array's device address (once, with that device current); make that
- * first call before any stream capture. */
+ *   a(8 (t+1)) + a(8 n_units) + a(16 n_units) + a(8 cap_members)   bytes,
+ * a(v) = v rounded up to a multiple of 256, n_units = n_trials * parts with
+ *   parts = 1                 when 4^k <= 32768 (u32 counters in one CTA),
+ *   parts = max(1, 4^k/65536) when 4^k > 32768 and x <= 65535 (u16 counters),
+ *   parts = 4^k / 32768       otherwise (u32 counters, key-range parts),
+ * x = number of l-mers.  A request above the limit returns PROJ_ECAPACITY with
+ * a message and launches nothing.  All calls share the array: calls whose
+ * device work overlaps (other streams, other threads) race and must be
+ * serialised by the caller.  The first call on each device looks up the
+ * array's device address (once, with that device current) and keeps it for
+ * the life of the process (no cudaDeviceReset in between); make that first
+ * call before any stream capture.  The sequence offsets reach the device
+ * inside kernel parameters, so no device work reads seq_off after the call
+ * returns. */
 #define PROJ_NOALLOC_SCRATCH_BYTES (8u << 20)
 int trial_hash_noalloc(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l, int k,
                        int s, uint64_t seed, int64_t trial_begin, int64_t n_trials,

@@ -935,7 +935,9 @@ void *g_noalloc_ptr[64];  // device address of g_noalloc_scratch per device ordi
 
 // Looks up (once per device, with that device current) the device address of
 // the scratch array.  In host code the array's name is only a host-side
-// stand-in, so kernels must receive this address instead.
+// stand-in, so kernels must receive this address instead.  The cached address
+// assumes the device's primary context lives as long as the process: after a
+// cudaDeviceReset the module is loaded again and the cache would be stale.
 int noalloc_scratch(void **out) {
     int dev = 0;
     PROJ_CUDA_TRY(cudaGetDevice(&dev));
@@ -951,6 +953,20 @@ int noalloc_scratch(void **out) {
 }
 
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+// The sequence and l-mer offsets travel to the scratch array inside kernel
+// parameters (copied by value at launch), not by a copy from host memory, so
+// nothing on the device refers to the caller's or this call's host buffers.
+constexpr int kOffChunk = 992;  // int32 values per launch (parameters stay under 4 KB)
+struct OffChunk {
+    int32_t *dst;
+    int n;
+    int32_t v[kOffChunk];
+};
+
+__global__ void noalloc_offsets_kernel(const OffChunk c) {
+    for (int i = threadIdx.x; i < c.n; i += blockDim.x) c.dst[i] = c.v[i];
+}
 
 }  // namespace
 }  // namespace proj
@@ -1058,8 +1074,14 @@ extern "C" int trial_hash_noalloc(const uint32_t *packed_dev, const int64_t *seq
     P.scratch_gid = (int32_t *)(P.scratch_key + cap_members);
     // every scratch word is written before it is read (offsets here, counts by
     // pass 1, bases by the scan, the list by pass 2), so nothing is cleared
-    PROJ_CUDA_TRY(cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int32_t),
-                                  cudaMemcpyHostToDevice, st));
+    for (size_t b = 0; b < off.size(); b += kOffChunk) {
+        OffChunk c;
+        c.dst = d_off + b;
+        c.n = (int)std::min<size_t>(kOffChunk, off.size() - b);
+        std::copy(off.begin() + b, off.begin() + b + c.n, c.v);
+        noalloc_offsets_kernel<<<1, 256, 0, st>>>(c);
+        PROJ_LAUNCH_CHECK("noalloc_offsets_kernel");
+    }
 
     if (n_units == 0) {
         PROJ_CUDA_TRY(cudaMemsetAsync(totals_dev, 0, 2 * sizeof(int64_t), st));

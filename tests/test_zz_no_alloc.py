@@ -96,3 +96,86 @@ def test_noalloc_refuses_work_beyond_its_scratch(native_lib):
         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == -3 and b"scratch" in native_lib.projection_last_error()
     assert tot.cpu().tolist() == [-9, -9]  # nothing was launched
+
+
+def _random_input(seed, t, nmin, nmax):
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(nmin, nmax + 1, t)
+    seqs = [np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, n)].tobytes() for n in lens]
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    return b"".join(seqs), off
+
+
+def _parts(k, x):
+    """Key-range parts per trial, as the header states them."""
+    nb = 4 ** k
+    if nb <= 32768:
+        return 1
+    if x <= 65535:
+        return max(1, nb // 65536)
+    return nb // 32768
+
+
+def test_noalloc_many_parts_over_a_large_input(native_lib):
+    """k = 9 over x > 65,535 l-mers: 8 key-range parts of u32 counters, each
+    CTA scanning every l-mer of its trial (trial_hash partitions the pairs
+    first instead).  Bit for bit the same lists."""
+    import paper_1605_06904_gb300 as P
+    torch.cuda.set_device(0)
+    ascii, off = _random_input(8, 6, 19000, 21000)
+    l, k, s = 16, 9, 2
+    x = int(np.sum(np.diff(off) - l + 1))
+    assert x > 65535 and _parts(k, x) == 8
+    packed = P.projection_pack(torch.frombuffer(bytearray(ascii), dtype=torch.uint8).cuda())
+    for seed, T in ((5, 6), (6, 3)):
+        C, M = _same(P, packed, off, l, k, s, seed, 1, T, native_lib)
+        assert C > 0 and M > 0
+
+
+def _need(t, n_trials, parts, cap_m):
+    a = lambda v: (v + 255) // 256 * 256  # noqa: E731
+    return a(8 * (t + 1)) + a(8 * n_trials * parts) + a(16 * n_trials * parts) + a(8 * cap_m)
+
+
+def test_noalloc_scratch_formula_is_exact(native_lib):
+    """The largest trial count the header's scratch formula allows is accepted;
+    one more is refused with ECAPACITY before anything is launched.  Three
+    counter layouts: one part (k = 7), u16 parts (k = 9, x <= 65,535), u32 parts
+    (k = 9, x > 65,535)."""
+    import paper_1605_06904_gb300 as P
+    torch.cuda.set_device(0)
+    limit = 8 << 20
+    inst = instance_for_config(1)
+    big_ascii, big_off = _random_input(8, 6, 19000, 21000)
+    shapes = [(inst.ascii.tobytes(), inst.seq_off, 11, 7, 4),
+              (inst.ascii.tobytes(), inst.seq_off, 11, 9, 3),
+              (big_ascii, big_off, 16, 9, 3)]
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for ascii, off, l, k, s in shapes:
+        t = off.size - 1
+        x = int(np.sum(np.diff(off) - l + 1))
+        parts = _parts(k, x)
+        # leave room for about 150 trials next to the compaction list
+        cap_m = (limit - 256 - 24 * parts * 150) // 8
+        n_max = 0
+        while _need(t, n_max + 1, parts, cap_m) <= limit:
+            n_max += 1
+        assert 100 <= n_max <= 200
+        packed = P.projection_pack(torch.frombuffer(bytearray(ascii), dtype=torch.uint8).cuda())
+        offc = np.ascontiguousarray(off, np.int64)
+        buf_c = torch.zeros(16, dtype=torch.int32, device="cuda")
+        buf_o = torch.zeros(17, dtype=torch.int64, device="cuda")
+        buf_m = torch.zeros(cap_m, dtype=torch.int32, device="cuda")
+        for n, want_rc in ((n_max, 0), (n_max + 1, -3)):
+            tot = torch.full((2,), -9, dtype=torch.int64, device="cuda")
+            rc = native_lib.trial_hash_noalloc(
+                _ptr(packed), ctypes.c_void_p(offc.ctypes.data), t, l, k, s, 3, 0, n, None, None,
+                None, 16, cap_m, _ptr(buf_c), _ptr(buf_c), _ptr(buf_c), _ptr(buf_o), _ptr(buf_m),
+                _ptr(tot), stream)
+            assert rc == want_rc, (k, x, n, native_lib.projection_last_error())
+            if want_rc == 0:
+                C, M = tot.cpu().tolist()
+                ref = P.trial_hash(packed, off, l, k, s, 3, 0, n)
+                assert (C, M) == (ref["n_candidates"], ref["n_members"])
+            else:
+                assert tot.cpu().tolist() == [-9, -9]
