@@ -181,11 +181,15 @@ int theta0_build(const uint32_t *packed_dev, const int64_t *seq_off, int t, int 
  *   LL = sum_i [ log sum_j exp r(i,j) - log(n_i - l + 1) ],
  * per-sequence log-sum-exp in FP32, sum over sequences in FP64.
  * bg_dev: double[4] from projection_background.  precision: PROJ_EM_FP32 or
- * PROJ_EM_BF16_SPLIT.  pseudocount must be > 0. */
+ * PROJ_EM_BF16_SPLIT.  pseudocount must be > 0.
+ * sites_out_dev: int32[C][t] or NULL.  When given, row c receives the start
+ * vector of Definition 1 (Section 2) under candidate c's final model: per
+ * sequence i the first 0-based start j maximising r(i,j), evaluated in FP64
+ * from theta_out_dev (as projection_finalize does for the winner). */
 int em_refine(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
               const double *bg_dev, const float *theta0_dev, int64_t C, int em_iters,
               float pseudocount, int precision, float *theta_out_dev, double *loglik_dev,
-              void *stream);
+              int32_t *sites_out_dev, void *stream);
 
 /* The same refinement under the zero-or-one-occurrence model (ZOOPS, the
  * second search model named in Section 2): a sequence holds one site with
@@ -195,11 +199,12 @@ int em_refine(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
  * the posterior of a site at j is (site_prob / ns_i) e^{r(i,j)} / e^{L_i}, and the
  * M-step is theta_p(a) = (sum z [x = a] + pseudocount) / (sum z + 4 pseudocount).
  * site_prob = 1 is the OOPS model of em_refine (up to rounding).  Arguments,
- * layouts and errors as em_refine; EINVAL for site_prob outside (0, 1]. */
+ * layouts and errors as em_refine (sites_out_dev: the first start of highest
+ * score in every sequence, as there); EINVAL for site_prob outside (0, 1]. */
 int em_refine_zoops(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
                     const double *bg_dev, const float *theta0_dev, int64_t C, int em_iters,
                     float pseudocount, int precision, double site_prob, float *theta_out_dev,
-                    double *loglik_dev, void *stream);
+                    double *loglik_dev, int32_t *sites_out_dev, void *stream);
 
 /* ---- step a9: rank and finalise ----------------------------------------- */
 

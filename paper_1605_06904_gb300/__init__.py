@@ -214,17 +214,22 @@ def theta0_build(packed, seq_off, l, cand_off, members, C, pseudocount, stream=N
 
 
 def em_refine(packed, seq_off, l, bg, theta0, em_iters, pseudocount, precision=PROJ_EM_FP32,
-              out=None, stream=None):
+              out=None, stream=None, want_sites=False):
     """OOPS EM (Section 5.1) from theta0 [C, l, 4] (float32 CUDA).  Returns
-    (theta [C, l, 4] float32, loglik [C] float64)."""
+    (theta [C, l, 4] float32, loglik [C] float64), plus sites [C, t] int32
+    (Definition 1's start vector under each final model) with want_sites."""
     off = _off(seq_off)
     C = theta0.shape[0]
+    t = off.size - 1
     theta0 = theta0.contiguous()
     th = torch.empty_like(theta0) if out is None else out
     ll = _dev(max(1, C), torch.float64, theta0.device)
-    check(lib().em_refine(_ptr(packed), _ptr(off), off.size - 1, l, _ptr(bg), _ptr(theta0), C,
+    sites = _dev(max(1, C * t), torch.int32, theta0.device) if want_sites else None
+    check(lib().em_refine(_ptr(packed), _ptr(off), t, l, _ptr(bg), _ptr(theta0), C,
                           em_iters, float(pseudocount), precision, _ptr(th), _ptr(ll),
-                          _stream(stream)))
+                          _ptr(sites), _stream(stream)))
+    if want_sites:
+        return th, ll[:C], sites[:C * t].view(C, t)
     return th, ll[:C]
 
 
@@ -313,17 +318,22 @@ def projection_find_protein(ascii, seq_off, l, k, s, m, seed=0, em_iters=5, pseu
 
 
 def em_refine_zoops(packed, seq_off, l, bg, theta0, em_iters, pseudocount, site_prob,
-                    precision=PROJ_EM_FP32, out=None, stream=None):
+                    precision=PROJ_EM_FP32, out=None, stream=None, want_sites=False):
     """ZOOPS EM (site probability `site_prob` per sequence) from theta0 [C, l, 4]
-    (float32 CUDA).  Returns (theta [C, l, 4] float32, loglik [C] float64)."""
+    (float32 CUDA).  Returns (theta [C, l, 4] float32, loglik [C] float64), plus
+    sites [C, t] int32 with want_sites."""
     off = _off(seq_off)
     C = theta0.shape[0]
+    t = off.size - 1
     theta0 = theta0.contiguous()
     th = torch.empty_like(theta0) if out is None else out
     ll = _dev(max(1, C), torch.float64, theta0.device)
-    check(lib().em_refine_zoops(_ptr(packed), _ptr(off), off.size - 1, l, _ptr(bg), _ptr(theta0),
+    sites = _dev(max(1, C * t), torch.int32, theta0.device) if want_sites else None
+    check(lib().em_refine_zoops(_ptr(packed), _ptr(off), t, l, _ptr(bg), _ptr(theta0),
                                 C, em_iters, float(pseudocount), precision, float(site_prob),
-                                _ptr(th), _ptr(ll), _stream(stream)))
+                                _ptr(th), _ptr(ll), _ptr(sites), _stream(stream)))
+    if want_sites:
+        return th, ll[:C], sites[:C * t].view(C, t)
     return th, ll[:C]
 
 

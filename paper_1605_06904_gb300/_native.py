@@ -48,8 +48,9 @@ SIGNATURES = {
     "trial_hash_noalloc": ([P, P, i32, i32, i32, i32, u64, i64, i64, P, P, P, i64, i64, P, P, P,
                             P, P, P, P], i32),
     "theta0_build": ([P, P, i32, i32, P, P, i64, f32, P, P], i32),
-    "em_refine": ([P, P, i32, i32, P, P, i64, i32, f32, i32, P, P, P], i32),
-    "em_refine_zoops": ([P, P, i32, i32, P, P, i64, i32, f32, i32, ctypes.c_double, P, P, P], i32),
+    "em_refine": ([P, P, i32, i32, P, P, i64, i32, f32, i32, P, P, P, P], i32),
+    "em_refine_zoops": ([P, P, i32, i32, P, P, i64, i32, f32, i32, ctypes.c_double, P, P, P,
+                         P], i32),
     "projection_find_packed_zoops": ([P, P, i32, i32, i32, i32, i32, i32, u64, i32, f32, i32,
                                       ctypes.c_double, i64, ctypes.POINTER(ProjectionResult), P],
                                      i32),

@@ -236,7 +236,7 @@ int theta0_build(const uint32_t *packed_dev, const int64_t *seq_off, int t, int 
 int em_refine(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
               const double *bg_dev, const float *theta0_dev, int64_t C, int em_iters,
               float pseudocount, int precision, float *theta_out_dev, double *loglik_dev,
-              void *stream) {
+              int32_t *sites_out_dev, void *stream) {
     clear_error();
     cudaStream_t st = (cudaStream_t)stream;
     PROJ_REQUIRE(C >= 0, "need C >= 0");
@@ -244,14 +244,17 @@ int em_refine(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
                  "NULL buffer");
     Layout L;
     PROJ_TRY(make_layout(seq_off, t, l, st, L));
-    return run_em(packed_dev, L, bg_dev, theta0_dev, C, em_iters, pseudocount, precision,
-                  theta_out_dev, loglik_dev, st);
+    PROJ_TRY(run_em(packed_dev, L, bg_dev, theta0_dev, C, em_iters, pseudocount, precision,
+                    theta_out_dev, loglik_dev, st));
+    if (sites_out_dev)
+        PROJ_TRY(launch_cand_sites(packed_dev, L, bg_dev, theta_out_dev, C, sites_out_dev, st));
+    return PROJ_OK;
 }
 
 int em_refine_zoops(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
                     const double *bg_dev, const float *theta0_dev, int64_t C, int em_iters,
                     float pseudocount, int precision, double site_prob, float *theta_out_dev,
-                    double *loglik_dev, void *stream) {
+                    double *loglik_dev, int32_t *sites_out_dev, void *stream) {
     clear_error();
     cudaStream_t st = (cudaStream_t)stream;
     PROJ_REQUIRE(C >= 0, "need C >= 0");
@@ -260,8 +263,11 @@ int em_refine_zoops(const uint32_t *packed_dev, const int64_t *seq_off, int t, i
                  "NULL buffer");
     Layout L;
     PROJ_TRY(make_layout(seq_off, t, l, st, L));
-    return run_em(packed_dev, L, bg_dev, theta0_dev, C, em_iters, pseudocount, precision,
-                  theta_out_dev, loglik_dev, st, site_prob);
+    PROJ_TRY(run_em(packed_dev, L, bg_dev, theta0_dev, C, em_iters, pseudocount, precision,
+                    theta_out_dev, loglik_dev, st, site_prob));
+    if (sites_out_dev)
+        PROJ_TRY(launch_cand_sites(packed_dev, L, bg_dev, theta_out_dev, C, sites_out_dev, st));
+    return PROJ_OK;
 }
 
 int projection_finalize(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,

@@ -190,6 +190,10 @@ int run_em(const uint32_t *packed, const Layout &L, const double *bg, const floa
            int64_t C, int iters, float beta, int precision, float *theta_out, double *ll,
            cudaStream_t st, double gamma = 1.0, int *err_dev = nullptr);
 
+// Per candidate c < C and sequence i: sites[c][i] = the first start j that
+// maximises r(i,j) under theta[c], scored in FP64 (Definition 1's start vector).
+int launch_cand_sites(const uint32_t *packed, const Layout &L, const double *bg,
+                      const float *theta, int64_t C, int32_t *sites, cudaStream_t st);
 int launch_finalize(const uint32_t *packed, const Layout &L, const double *bg,
                     const float *theta, const double *ll, int64_t C, int64_t *best,
                     int32_t *sites, uint8_t *consensus, int32_t *score, cudaStream_t st);

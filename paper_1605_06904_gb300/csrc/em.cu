@@ -350,6 +350,40 @@ __global__ void __launch_bounds__(32) sites_kernel(
     if (lane == 0) sites[i] = ns > 0 ? bj : -1;
 }
 
+// Sites of every candidate (Definition 1's start vector s under each model):
+// one CTA per candidate, W = log theta - log bg in FP64 in shared memory, one
+// warp per sequence in turn; ties go to the first start, as for the winner.
+__global__ void __launch_bounds__(256) cand_sites_kernel(
+    const uint32_t *__restrict__ packed, int64_t nwords, const int32_t *__restrict__ seq_off,
+    int t, int l, const double *__restrict__ bg, const float *__restrict__ theta,
+    int32_t *__restrict__ sites) {
+    __shared__ double W[32 * 4];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t c = blockIdx.x;
+    const float *th = theta + c * (int64_t)(4 * l);
+    for (int q = tid; q < 4 * l; q += blockDim.x) W[q] = log((double)th[q]) - log(bg[q & 3]);
+    __syncthreads();
+    for (int i = warp; i < t; i += blockDim.x / 32) {
+        const int64_t base = seq_off[i];
+        const int ns = seq_off[i + 1] - seq_off[i] - l + 1;
+        double bestv = -INFINITY;
+        int bj = 0x7fffffff;
+        for (int j = lane; j < ns; j += 32) {
+            const uint64_t win = window64(packed, nwords, base + j);
+            double r = 0.0;
+            for (int p = 0; p < l; ++p) r += W[p * 4 + (int)((win >> (2 * p)) & 3u)];
+            if (r > bestv) { bestv = r; bj = j; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_down_sync(0xffffffffu, bestv, o);
+            const int oj = __shfl_down_sync(0xffffffffu, bj, o);
+            if (ob > bestv || (ob == bestv && oj < bj)) { bestv = ob; bj = oj; }
+        }
+        if (lane == 0) sites[c * t + i] = ns > 0 ? bj : -1;
+    }
+}
+
 // Score(s, DNA) of the winner's sites: sum over columns of the largest count.
 __global__ void __launch_bounds__(1024) score_kernel(
     const uint32_t *__restrict__ packed, int64_t nwords, const int32_t *__restrict__ seq_off,
@@ -572,6 +606,20 @@ int launch_finalize(const uint32_t *packed, const Layout &L, const double *bg,
         score_kernel<<<1, 1024, 0, st>>>(packed, L.nwords, L.seq_off_dev(), L.t, L.l, sites, score);
     }
     PROJ_LAUNCH_CHECK("score_kernel");
+    return PROJ_OK;
+}
+
+int launch_cand_sites(const uint32_t *packed, const Layout &L, const double *bg,
+                      const float *theta, int64_t C, int32_t *sites, cudaStream_t st) {
+    PROJ_REQUIRE(L.l <= 32, "l above 32 is not supported");
+    PROJ_REQUIRE(C < ((int64_t)1 << 31), "too many candidates");
+    if (C == 0) return PROJ_OK;
+    {
+        TraceSpan ts_("cand_sites", st);
+        cand_sites_kernel<<<(unsigned)C, 256, 0, st>>>(packed, L.nwords, L.seq_off_dev(), L.t, L.l,
+                                                       bg, theta, sites);
+    }
+    PROJ_LAUNCH_CHECK("cand_sites_kernel");
     return PROJ_OK;
 }
 

@@ -374,3 +374,42 @@ def test_find_config2_full_size(P):
     assert np.all(np.abs(ll.cpu().numpy()[sample] - want["ll_all"][sample]) <=
                   ll_tol(want["ll_all"][sample], inst.t))
     assert fin["consensus"] == want["consensus"]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16split"])
+def test_em_refine_sites_of_every_candidate(P, precision):
+    """em_refine's sites_out: per candidate, Definition 1's start vector under
+    its final model (first start of highest r, FP64), identical to the oracle's
+    `sites` evaluated on the same model, for 300 candidates of config 1."""
+    inst = instance_for_config(1)
+    th0 = _sample_theta0(P, inst, 1001, 300)
+    codes = O.encode(inst.ascii)
+    packed = upload(P, inst.ascii)
+    bg = P.projection_background(packed, inst.seq_off[-1])
+    prec = P.PROJ_EM_FP32 if precision == "fp32" else P.PROJ_EM_BF16_SPLIT
+    th, ll, st = P.em_refine(packed, inst.seq_off, inst.l, bg, torch.from_numpy(th0).cuda(), 5,
+                             0.25, prec, want_sites=True)
+    th, st = th.cpu().numpy().astype(np.float64), st.cpu().numpy()
+    assert st.shape == (th0.shape[0], inst.t)
+    obg = O.background(codes)
+    for c in range(th.shape[0]):
+        assert np.array_equal(st[c], O.sites(codes, inst.seq_off, inst.l, obg, th[c])), c
+    # the models themselves still match the oracle's
+    w_pwm, _ = O.em(codes, inst.seq_off, inst.l, obg, th0.astype(np.float64), 5, 0.25, nthreads=8)
+    assert np.max(np.abs(th - w_pwm)) <= (PWM_TOL if precision == "fp32" else 5e-5)
+
+
+def test_em_refine_zoops_sites_of_every_candidate(P):
+    """The same output of the ZOOPS refinement (sites as for OOPS: the first
+    start of highest score in every sequence)."""
+    inst = instance_for_config(1)
+    th0 = _sample_theta0(P, inst, 1001, 64)
+    codes = O.encode(inst.ascii)
+    packed = upload(P, inst.ascii)
+    bg = P.projection_background(packed, inst.seq_off[-1])
+    th, ll, st = P.em_refine_zoops(packed, inst.seq_off, inst.l, bg, torch.from_numpy(th0).cuda(),
+                                   5, 0.25, 0.6, P.PROJ_EM_FP32, want_sites=True)
+    th, st = th.cpu().numpy().astype(np.float64), st.cpu().numpy()
+    obg = O.background(codes)
+    for c in range(th.shape[0]):
+        assert np.array_equal(st[c], O.sites(codes, inst.seq_off, inst.l, obg, th[c])), c
