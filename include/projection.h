@@ -127,6 +127,25 @@ int trial_hash(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l,
                int32_t *cand_cnt_dev, int64_t *cand_off_dev, int32_t *members_dev,
                int64_t *totals_dev, void *stream);
 
+/* Algorithm 2 steps 2-3 for trials 0 .. n_trials-1, keeping only the `top`
+ * largest enriched buckets: the paper enriches buckets by the threshold s
+ * alone (Algorithm 2 step 3); inputs with 10^6..10^7 enriched buckets refine
+ * a bounded number of them.  Buckets are ordered by size, largest first, ties
+ * in (trial, key) order, and R = min(top, C) are kept, C = all enriched.
+ * Outputs, in that order (device buffers of top entries, cand_off top+1):
+ *   sel_index_dev  int64: the bucket's index in trial_hash's (trial, key) list
+ *   cand_trial_dev, cand_key_dev, cand_cnt_dev: as trial_hash
+ *   cand_off_dev   int64[R+1] offsets of the kept buckets' members in
+ *   members_dev    int32[cap_members]: global l-mer ids, ascending per bucket.
+ * totals_dev int64[4] receives C, the members of all enriched buckets, R and
+ * the members of the kept ones; PROJ_ECAPACITY (nothing else written) when
+ * the last exceeds cap_members.  top >= 1.  Synchronises `stream`. */
+int trial_hash_top(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l, int k, int s,
+                   uint64_t seed, int64_t n_trials, int64_t top, int64_t cap_members,
+                   int64_t *sel_index_dev, int32_t *cand_trial_dev, uint32_t *cand_key_dev,
+                   int32_t *cand_cnt_dev, int64_t *cand_off_dev, int32_t *members_dev,
+                   int64_t *totals_dev, void *stream);
+
 /* The paper has no counterpart to this call; it serves callers of this library
  * that cannot allocate device memory -- a service that gave all device memory
  * to its own pool allocator at start-up, or a latency-critical path that must

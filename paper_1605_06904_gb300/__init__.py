@@ -17,7 +17,7 @@ from ._native import (PROJ_EM_BF16_SPLIT, PROJ_EM_FP32, ProjectionError,  # noqa
 
 __all__ = ["projection_packed_words", "projection_default_params", "projection_pack",
            "projection_background", "projection_positions", "trial_hash",
-           "trial_hash_noalloc", "theta0_build",
+           "trial_hash_noalloc", "trial_hash_top", "theta0_build",
            "em_refine", "projection_finalize", "projection_find", "projection_find_packed",
            "projection_find_batch", "projection_find_top", "projection_find_protein", "projection_find_packed_top",
            "projection_trace_enable", "projection_trace_read", "projection_selftest_wait",
@@ -141,6 +141,38 @@ def trial_hash(packed, seq_off, l, k, s, seed, trial_begin, n_trials, positions_
     if want_counts:
         out["counts"] = cnt[:n_trials * 4 ** k].view(n_trials, 4 ** k)
     return out
+
+
+def trial_hash_top(packed, seq_off, l, k, s, seed, n_trials, top, cap_members=None, stream=None):
+    """Algorithm 2 steps 2-3 for trials [0, n_trials), keeping the `top` largest
+    enriched buckets (size descending, ties in (trial, key) order).  Returns a
+    dict of CUDA tensors sel_index, cand_trial, cand_key (int32 storage of
+    uint32), cand_cnt, cand_off, members, and the totals."""
+    off = _off(seq_off)
+    t = off.size - 1
+    dev = packed.device
+    if cap_members is None:
+        cap_members = max(1, 64 * top)
+    while True:
+        si = _dev(top, torch.int64, dev)
+        ct = _dev(top, torch.int32, dev)
+        ck = _dev(top, torch.int32, dev)
+        cc = _dev(top, torch.int32, dev)
+        co = _dev(top + 1, torch.int64, dev)
+        mem = _dev(cap_members, torch.int32, dev)
+        tot = _dev(4, torch.int64, dev)
+        rc = lib().trial_hash_top(_ptr(packed), _ptr(off), t, l, k, s, seed & (2**64 - 1), n_trials,
+                                  top, cap_members, _ptr(si), _ptr(ct), _ptr(ck), _ptr(cc),
+                                  _ptr(co), _ptr(mem), _ptr(tot), _stream(stream))
+        if rc == _native.PROJ_ECAPACITY:
+            cap_members = int(tot.cpu()[3])
+            continue
+        check(rc)
+        break
+    C, M, R, K = (int(v) for v in tot.cpu())
+    return {"sel_index": si[:R], "cand_trial": ct[:R], "cand_key": ck[:R], "cand_cnt": cc[:R],
+            "cand_off": co[:R + 1], "members": mem[:K], "n_candidates": C, "n_members": M,
+            "n_kept": R, "kept_members": K}
 
 
 def trial_hash_allpairs(packed, seq_off, l, k, s, seed, trial_begin, n_trials, cap_cand=None,

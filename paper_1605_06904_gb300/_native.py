@@ -47,6 +47,8 @@ SIGNATURES = {
                     P, P], i32),
     "trial_hash_noalloc": ([P, P, i32, i32, i32, i32, u64, i64, i64, P, P, P, i64, i64, P, P, P,
                             P, P, P, P], i32),
+    "trial_hash_top": ([P, P, i32, i32, i32, i32, u64, i64, i64, i64, P, P, P, P, P, P, P, P],
+                       i32),
     "theta0_build": ([P, P, i32, i32, P, P, i64, f32, P, P], i32),
     "em_refine": ([P, P, i32, i32, P, P, i64, i32, f32, i32, P, P, P, P], i32),
     "em_refine_zoops": ([P, P, i32, i32, P, P, i64, i32, f32, i32, ctypes.c_double, P, P, P,

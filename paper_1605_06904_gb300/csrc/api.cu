@@ -327,6 +327,103 @@ struct SearchHead {
     uint32_t key;
 };
 
+// Steps a2-a5 of a search plus the optional cap on refined buckets: counts
+// every trial (sizing probe), builds the candidate list, and when `top` keeps
+// fewer buckets than were enriched selects them (size descending, ties in
+// (trial, key) order) and gathers their members into a compact list.
+struct HashedSearch {
+    HashState hstate;
+    DevBuf off0, cand, compact;
+    HashOut ho;
+    int64_t C = 0, M = 0, R = 0;
+    std::vector<int64_t> sel;      // kept candidate -> index in the full list (capped only)
+    std::vector<int32_t> sel_cnt;
+    const int64_t *r_off = nullptr;     // CSR of the refined buckets
+    const int32_t *r_members = nullptr;
+    int64_t *sel_dev = nullptr;         // device copy of sel (capped + table-only only)
+};
+
+static int hash_and_select(const uint32_t *packed, const Layout &L, int k, int s, uint64_t seed,
+                           int m, int64_t top, int64_t *totals, const int64_t *bad_dev,
+                           const uint8_t *ascii, HashedSearch &H, cudaStream_t st) {
+    // pass sizes: count first, then size the candidate list exactly
+    HashOut probe;
+    PROJ_TRY(H.off0.alloc(sizeof(int64_t), st));
+    probe.state = &H.hstate;  // the counting pass's partition and offsets, reused by the fill
+    probe.totals = totals;
+    probe.cand_off = H.off0.as<int64_t>();
+    probe.count_only = true;
+    probe.want_emit = top > 0;  // a capped search may build its table from the count
+    PROJ_TRY(run_trial_hash(packed, L, k, s, seed, 0, m, nullptr, probe, st));
+    int64_t tot_h[2], bad_h = -1;
+    PROJ_CUDA_TRY(cudaMemcpyAsync(tot_h, totals, sizeof tot_h, cudaMemcpyDeviceToHost, st));
+    if (bad_dev)
+        PROJ_CUDA_TRY(cudaMemcpyAsync(&bad_h, bad_dev, sizeof bad_h, cudaMemcpyDeviceToHost, st));
+    PROJ_CUDA_TRY(cudaStreamSynchronize(st));
+    if (bad_h >= 0) {
+        set_error("character %d at index %lld is not A/C/G/T", ascii ? (int)ascii[bad_h] : -1,
+                  (long long)bad_h);
+        return PROJ_EBADCHAR;
+    }
+    const int64_t C = tot_h[0], M = tot_h[1];
+    H.C = C;
+    H.M = M;
+
+    // a capped search (top < C) needs the members of its kept buckets only: the
+    // candidate table comes from the counting pass's lists and the kept
+    // buckets' members are gathered afterwards
+    const bool capped = top > 0 && C > top;
+    const bool table_only = capped && H.hstate.emitted;
+    const size_t cand_bytes = (size_t)C * (4 + 4 + 4) + (size_t)(C + 1) * 8 +
+                              (table_only ? 0 : (size_t)M * 4) + 64;
+    PROJ_TRY(H.cand.alloc(cand_bytes, st));
+    HashOut &ho = H.ho;
+    ho.cap_cand = C;
+    ho.cap_members = table_only ? 0 : M;
+    ho.cand_off = H.cand.as<int64_t>();
+    ho.cand_trial = reinterpret_cast<int32_t *>(ho.cand_off + C + 1);
+    ho.cand_key = reinterpret_cast<uint32_t *>(ho.cand_trial + C);
+    ho.cand_cnt = reinterpret_cast<int32_t *>(ho.cand_key + C);
+    ho.members = table_only ? nullptr : ho.cand_cnt + C;
+    ho.totals = totals;
+    ho.state = &H.hstate;
+    ho.table_only = table_only;
+    PROJ_TRY(run_trial_hash(packed, L, k, s, seed, 0, m, nullptr, ho, st));
+
+    H.r_off = ho.cand_off;
+    H.r_members = ho.members;
+    H.R = C;
+    if (capped) {
+        PROJ_TRY(select_top(ho.cand_cnt, C, top, H.sel, H.sel_cnt, st));
+        const int64_t n = (int64_t)H.sel.size();
+        if (table_only) {
+            // [new_off (n+1) | sel (n) | members]
+            std::vector<int64_t> no_h(n + 1, 0);
+            for (int64_t i = 0; i < n; ++i) no_h[i + 1] = no_h[i] + H.sel_cnt[i];
+            PROJ_TRY(H.compact.alloc((size_t)(2 * n + 1) * 8 + (size_t)no_h[n] * 4 + 64, st));
+            int64_t *no = H.compact.as<int64_t>();
+            int64_t *sd = no + n + 1;
+            int32_t *nm = reinterpret_cast<int32_t *>(sd + n);
+            PROJ_CUDA_TRY(cudaMemcpyAsync(no, no_h.data(), (n + 1) * 8, cudaMemcpyHostToDevice, st));
+            PROJ_CUDA_TRY(cudaMemcpyAsync(sd, H.sel.data(), n * 8, cudaMemcpyHostToDevice, st));
+            PROJ_TRY(run_gather_members(packed, L, H.hstate, k, seed, sd, n, ho.cand_trial,
+                                        ho.cand_key, no, nm, st));
+            H.r_off = no;
+            H.r_members = nm;
+            H.sel_dev = sd;
+        } else {
+            int64_t *no = nullptr;
+            int32_t *nm = nullptr;
+            PROJ_TRY(gather_selected(H.sel, H.sel_cnt, ho.cand_off, ho.members, H.compact, &no, &nm,
+                                     st));
+            H.r_off = no;
+            H.r_members = nm;
+        }
+        H.R = n;
+    }
+    return PROJ_OK;
+}
+
 static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int l, int d, int k,
                      int s, int m, uint64_t seed, int em_iters, float pseudocount, int precision,
                      int64_t top, projection_result *out, cudaStream_t st, double gamma = 1.0,
@@ -360,61 +457,15 @@ static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int 
     uint8_t *cons = reinterpret_cast<uint8_t *>(pwm_w + 4 * l);
     PROJ_TRY(launch_background(packed, L.total, bg, st));
 
-    // pass sizes: count first, then size the candidate list exactly
-    HashOut probe;
-    HashState hstate;  // the counting pass's partition and offsets, reused by the fill
-    DevBuf off0;
-    PROJ_TRY(off0.alloc(sizeof(int64_t), st));
-    probe.state = &hstate;
-    probe.totals = totals;
-    probe.cand_off = off0.as<int64_t>();
-    probe.count_only = true;
-    PROJ_TRY(run_trial_hash(packed, L, k, s, seed, 0, m, nullptr, probe, st));
-    int64_t tot_h[2], bad_h = -1;
-    PROJ_CUDA_TRY(cudaMemcpyAsync(tot_h, totals, sizeof tot_h, cudaMemcpyDeviceToHost, st));
-    if (bad_dev)
-        PROJ_CUDA_TRY(cudaMemcpyAsync(&bad_h, bad_dev, sizeof bad_h, cudaMemcpyDeviceToHost, st));
-    PROJ_CUDA_TRY(cudaStreamSynchronize(st));
-    if (bad_h >= 0) {
-        set_error("character %d at index %lld is not A/C/G/T", ascii ? (int)ascii[bad_h] : -1,
-                  (long long)bad_h);
-        return PROJ_EBADCHAR;
-    }
-    const int64_t C = tot_h[0], M = tot_h[1];
+    HashedSearch hsr;
+    PROJ_TRY(hash_and_select(packed, L, k, s, seed, m, top, totals, bad_dev, ascii, hsr, st));
+    const int64_t C = hsr.C, R = hsr.R;
     out->n_candidates = C;
-    out->n_members = M;
-
-    DevBuf cand;
-    const size_t cand_bytes = (size_t)C * (4 + 4 + 4) + (size_t)(C + 1) * 8 + (size_t)M * 4 + 64;
-    PROJ_TRY(cand.alloc(cand_bytes, st));
-    HashOut ho;
-    ho.cap_cand = C;
-    ho.cap_members = M;
-    ho.cand_off = cand.as<int64_t>();
-    ho.cand_trial = reinterpret_cast<int32_t *>(ho.cand_off + C + 1);
-    ho.cand_key = reinterpret_cast<uint32_t *>(ho.cand_trial + C);
-    ho.cand_cnt = reinterpret_cast<int32_t *>(ho.cand_key + C);
-    ho.members = ho.cand_cnt + C;
-    ho.totals = totals;
-    ho.state = &hstate;
-    PROJ_TRY(run_trial_hash(packed, L, k, s, seed, 0, m, nullptr, ho, st));
-
-    // keep only the `top` largest buckets when asked (serving-scale inputs)
-    std::vector<int64_t> sel;
-    std::vector<int32_t> sel_cnt;
-    const int64_t *r_off = ho.cand_off;
-    const int32_t *r_members = ho.members;
-    int64_t R = C;
-    DevBuf compact;
-    if (top > 0 && C > top) {
-        PROJ_TRY(select_top(ho.cand_cnt, C, top, sel, sel_cnt, st));
-        int64_t *no = nullptr;
-        int32_t *nm = nullptr;
-        PROJ_TRY(gather_selected(sel, sel_cnt, ho.cand_off, ho.members, compact, &no, &nm, st));
-        r_off = no;
-        r_members = nm;
-        R = (int64_t)sel.size();
-    }
+    out->n_members = hsr.M;
+    const int64_t *r_off = hsr.r_off;
+    const int32_t *r_members = hsr.r_members;
+    const std::vector<int64_t> &sel = hsr.sel;
+    HashOut &ho = hsr.ho;
     out->n_refined = R;
 
     DevBuf model;
@@ -469,6 +520,84 @@ static int find_impl(const uint32_t *packed, const int64_t *seq_off, int t, int 
     return PROJ_OK;
 }
 
+
+// Kept buckets' (trial, key, size) in selection order.
+__global__ void sel_table_kernel(const int64_t *__restrict__ sel, int64_t n,
+                                 const int32_t *__restrict__ cand_trial,
+                                 const uint32_t *__restrict__ cand_key,
+                                 const int32_t *__restrict__ cand_cnt, int64_t *__restrict__ o_idx,
+                                 int32_t *__restrict__ o_trial, uint32_t *__restrict__ o_key,
+                                 int32_t *__restrict__ o_cnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t c = sel[i];
+    o_idx[i] = c;
+    o_trial[i] = cand_trial[c];
+    o_key[i] = cand_key[c];
+    o_cnt[i] = cand_cnt[c];
+}
+
+int trial_hash_top(const uint32_t *packed_dev, const int64_t *seq_off, int t, int l, int k, int s,
+                   uint64_t seed, int64_t n_trials, int64_t top, int64_t cap_members,
+                   int64_t *sel_index_dev, int32_t *cand_trial_dev, uint32_t *cand_key_dev,
+                   int32_t *cand_cnt_dev, int64_t *cand_off_dev, int32_t *members_dev,
+                   int64_t *totals_dev, void *stream) {
+    clear_error();
+    cudaStream_t st = (cudaStream_t)stream;
+    PROJ_REQUIRE(packed_dev != nullptr && totals_dev != nullptr, "NULL buffer");
+    PROJ_REQUIRE(top >= 1, "need top >= 1");
+    PROJ_REQUIRE(n_trials >= 1 && n_trials <= (1 << 24), "need 1 <= n_trials <= 2^24");
+    PROJ_REQUIRE(sel_index_dev && cand_trial_dev && cand_key_dev && cand_cnt_dev && cand_off_dev,
+                 "NULL candidate buffer");
+    PROJ_REQUIRE(cap_members >= 0 && (cap_members == 0 || members_dev), "bad member buffer");
+    Layout L;
+    PROJ_TRY(make_layout(seq_off, t, l, st, L));
+    DevBuf tb;
+    PROJ_TRY(tb.alloc(2 * sizeof(int64_t), st));
+    HashedSearch H;
+    PROJ_TRY(hash_and_select(packed_dev, L, k, s, seed, (int)n_trials, top, tb.as<int64_t>(),
+                             nullptr, nullptr, H, st));
+    if (H.sel.empty() && H.C > 0) {
+        // every enriched bucket is kept: put them in the same size order
+        PROJ_TRY(select_top(H.ho.cand_cnt, H.C, H.C, H.sel, H.sel_cnt, st));
+        int64_t *no = nullptr;
+        int32_t *nm = nullptr;
+        PROJ_TRY(gather_selected(H.sel, H.sel_cnt, H.ho.cand_off, H.ho.members, H.compact, &no,
+                                 &nm, st));
+        H.r_off = no;
+        H.r_members = nm;
+    }
+    const int64_t R = (int64_t)H.sel.size();
+    int64_t kept = 0;
+    for (int32_t c : H.sel_cnt) kept += c;
+    const int64_t tot[4] = {H.C, H.M, R, kept};
+    PROJ_CUDA_TRY(cudaMemcpyAsync(totals_dev, tot, sizeof tot, cudaMemcpyHostToDevice, st));
+    if (kept > cap_members) {
+        PROJ_CUDA_TRY(cudaStreamSynchronize(st));
+        set_error("the kept buckets hold %lld members, above cap_members = %lld", (long long)kept,
+                  (long long)cap_members);
+        return PROJ_ECAPACITY;
+    }
+    if (R > 0) {
+        DevBuf sd;
+        PROJ_TRY(sd.alloc((size_t)R * 8, st));
+        PROJ_CUDA_TRY(cudaMemcpyAsync(sd.as<int64_t>(), H.sel.data(), R * 8, cudaMemcpyHostToDevice,
+                                      st));
+        sel_table_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(
+            sd.as<int64_t>(), R, H.ho.cand_trial, H.ho.cand_key, H.ho.cand_cnt, sel_index_dev,
+            cand_trial_dev, cand_key_dev, cand_cnt_dev);
+        PROJ_LAUNCH_CHECK("sel_table_kernel");
+        PROJ_CUDA_TRY(cudaMemcpyAsync(cand_off_dev, H.r_off, (R + 1) * 8, cudaMemcpyDeviceToDevice,
+                                      st));
+        if (kept > 0)
+            PROJ_CUDA_TRY(cudaMemcpyAsync(members_dev, H.r_members, kept * 4,
+                                          cudaMemcpyDeviceToDevice, st));
+    } else {
+        PROJ_CUDA_TRY(cudaMemsetAsync(cand_off_dev, 0, sizeof(int64_t), st));
+    }
+    PROJ_CUDA_TRY(cudaStreamSynchronize(st));
+    return PROJ_OK;
+}
 
 static void result_init(projection_result *out) {
     memset(out, 0, sizeof *out);

@@ -101,7 +101,15 @@ int launch_positions(uint64_t seed, int64_t trial_begin, int64_t n_trials, int l
 // partition, the per-unit counts and their offsets are not computed twice.
 struct HashState {
     DevBuf meta, part_buf;
+    DevBuf emit_buf;     // the counting pass's per-unit enriched (key, size) lists
     bool valid = false;
+    bool emitted = false;  // emit_buf holds the lists (counting call had want_emit)
+    // what the member gather of selected buckets needs from the counting call
+    int parts = 1, hb = 0, n_chunks = 0;
+    bool partitioned = false;
+    const uint16_t *prel = nullptr;    // partitioned mode: keys grouped by part per chunk
+    const uint16_t *plid = nullptr;    //                   chunk-local l-mer ids
+    const int32_t *pstart = nullptr;   //                   part starts per (trial, chunk)
 };
 
 struct HashOut {
@@ -116,12 +124,23 @@ struct HashOut {
     int32_t *members = nullptr;
     int64_t *totals = nullptr;      // device int64[2]
     bool count_only = false;        // stop after the totals (sizing probe)
+    bool want_emit = false;         // counting call: also keep each unit's enriched lists
+    bool table_only = false;        // filling call: candidate table from those lists, no
+                                    // members (the caller gathers the ones it keeps)
 };
 
 // Both passes of the bucket kernels plus the scan between them.
 int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64_t seed,
                    int64_t trial_begin, int64_t n_trials, const int32_t *positions_in,
                    const HashOut &out, cudaStream_t st);
+
+// Members (ascending l-mer ids) of n selected candidates of a search whose
+// counting call kept its state: candidate sel[i] = (cand_trial, cand_key) of
+// the full list; its members go to new_members[new_off[i] .. new_off[i+1]).
+int run_gather_members(const uint32_t *packed, const Layout &L, const HashState &hs, int k,
+                       uint64_t seed, const int64_t *sel, int64_t n, const int32_t *cand_trial,
+                       const uint32_t *cand_key, const int64_t *new_off, int32_t *new_members,
+                       cudaStream_t st);
 
 // ---- batched motif searches ------------------------------------------------
 // One instance of a batched hash: its packed words start at `packed`

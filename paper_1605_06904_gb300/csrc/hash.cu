@@ -33,6 +33,8 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kHistBytes = 128 * 1024;    // shared-memory histogram budget
 constexpr int kSmemLimit = 226 * 1024;    // dynamic shared memory per CTA (227 KB opt-in
                                           // minus room for the static arrays)
+constexpr int kSortChunk = 8192;          // l-mers per (trial, chunk) of the partition
+constexpr int kMaxSortChunks = 8192;      // chunks per trial in partitioned mode
 
 struct HashParams {
     const uint32_t *packed;
@@ -62,29 +64,44 @@ struct HashParams {
     int32_t *members;
     uint32_t *scratch_key;    // [cap_members]
     int32_t *scratch_gid;     // [cap_members]
-    // partitioned mode (large inputs split into many key-range parts): the
-    // (key - part * hb, l-mer id) pairs of (trial, part) are
-    // pairs[seg_off[(trial*parts + part)*n_chunks] .. seg_off[(trial*parts + part + 1)*n_chunks]),
-    // in l-mer id order
-    const uint2 *pairs;
-    const int64_t *seg_off;
+    // partitioned mode (large inputs split into many key-range parts; always u32
+    // counters, so key - part * hb < 32768 fits 16 bits): the l-mers of chunk c
+    // (ids c*kSortChunk ..) of a trial sit in region (trial*n_chunks + c)*kSortChunk
+    // of prel (key - part * hb) and plid (id - c*kSortChunk), grouped by part in
+    // l-mer order; part p occupies [pstart[q*(parts+1) + p], pstart[q*(parts+1) + p+1])
+    // of region q.  A unit (trial, part) walks its pieces chunk by chunk, i.e. in
+    // l-mer order (two 16-bit arrays: the counting pass reads 2 bytes per l-mer).
+    int partitioned;
+    const uint16_t *prel;
+    const uint16_t *plid;
+    const int32_t *pstart;
     int n_chunks;
+    // counting pass: each unit's enriched buckets as (key - part * hb, size), in
+    // key order, at emit[emit_off[unit] ..] (capacity: every enriched bucket
+    // holds >= s of the unit's l-mers)
+    uint2 *emit;
+    const int64_t *emit_off;
 };
 
 struct SmemLayout {
-    int hist_bytes, bitmap_bytes, off_bytes, words_bytes, total;
+    int hist_bytes, bitmap_bytes, cb_bytes, off_bytes, words_bytes, total;
 };
 
+// histogram | enriched bitmap (fill) | partitioned: the unit's chunk walk
+// (int32 prefix [n_chunks+1], int64 bases [n_chunks]) | else: sequence and
+// l-mer offsets, staged packed words
 __host__ __device__ inline SmemLayout smem_layout(const HashParams &P, bool fill) {
     SmemLayout S;
     S.hist_bytes = (P.hist16 ? 2 : 4) * P.hb;
     S.hist_bytes = (S.hist_bytes + 15) & ~15;
     S.bitmap_bytes = fill ? (((P.hb + 31) / 32) * 4 + 15) & ~15 : 0;
-    S.off_bytes = ((2 * (P.t + 1) * 4) + 15) & ~15;
+    S.cb_bytes = P.partitioned ? (((P.n_chunks + 1) * 4 + 15) & ~15) + P.n_chunks * 8 : 0;
+    S.off_bytes = P.partitioned ? 0 : ((2 * (P.t + 1) * 4) + 15) & ~15;
     S.words_bytes = P.stage_words ? ((P.stage_words + 2) * 4 + 15) & ~15 : 0;
-    S.total = S.hist_bytes + S.bitmap_bytes + S.off_bytes + S.words_bytes;
+    S.total = S.hist_bytes + S.bitmap_bytes + S.cb_bytes + S.off_bytes + S.words_bytes;
     return S;
 }
+
 
 __device__ __forceinline__ uint32_t lmer_key(uint64_t win, const int *pos, int k) {
     uint32_t key = 0u;
@@ -138,6 +155,28 @@ __device__ inline void block_scan2(int a, int b, int &pa, int &pb, int &ta, int 
     __syncthreads();
 }
 
+// Partitioned mode: the pieces of unit (trial, part) in chunk order.  Piece c
+// holds the unit's flat entries [cb[c], cb[c+1]), entry f of it at
+// prel/plid[pb[c] + f].  Ends with a CTA barrier.
+__device__ inline void unit_walk_setup(const HashParams &P, int trial_local, int part,
+                                       int32_t *cb, long long *pb, int2 *s_warp) {
+    const int per = (P.n_chunks + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int c0 = min((int)threadIdx.x * per, P.n_chunks), c1 = min(c0 + per, P.n_chunks);
+    const int32_t *ps = P.pstart + (int64_t)trial_local * P.n_chunks * (P.parts + 1);
+    int sum = 0;
+    for (int c = c0; c < c1; ++c) sum += ps[c * (P.parts + 1) + part + 1] - ps[c * (P.parts + 1) + part];
+    int pre, pz, tot, tz;
+    block_scan2(sum, 0, pre, pz, tot, tz, s_warp);
+    for (int c = c0; c < c1; ++c) {
+        const int a = ps[c * (P.parts + 1) + part];
+        cb[c] = pre;
+        pb[c] = ((long long)trial_local * P.n_chunks + c) * kSortChunk + a - pre;
+        pre += ps[c * (P.parts + 1) + part + 1] - a;
+    }
+    if (threadIdx.x == 0) cb[P.n_chunks] = tot;
+    __syncthreads();
+}
+
 // One (trial, key-range part) unit of the bucket kernels; `unit` indexes the
 // per-unit arrays of P (part_nb, part_nm, cand_base, mem_base).
 template <bool FILL, int K>
@@ -148,10 +187,13 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     uint32_t *hist32 = reinterpret_cast<uint32_t *>(smem);
     uint16_t *hist16 = reinterpret_cast<uint16_t *>(smem);
     uint32_t *bitmap = reinterpret_cast<uint32_t *>(smem + S.hist_bytes);
-    int32_t *s_seq = reinterpret_cast<int32_t *>(smem + S.hist_bytes + S.bitmap_bytes);
+    int32_t *s_cb = reinterpret_cast<int32_t *>(smem + S.hist_bytes + S.bitmap_bytes);
+    long long *s_pb = reinterpret_cast<long long *>(
+        smem + S.hist_bytes + S.bitmap_bytes + (((P.n_chunks + 1) * 4 + 15) & ~15));
+    int32_t *s_seq = reinterpret_cast<int32_t *>(smem + S.hist_bytes + S.bitmap_bytes + S.cb_bytes);
     int32_t *s_lmer = s_seq + (P.t + 1);
-    uint32_t *s_words =
-        reinterpret_cast<uint32_t *>(smem + S.hist_bytes + S.bitmap_bytes + S.off_bytes);
+    uint32_t *s_words = reinterpret_cast<uint32_t *>(smem + S.hist_bytes + S.bitmap_bytes +
+                                                     S.cb_bytes + S.off_bytes);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int trial_local = unit / P.parts;
@@ -170,10 +212,11 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
         if (!FILL && P.pos_out && part == 0)
             for (int q = 0; q < P.k; ++q) P.pos_out[(int64_t)trial_local * P.k + q] = (uint8_t)s_pos[q];
     }
-    for (int i = tid; i <= P.t; i += kThreads) {
-        s_seq[i] = P.seq_off[i];
-        s_lmer[i] = P.lmer_off[i];
-    }
+    if (!P.partitioned)
+        for (int i = tid; i <= P.t; i += kThreads) {
+            s_seq[i] = P.seq_off[i];
+            s_lmer[i] = P.lmer_off[i];
+        }
     const uint32_t *words = P.packed;
     int64_t nwords = P.nwords;
     if (P.stage_words) {
@@ -195,20 +238,32 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     if (FILL)
         for (int w = tid; w < S.bitmap_bytes / 4; w += kThreads) bitmap[w] = 0u;
     __syncthreads();
+    if (P.partitioned) unit_walk_setup(P, trial_local, part, s_cb, s_pb, s_warp);
 
     int pos[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) pos[q] = q < P.k ? s_pos[q] : 0;
 
     // Algorithm 2 steps 2b-2c: project every l-mer and count its bucket.
-    int64_t seg_b = 0, seg_e = 0;
-    if (P.pairs) {
-        seg_b = P.seg_off[((int64_t)trial_local * P.parts + part) * P.n_chunks];
-        seg_e = P.seg_off[((int64_t)trial_local * P.parts + part + 1) * P.n_chunks];
-        for (int64_t e = seg_b + tid; e < seg_e; e += kThreads) {
-            const uint32_t rel = P.pairs[e].x;
-            if (P.hist16) atomicAdd(&hist32[rel >> 1], 1u << (16 * (rel & 1u)));
-            else atomicAdd(&hist32[rel], 1u);
+    const int n_flat = P.partitioned ? s_cb[P.n_chunks] : 0;  // the unit's l-mers
+    if (P.partitioned) {
+        // eight loads in flight per thread ahead of their increments (the
+        // pieces stream from HBM); u32 counters in this mode
+        int c = 0;  // piece of this thread's current entry (entries only grow)
+        for (int f0 = tid; f0 < n_flat; f0 += 8 * kThreads) {
+            uint32_t r[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int f = f0 + q * kThreads;
+                r[q] = 0xFFFFFFFFu;
+                if (f < n_flat) {
+                    while (s_cb[c + 1] <= f) ++c;
+                    r[q] = __ldg(P.prel + s_pb[c] + f);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (r[q] != 0xFFFFFFFFu) atomicAdd(&hist32[r[q]], 1u);
         }
     } else {
         int i = 0;
@@ -230,17 +285,39 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     }
 
     // Algorithm 2 step 3: enriched buckets (count >= s) of this key range.
-    const int chunk = (P.hb + kThreads - 1) / kThreads;
-    const int b_begin = min(tid * chunk, P.hb), b_end = min(b_begin + chunk, P.hb);
+    // Warp w takes buckets [w*span, (w+1)*span) in rows of 32 consecutive
+    // buckets, lane i reading bucket row + i (consecutive words: no bank
+    // conflicts); a row's ballot and lane scan keep key order.
+    const int span = (((P.hb + kWarps - 1) / kWarps) + 31) & ~31;
+    const int wb = min(warp * span, P.hb), we = min(wb + span, P.hb);
     int nb = 0, nm = 0;
-    for (int b = b_begin; b < b_end; ++b) {
-        const int c = P.hist16 ? hist16[b] : (int)hist32[b];
+    for (int r = wb; r < we; r += 32) {
+        const int b = r + lane;
+        const int c = b < we ? (P.hist16 ? (int)hist16[b] : (int)hist32[b]) : 0;
         if (c >= P.s) { ++nb; nm += c; }
     }
-    int rb, rm, NB, NM;
-    block_scan2(nb, nm, rb, rm, NB, NM, s_warp);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nb += __shfl_xor_sync(0xffffffffu, nb, o);
+        nm += __shfl_xor_sync(0xffffffffu, nm, o);
+    }
+    int rb, rm, NB, NM;  // this warp's first enriched bucket and member offset; unit totals
+    block_scan2(lane == 0 ? nb : 0, lane == 0 ? nm : 0, rb, rm, NB, NM, s_warp);
+    rb = __shfl_sync(0xffffffffu, rb, 0);
+    rm = __shfl_sync(0xffffffffu, rm, 0);
 
     if (!FILL) {
+        if (P.emit) {  // this unit's enriched buckets, in key order
+            uint2 *dst = P.emit + P.emit_off[unit];
+            for (int r = wb; r < we; r += 32) {
+                const int b = r + lane;
+                const int c = b < we ? (P.hist16 ? (int)hist16[b] : (int)hist32[b]) : 0;
+                const bool e = c >= P.s;
+                const uint32_t bal = __ballot_sync(0xffffffffu, e);
+                if (e) dst[rb + __popc(bal & ((1u << lane) - 1u))] = make_uint2((uint32_t)b, (uint32_t)c);
+                rb += __popc(bal);
+            }
+        }
         if (tid == 0) {
             P.part_nb[unit] = NB;
             P.part_nm[unit] = NM;
@@ -251,39 +328,49 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     // pass 2: candidate table in key order, bucket cursors, enriched bitmap
     const int64_t cbase = P.cand_base[unit];
     const int64_t mbase = P.mem_base[unit];
-    for (int b = b_begin; b < b_end; ++b) {
-        const int c = P.hist16 ? hist16[b] : (int)hist32[b];
-        if (c >= P.s) {
-            const int64_t ci = cbase + rb;
+    for (int r = wb; r < we; r += 32) {
+        const int b = r + lane;
+        const int c = b < we ? (P.hist16 ? (int)hist16[b] : (int)hist32[b]) : 0;
+        const bool e = c >= P.s;
+        const uint32_t bal = __ballot_sync(0xffffffffu, e);
+        int v = e ? c : 0;  // inclusive lane scan of the enriched sizes of this row
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (e) {
+            const int64_t ci = cbase + rb + __popc(bal & ((1u << lane) - 1u));
+            const int mo = rm + v - c;
             if (ci < P.cap_cand) {
                 P.cand_trial[ci] = (int32_t)trial;
                 P.cand_key[ci] = lo_key + (uint32_t)b;
                 P.cand_cnt[ci] = c;
-                P.cand_off[ci] = mbase + rm;
+                P.cand_off[ci] = mbase + mo;
             }
-            if (P.hist16) hist16[b] = (uint16_t)rm; else hist32[b] = (uint32_t)rm;
-            atomicOr(&bitmap[b >> 5], 1u << (b & 31));
-            ++rb;
-            rm += c;
+            if (P.hist16) hist16[b] = (uint16_t)mo; else hist32[b] = (uint32_t)mo;
         }
+        if (lane == 0) bitmap[b >> 5] = bal;  // rows are 32-aligned: one bitmap word each
+        rb += __popc(bal);
+        rm += __shfl_sync(0xffffffffu, v, 31);
     }
     __syncthreads();
     if (mbase + NM > P.cap_members || NM == 0) return;  // block-uniform
 
     // enriched l-mers in id order -> scratch[mbase .. mbase+NM)
     {
-        int i = 0, running = 0;
-        const int64_t n_iter = P.pairs ? seg_e - seg_b : (int64_t)P.x;
+        int i = 0, running = 0, c = 0;
+        const int64_t n_iter = P.partitioned ? (int64_t)n_flat : (int64_t)P.x;
         for (int64_t base = 0; base < n_iter; base += kThreads) {
             const int64_t it = base + tid;
             bool e = false;
             uint32_t rel = 0u;
             int gid = 0;
             if (it < n_iter) {
-                if (P.pairs) {
-                    const uint2 pr = P.pairs[seg_b + it];
-                    rel = pr.x;
-                    gid = (int)pr.y;
+                if (P.partitioned) {
+                    while (s_cb[c + 1] <= it) ++c;
+                    rel = P.prel[s_pb[c] + it];
+                    gid = c * kSortChunk + (int)P.plid[s_pb[c] + it];
                 } else {
                     gid = (int)it;
                     while (s_lmer[i + 1] <= gid) ++i;
@@ -390,16 +477,22 @@ __global__ void __launch_bounds__(kThreads, 1) hash_batch_kernel(const HashParam
 // ---------------------------------------------------------------------------
 // Partitioned mode for large inputs: when 4^k counters need several key-range
 // parts and x is large, every part's CTA would otherwise rebuild all x keys.
-// Instead the keys are built twice per trial in total: (1) each (trial, chunk)
-// counts its l-mers per part, (2) a scan lays the parts out contiguously
-// (chunks in order inside each part), (3) a stable scatter writes
-// (key - part * hb, l-mer id) pairs, so each part's segment is in l-mer id
-// order and the bucket kernels read only their own segment.
+// Instead each (trial, chunk of kSortChunk l-mers) builds its keys once,
+// groups them by part inside the CTA (stable, so each group is in l-mer
+// order) and writes the groups with a table of where each part starts; the
+// bucket kernels of unit (trial, part) then read only their part's piece of
+// every chunk.  No step depends on another CTA.
 // ---------------------------------------------------------------------------
-constexpr int kPartThreads = 256;
-constexpr int kPartWarps = kPartThreads / 32;
-constexpr int kChunk = 32768;  // l-mers per (trial, chunk)
 constexpr int kMaxParts = 32;
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;  // one warp per 1024 l-mers of a chunk
+static_assert(kSortWarps * 1024 == kSortChunk, "chunk = warps x 1024 l-mers");
+// a chunk's packed words and sequence offsets are staged in shared memory
+// when they fit (kSortChunk l-mers of length <= 32 always span fewer than
+// 2^18 bases, but long runs of short sequences can exceed these)
+constexpr int kStageWords = 4096;
+constexpr int kStageSeqs = (kSortChunk - kStageWords - 2) / 2 - 1;
+constexpr int kSortSmem = 2 * kSortChunk * 4;
 
 __device__ __forceinline__ void part_setup(const HashParams &P, int trial_local, int *s_pos) {
     if (threadIdx.x == 0) {
@@ -422,28 +515,144 @@ __device__ __forceinline__ int seq_of(const int32_t *lmer_off, int t, int g) {
     return lo;
 }
 
+// The active lanes of this warp whose part equals this lane's (five ballots
+// over the bits of a part index below 32).
+__device__ __forceinline__ unsigned same_part(uint32_t part, bool act) {
+    unsigned eq = __ballot_sync(0xffffffffu, act);
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+        const bool bit = (part >> b) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, act && bit);
+        eq &= bit ? bal : ~bal;
+    }
+    return eq;
+}
+
 template <int K>
-__global__ void __launch_bounds__(kPartThreads) part_count_kernel(const HashParams P,
-                                                                  int64_t *__restrict__ counts) {
+__global__ void __launch_bounds__(kSortThreads) part_sort_kernel(const HashParams P,
+                                                                 uint16_t *__restrict__ orel,
+                                                                 uint16_t *__restrict__ olid,
+                                                                 int32_t *__restrict__ pstart) {
+    // dynamic shared memory: keys [kSortChunk] | grouped output [kSortChunk]; the
+    // output area first holds the chunk's packed words and sequence offsets
+    extern __shared__ __align__(16) uint32_t s_dyn[];
+    uint32_t *s_key = s_dyn;
+    uint32_t *s_out = s_dyn + kSortChunk;
+    uint32_t *s_words = s_out;                                       // [kStageWords + 2]
+    int32_t *s_soff = reinterpret_cast<int32_t *>(s_out + kStageWords + 2);  // [kStageSeqs + 1]
+    int32_t *s_loff = s_soff + kStageSeqs + 1;
     __shared__ int s_pos[16];
-    __shared__ unsigned s_cnt[kMaxParts];
+    __shared__ int s_cnt[kSortWarps][kMaxParts];  // per warp: sizes, then output offsets
+    __shared__ int s_tot[kMaxParts + 1];
+    __shared__ int s_rng[4];                       // first / last sequence, first word, staged
     const int trial_local = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
-    if (tid < kMaxParts) s_cnt[tid] = 0u;
-    part_setup(P, trial_local, s_pos);
+    const int lane = tid & 31, warp = tid >> 5;
+    const int g0 = chunk * kSortChunk;
+    const int n = min(kSortChunk, P.x - g0);
+    for (int q = tid; q < kSortWarps * kMaxParts; q += kSortThreads) (&s_cnt[0][0])[q] = 0;
+    if (tid == 32) {  // the chunk's sequences and packed words
+        const int i0 = seq_of(P.lmer_off, P.t, g0), i1 = seq_of(P.lmer_off, P.t, g0 + n - 1);
+        const int64_t b_lo = (int64_t)P.seq_off[i0] + (g0 - P.lmer_off[i0]);
+        const int64_t b_hi = (int64_t)P.seq_off[i1] + (g0 + n - 1 - P.lmer_off[i1]) + P.l;
+        const int64_t w_lo = b_lo >> 4, w_hi = (b_hi + 15) >> 4;
+        s_rng[0] = i0;
+        s_rng[1] = i1;
+        s_rng[2] = (int)w_lo;
+        s_rng[3] = (w_hi - w_lo <= kStageWords && i1 - i0 + 2 <= kStageSeqs) ? (int)(w_hi - w_lo) : -1;
+    }
+    part_setup(P, trial_local, s_pos);  // ends with a barrier
+    const int i0 = s_rng[0], i1 = s_rng[1], w_lo = s_rng[2], nw = s_rng[3];
+    const bool staged = nw >= 0;
+    if (staged) {
+        for (int w = tid; w < nw + 2; w += kSortThreads)
+            s_words[w] = w_lo + w < P.nwords ? __ldg(P.packed + w_lo + w) : 0u;
+        for (int q = tid; q <= i1 - i0 + 1; q += kSortThreads) {
+            s_soff[q] = P.seq_off[i0 + q];
+            s_loff[q] = P.lmer_off[i0 + q];
+        }
+    }
+    __syncthreads();
     int pos[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) pos[q] = q < P.k ? s_pos[q] : 0;
-    const int g0 = chunk * kChunk, g1 = min(P.x, g0 + kChunk);
-    int i = g0 + tid < g1 ? seq_of(P.lmer_off, P.t, g0 + tid) : 0;
-    for (int g = g0 + tid; g < g1; g += kPartThreads) {
-        while (__ldg(P.lmer_off + i + 1) <= g) ++i;
-        const int64_t b0 = (int64_t)__ldg(P.seq_off + i) + (g - __ldg(P.lmer_off + i));
-        const uint32_t key = lmer_key_k<K>(window64(P.packed, P.nwords, b0), pos, P.k);
-        atomicAdd(&s_cnt[key / (uint32_t)P.hb], 1u);
+    const uint32_t hb = (uint32_t)P.hb;
+    const int j0 = warp * 1024;  // this warp's l-mers of the chunk, in rounds of 32
+    const unsigned below = (1u << lane) - 1u;
+
+    // keys into shared memory; sizes of the parts per warp
+    int i = 0;  // sequence of this lane's l-mer, relative to i0
+    for (int r = 0; r < 32; ++r) {
+        const int j = j0 + 32 * r + lane;
+        const bool act = j < n;
+        uint32_t part = 0u;
+        if (act) {
+            const int g = g0 + j;
+            uint32_t key;
+            if (staged) {
+                while (s_loff[i + 1] <= g) ++i;
+                const int64_t b0 = (int64_t)s_soff[i] + (g - s_loff[i]) - 16 * (int64_t)w_lo;
+                key = lmer_key_k<K>(window64(s_words, nw + 2, b0), pos, P.k);
+            } else {
+                while (__ldg(P.lmer_off + i0 + i + 1) <= g) ++i;
+                const int64_t b0 = (int64_t)__ldg(P.seq_off + i0 + i) + (g - __ldg(P.lmer_off + i0 + i));
+                key = lmer_key_k<K>(window64(P.packed, P.nwords, b0), pos, P.k);
+            }
+            s_key[j] = key;
+            part = key / hb;
+        }
+        const unsigned eq = same_part(part, act);
+        if (act && (eq & below) == 0u) s_cnt[warp][part] += __popc(eq);
+        __syncwarp();
     }
     __syncthreads();
-    if (tid < P.parts)
-        counts[((int64_t)trial_local * P.parts + tid) * P.n_chunks + chunk] = s_cnt[tid];
+    // part p starts at s_tot[p] in the chunk; warp w's entries of part p follow
+    // those of warps w' < w
+    if (tid < kMaxParts) {
+        int a = 0;
+        for (int w = 0; w < kSortWarps; ++w) {
+            const int v = s_cnt[w][tid];
+            s_cnt[w][tid] = a;
+            a += v;
+        }
+        s_tot[tid] = a;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int v = s_tot[lane];
+        int sc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, sc, o);
+            if (lane >= o) sc += u;
+        }
+        s_tot[lane] = sc - v;
+        if (lane == 31) s_tot[kMaxParts] = sc;
+    }
+    __syncthreads();
+    if (tid <= P.parts)
+        pstart[((int64_t)trial_local * P.n_chunks + chunk) * (P.parts + 1) + tid] = s_tot[tid];
+
+    // stable placement into shared memory: round r of warp w after rounds < r
+    // of w and all of w' < w; entry = (key - part * hb) | chunk-local id << 16
+    for (int r = 0; r < 32; ++r) {
+        const int j = j0 + 32 * r + lane;
+        const bool act = j < n;
+        const uint32_t key = act ? s_key[j] : 0u;
+        const uint32_t part = key / hb;
+        const unsigned eq = same_part(part, act);
+        if (act) s_out[s_tot[part] + s_cnt[warp][part] + __popc(eq & below)] =
+            (key - part * hb) | ((uint32_t)j << 16);
+        __syncwarp();
+        if (act && (eq & below) == 0u) s_cnt[warp][part] += __popc(eq);
+        __syncwarp();
+    }
+    __syncthreads();
+    const int64_t region = ((int64_t)trial_local * P.n_chunks + chunk) * kSortChunk;
+    for (int e = tid; e < n; e += kSortThreads) {
+        const uint32_t v = s_out[e];
+        orel[region + e] = (uint16_t)(v & 0xFFFFu);
+        olid[region + e] = (uint16_t)(v >> 16);
+    }
 }
 
 // exclusive scan of n int64 values in one CTA, out[n] = total
@@ -469,60 +678,6 @@ __global__ void __launch_bounds__(1024) scan_i64_kernel(const int64_t *__restric
         p += in[e];
     }
     if (tid == 1023) out[n] = s[1023];
-}
-
-template <int K>
-__global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const HashParams P,
-                                                                    const int64_t *__restrict__ offs,
-                                                                    uint2 *__restrict__ pairs) {
-    __shared__ int s_pos[16];
-    __shared__ long long s_base[kMaxParts];
-    __shared__ int s_w[kPartWarps][kMaxParts];
-    const int trial_local = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    if (tid < kMaxParts)
-        s_base[tid] = tid < P.parts ? offs[((int64_t)trial_local * P.parts + tid) * P.n_chunks + chunk] : 0;
-    part_setup(P, trial_local, s_pos);
-    int pos[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) pos[q] = q < P.k ? s_pos[q] : 0;
-    const int g0 = chunk * kChunk, g1 = min(P.x, g0 + kChunk);
-    int i = g0 + tid < g1 ? seq_of(P.lmer_off, P.t, g0 + tid) : 0;  // advanced as g grows
-    for (int r0 = g0; r0 < g1; r0 += kPartThreads) {
-        for (int q = tid; q < kPartWarps * kMaxParts; q += kPartThreads) (&s_w[0][0])[q] = 0;
-        __syncthreads();
-        const int g = r0 + tid;
-        const bool ok = g < g1;
-        uint32_t key = 0u, part = 0u;
-        if (ok) {
-            while (__ldg(P.lmer_off + i + 1) <= g) ++i;
-            const int64_t b0 = (int64_t)__ldg(P.seq_off + i) + (g - __ldg(P.lmer_off + i));
-            key = lmer_key_k<K>(window64(P.packed, P.nwords, b0), pos, P.k);
-            part = key / (uint32_t)P.hb;
-        }
-        const unsigned act = __ballot_sync(0xffffffffu, ok);
-        unsigned grp = 0u;
-        int rank = 0;
-        if (ok) {
-            grp = __match_any_sync(act, part);
-            rank = __popc(grp & ((1u << lane) - 1u));
-            if (rank == 0) s_w[warp][part] = __popc(grp);
-        }
-        __syncthreads();
-        if (ok) {
-            int before = 0;
-            for (int w = 0; w < warp; ++w) before += s_w[w][part];
-            const long long at = s_base[part] + before + rank;
-            pairs[at] = make_uint2(key - part * (uint32_t)P.hb, (uint32_t)g);
-        }
-        __syncthreads();
-        if (tid < P.parts) {
-            int add = 0;
-            for (int w = 0; w < kPartWarps; ++w) add += s_w[w][tid];
-            s_base[tid] += add;
-        }
-        __syncthreads();
-    }
 }
 
 // Exclusive scan over the (trial, part) counts in launch order, which is
@@ -597,32 +752,150 @@ int launch_hash(const HashParams &P, unsigned grid, int smem, cudaStream_t st) {
 }
 
 template <int K>
-int launch_partition_k(const HashParams &P, dim3 grid, int64_t *cnt, int64_t *seg, uint2 *pairs,
-                       int64_t n_cnt, cudaStream_t st) {
+int launch_partition_k(const HashParams &P, dim3 grid, uint16_t *orel, uint16_t *olid,
+                       int32_t *pstart, cudaStream_t st) {
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(part_sort_kernel<K>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmem));
     {
         TraceSpan ts_("hash_partition", st);
-        part_count_kernel<K><<<grid, kPartThreads, 0, st>>>(P, cnt);
+        part_sort_kernel<K><<<grid, kSortThreads, kSortSmem, st>>>(P, orel, olid, pstart);
     }
-    PROJ_LAUNCH_CHECK("part_count_kernel");
-    {
-        TraceSpan ts_("hash_partition", st);
-        scan_i64_kernel<<<1, 1024, 0, st>>>(cnt, n_cnt, seg);
-    }
-    PROJ_LAUNCH_CHECK("scan_i64_kernel");
-    {
-        TraceSpan ts_("hash_partition", st);
-        part_scatter_kernel<K><<<grid, kPartThreads, 0, st>>>(P, seg, pairs);
-    }
-    PROJ_LAUNCH_CHECK("part_scatter_kernel");
+    PROJ_LAUNCH_CHECK("part_sort_kernel");
     return PROJ_OK;
 }
 
-int launch_partition(const HashParams &P, dim3 grid, int64_t *cnt, int64_t *seg, uint2 *pairs,
-                     int64_t n_cnt, cudaStream_t st) {
+int launch_partition(const HashParams &P, dim3 grid, uint16_t *orel, uint16_t *olid,
+                     int32_t *pstart, cudaStream_t st) {
     switch (P.k) {
-        case 9: return launch_partition_k<9>(P, grid, cnt, seg, pairs, n_cnt, st);
-        case 10: return launch_partition_k<10>(P, grid, cnt, seg, pairs, n_cnt, st);
-        default: return launch_partition_k<0>(P, grid, cnt, seg, pairs, n_cnt, st);
+        case 9: return launch_partition_k<9>(P, grid, orel, olid, pstart, st);
+        case 10: return launch_partition_k<10>(P, grid, orel, olid, pstart, st);
+        default: return launch_partition_k<0>(P, grid, orel, olid, pstart, st);
+    }
+}
+
+// Capacity of each unit's enriched list: partitioned mode, the unit's l-mers
+// over s; else a bound shared by all units.
+__global__ void emit_cap_kernel(const int32_t *__restrict__ pstart, int n_chunks, int parts,
+                                int64_t units, int s, int64_t uniform_cap,
+                                int64_t *__restrict__ cap) {
+    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u >= units) return;
+    if (!pstart) {
+        cap[u] = uniform_cap;
+        return;
+    }
+    const int64_t trial = u / parts;
+    const int part = (int)(u % parts);
+    const int32_t *ps = pstart + trial * n_chunks * (parts + 1);
+    int64_t n = 0;
+    for (int c = 0; c < n_chunks; ++c) n += ps[c * (parts + 1) + part + 1] - ps[c * (parts + 1) + part];
+    cap[u] = n / s;
+}
+
+// Candidate table from the counting pass's lists (no recount): unit u's
+// (key, size) entries go to cand_base[u] .., their member offsets continue
+// from mem_base[u] in key order.
+__global__ void __launch_bounds__(kThreads) hash_table_kernel(const HashParams P) {
+    __shared__ int2 s_warp[kWarps + 1];
+    const int unit = blockIdx.x, tid = threadIdx.x;
+    const int trial = (int)(P.trial_begin + unit / P.parts);
+    const uint32_t lo_key = (uint32_t)(unit % P.parts) * (uint32_t)P.hb;
+    const uint2 *src = P.emit + P.emit_off[unit];
+    const int nb = P.part_nb[unit];
+    const int64_t cb = P.cand_base[unit];
+    int64_t run = P.mem_base[unit];
+    for (int base = 0; base < nb; base += kThreads) {
+        const int i = base + tid;
+        const uint2 e = i < nb ? src[i] : make_uint2(0u, 0u);
+        int pc, pz, tc, tz;
+        block_scan2((int)e.y, 0, pc, pz, tc, tz, s_warp);
+        if (i < nb && cb + i < P.cap_cand) {
+            P.cand_trial[cb + i] = trial;
+            P.cand_key[cb + i] = lo_key + e.x;
+            P.cand_cnt[cb + i] = (int32_t)e.y;
+            P.cand_off[cb + i] = run + pc;
+        }
+        run += tc;
+    }
+}
+
+// Members of selected candidates (one CTA each), ascending: the l-mers of the
+// candidate's trial whose projected key is the candidate's, compacted in
+// l-mer order with ballot scans.  Partitioned mode scans the (trial, part)
+// segment of the partition; otherwise every l-mer of the trial is rehashed.
+__global__ void __launch_bounds__(kThreads) gather_sel_kernel(
+    const HashParams P, const int64_t *__restrict__ sel, const int32_t *__restrict__ cand_trial,
+    const uint32_t *__restrict__ cand_key, const int64_t *__restrict__ new_off,
+    int32_t *__restrict__ out) {
+    extern __shared__ __align__(16) uint8_t g_smem[];  // partitioned: the unit's chunk walk
+    __shared__ int s_pos[16];
+    __shared__ int s_round[kWarps + 1];
+    __shared__ int2 s_warp[kWarps + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t ci = sel[blockIdx.x];
+    const int trial_local = (int)(cand_trial[ci] - P.trial_begin);
+    const uint32_t key = cand_key[ci];
+    const uint32_t part = key / (uint32_t)P.hb, rel = key - part * (uint32_t)P.hb;
+    const int64_t o0 = new_off[blockIdx.x], len = new_off[blockIdx.x + 1] - o0;
+    int32_t *s_cb = reinterpret_cast<int32_t *>(g_smem);
+    long long *s_pb = reinterpret_cast<long long *>(g_smem + (((P.n_chunks + 1) * 4 + 15) & ~15));
+    int64_t n_iter;
+    if (P.partitioned) {
+        unit_walk_setup(P, trial_local, (int)part, s_cb, s_pb, s_warp);
+        n_iter = s_cb[P.n_chunks];
+    } else {
+        n_iter = P.x;
+        if (tid == 0) {
+            if (P.fixed_pos) {
+                for (int q = 0; q < P.k; ++q) s_pos[q] = P.pos_in[q];
+            } else {
+                draw_positions(P.seed, (uint64_t)(P.trial_begin + trial_local), P.l, P.k, s_pos);
+            }
+        }
+        __syncthreads();
+    }
+    int pos[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) pos[q] = (!P.partitioned && q < P.k) ? s_pos[q] : 0;
+    int i = 0, c = 0;
+    int64_t running = 0;
+    for (int64_t base = 0; base < n_iter; base += kThreads) {
+        const int64_t it = base + tid;
+        bool e = false;
+        int gid = 0;
+        if (it < n_iter) {
+            if (P.partitioned) {
+                while (s_cb[c + 1] <= it) ++c;
+                e = P.prel[s_pb[c] + it] == rel;
+                if (e) gid = c * kSortChunk + (int)P.plid[s_pb[c] + it];
+            } else {
+                gid = (int)it;
+                while (__ldg(P.lmer_off + i + 1) <= gid) ++i;
+                const int64_t b0 = (int64_t)__ldg(P.seq_off + i) + (gid - __ldg(P.lmer_off + i));
+                e = lmer_key(window64(P.packed, P.nwords, b0), pos, P.k) == key;
+            }
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, e);
+        if (lane == 0) s_round[warp] = __popc(bal);
+        __syncthreads();
+        if (warp == 0) {
+            const int v = lane < kWarps ? s_round[lane] : 0;
+            int sc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, sc, o);
+                if (lane >= o) sc += u;
+            }
+            if (lane < kWarps) s_round[lane] = sc - v;
+            if (lane == kWarps - 1) s_round[kWarps] = sc;
+        }
+        __syncthreads();
+        if (e) {
+            const int64_t q = running + s_round[warp] + __popc(bal & ((1u << lane) - 1u));
+            if (q < len) out[o0 + q] = gid;
+        }
+        running += s_round[kWarps];
+        __syncthreads();
     }
 }
 
@@ -673,7 +946,13 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
     // stage the packed input when it fits next to the histogram (the
     // partitioned mode reads precomputed keys instead)
     const bool partitioned = P.parts > 1 && L.x > 65535;
-    if (!partitioned) {
+    if (partitioned) {
+        P.partitioned = 1;
+        P.n_chunks = (int)((L.x + kSortChunk - 1) / kSortChunk);
+        PROJ_REQUIRE(P.n_chunks <= kMaxSortChunks,
+                     "%lld l-mers exceed the partitioned mode's %d chunks of %d",
+                     (long long)L.x, kMaxSortChunks, kSortChunk);
+    } else {
         HashParams Q = P;
         Q.stage_words = (int)L.nwords;
         if (smem_layout(Q, true).total <= kSmemLimit) P.stage_words = (int)L.nwords;
@@ -701,27 +980,53 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
     P.cand_base = cbase;
     P.mem_base = mbase;
 
-    // large inputs over several key-range parts: partition (key, id) pairs first
+    // large inputs over several key-range parts: group each trial's keys by
+    // part first.  part_buf: [part starts (int32) | keys (u16) | chunk-local ids (u16)]
     if (partitioned) {
         PROJ_REQUIRE(P.parts <= kMaxParts, "too many key-range parts");
-        P.n_chunks = (int)((L.x + kChunk - 1) / kChunk);
-        const int64_t n_cnt = n_trials * P.parts * P.n_chunks;
-        PROJ_REQUIRE(n_trials * L.x < ((int64_t)1 << 40), "partition too large");
+        const int64_t n_pst = n_trials * P.n_chunks * (P.parts + 1);
+        const int64_t n_ent = n_trials * P.n_chunks * kSortChunk;
         if (!reuse)
-            PROJ_TRY(part_buf.alloc((size_t)(2 * n_cnt + 1) * 8 + (size_t)n_trials * L.x * 8, st));
-        int64_t *cnt = part_buf.as<int64_t>();
-        int64_t *seg = cnt + n_cnt;
-        uint2 *pairs = reinterpret_cast<uint2 *>(seg + n_cnt + 1);
-        P.pairs = pairs;
-        P.seg_off = seg;
+            PROJ_TRY(part_buf.alloc((size_t)n_pst * 4 + 16 + (size_t)n_ent * 4, st));
+        int32_t *pst = part_buf.as<int32_t>();
+        uint16_t *rel = reinterpret_cast<uint16_t *>(
+            (reinterpret_cast<uintptr_t>(pst + n_pst) + 15) & ~(uintptr_t)15);
+        P.pstart = pst;
+        P.prel = rel;
+        P.plid = rel + n_ent;
+        if (!reuse) {
+            const dim3 grid((unsigned)P.n_chunks, (unsigned)n_trials);
+            PROJ_TRY(launch_partition(P, grid, rel, rel + n_ent, pst, st));
+        }
     }
-    if (partitioned && !reuse) {
-        const int64_t n_cnt = n_trials * P.parts * P.n_chunks;
-        int64_t *cnt = part_buf.as<int64_t>();
-        int64_t *seg = cnt + n_cnt;
-        uint2 *pairs = reinterpret_cast<uint2 *>(seg + n_cnt + 1);
-        const dim3 grid((unsigned)P.n_chunks, (unsigned)n_trials);
-        PROJ_TRY(launch_partition(P, grid, cnt, seg, pairs, n_cnt, st));
+    // each unit's enriched (key, size) list kept by the counting pass (a search
+    // that keeps only its largest buckets builds its table from them)
+    HashState *hs = out.state;
+    if (hs && out.want_emit && !reuse) {
+        const int64_t cap_u = std::min<int64_t>(P.hb, L.x / s);
+        const int64_t ub = partitioned ? n_trials * L.x / s + n_units : n_units * cap_u;
+        PROJ_TRY(hs->emit_buf.alloc((size_t)(2 * n_units + 1) * 8 + (size_t)ub * 8, st));
+        int64_t *eoff = hs->emit_buf.as<int64_t>();
+        int64_t *ecap = eoff + n_units + 1;
+        emit_cap_kernel<<<(unsigned)((n_units + 255) / 256), 256, 0, st>>>(
+            partitioned ? P.pstart : nullptr, P.n_chunks, P.parts, n_units, s, cap_u, ecap);
+        PROJ_LAUNCH_CHECK("emit_cap_kernel");
+        scan_i64_kernel<<<1, 1024, 0, st>>>(ecap, n_units, eoff);
+        PROJ_LAUNCH_CHECK("scan_i64_kernel");
+        hs->emitted = true;
+    }
+    if (hs && hs->emitted) {
+        P.emit_off = hs->emit_buf.as<int64_t>();
+        P.emit = reinterpret_cast<uint2 *>(hs->emit_buf.as<int64_t>() + 2 * n_units + 1);
+    }
+    if (hs) {
+        hs->parts = P.parts;
+        hs->hb = P.hb;
+        hs->n_chunks = P.n_chunks;
+        hs->partitioned = partitioned;
+        hs->prel = P.prel;
+        hs->plid = P.plid;
+        hs->pstart = P.pstart;
     }
     if (!reuse) {
         {
@@ -743,6 +1048,21 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
         if (out.state) out.state->valid = true;
         return PROJ_OK;
     }
+    P.cap_cand = out.cap_cand;
+    P.cand_trial = out.cand_trial;
+    P.cand_key = out.cand_key;
+    P.cand_cnt = out.cand_cnt;
+    P.cand_off = out.cand_off;
+    if (out.table_only) {
+        PROJ_REQUIRE(reuse && hs && hs->emitted, "a table-only fill needs the counting call's lists");
+        {
+            TraceSpan ts_("hash_table", st);
+            hash_table_kernel<<<(unsigned)n_units, kThreads, 0, st>>>(P);
+        }
+        PROJ_LAUNCH_CHECK("hash_table_kernel");
+        return PROJ_OK;
+    }
+    P.emit = nullptr;
 
     DevBuf scratch;
     if (out.cap_members > 0) PROJ_TRY(scratch.alloc((size_t)out.cap_members * 8, st));
@@ -761,6 +1081,42 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
         TraceSpan ts_("hash_fill", st);
         PROJ_TRY(launch_hash<true>(P, (unsigned)n_units, S2.total, st));
     }
+    return PROJ_OK;
+}
+
+int run_gather_members(const uint32_t *packed, const Layout &L, const HashState &hs, int k,
+                       uint64_t seed, const int64_t *sel, int64_t n, const int32_t *cand_trial,
+                       const uint32_t *cand_key, const int64_t *new_off, int32_t *new_members,
+                       cudaStream_t st) {
+    PROJ_REQUIRE(hs.valid && hs.hb > 0, "the member gather needs the counting call's state");
+    if (n == 0) return PROJ_OK;
+    HashParams P{};
+    P.packed = packed;
+    P.nwords = L.nwords;
+    P.seq_off = L.seq_off_dev();
+    P.lmer_off = L.lmer_off_dev();
+    P.t = L.t; P.l = L.l; P.k = k; P.x = (int)L.x;
+    P.seed = seed;
+    P.trial_begin = 0;
+    P.parts = hs.parts;
+    P.hb = hs.hb;
+    P.n_chunks = hs.n_chunks;
+    int smem = 0;
+    if (hs.partitioned) {
+        P.partitioned = 1;
+        P.prel = hs.prel;
+        P.plid = hs.plid;
+        P.pstart = hs.pstart;
+        smem = (((P.n_chunks + 1) * 4 + 15) & ~15) + P.n_chunks * 8;
+    }
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(gather_sel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       std::max(smem, 1)));
+    {
+        TraceSpan ts_("hash_gather", st);
+        gather_sel_kernel<<<(unsigned)n, kThreads, smem, st>>>(P, sel, cand_trial, cand_key, new_off,
+                                                              new_members);
+    }
+    PROJ_LAUNCH_CHECK("gather_sel_kernel");
     return PROJ_OK;
 }
 

@@ -109,3 +109,42 @@ def test_batch_rejects_fp32(P):
         P.projection_find_batch([inst.seqs], [inst.l], [inst.d], [6], [4], [5], [1],
                                 precision=P.PROJ_EM_FP32)
     assert e.value.status == -7
+
+
+def test_config4_mix_sample_matches_oracle(P):
+    """A deterministic sample of the 256-instance serving mix (every 32nd
+    instance, at its real trial count from the Section 5 bound) through the
+    batched call, each checked against the FP64 oracle: the enriched-bucket
+    count exactly, and EM on every 97th candidate plus the batch's winner
+    (the oracle's EM over all ~10^4-10^5 candidates of an instance is too slow
+    for a test): the winner is the oracle's best of that subset up to the
+    BF16-split tolerance, its model is the oracle's model of the same bucket,
+    and its consensus and sites follow from it."""
+    insts = mix_instances(256)[::32]
+    K = [i.params["k"] for i in insts]
+    S = [i.params["s"] for i in insts]
+    M = [P.projection_default_params(i.lens, i.l, i.d, k, s, 0)[2]
+         for i, k, s in zip(insts, K, S)]
+    seeds = [4000 + 32 * q for q in range(len(insts))]
+    got = P.projection_find_batch([i.seqs for i in insts], [i.l for i in insts],
+                                  [i.d for i in insts], K, S, M, seeds, em_iters=5,
+                                  pseudocount=0.25)
+    for inst, k, s, m, sd, g in zip(insts, K, S, M, seeds, got):
+        codes = O.encode(inst.ascii)
+        h = O.hash_trials(codes, inst.seq_off, inst.l, k, s, sd, 0, m)
+        C = h["cand_key"].size
+        assert g["n_candidates"] == C and g["m"] == m
+        if C == 0:
+            continue
+        w = g["win_index"]
+        sub = np.array(sorted(set(range(0, C, 97)) | {w}), np.int64)
+        want = O.find([q.decode() for q in inst.seqs], inst.l, inst.d, k, s, m, seed=sd,
+                      em_iters=5, beta=0.25, nthreads=16, subset=sub)
+        at = int(np.searchsorted(sub, w))
+        tol = ll_tol(want["loglik"], inst.t, LL_REL_BF16)
+        assert want["ll_all"][at] >= want["loglik"] - 2 * tol
+        assert abs(g["loglik"] - want["ll_all"][at]) <= tol
+        assert np.max(np.abs(g["pwm"] - want["pwm_all"][at])) <= 5e-5
+        assert g["consensus"] == O.consensus(want["pwm_all"][at])
+        assert np.array_equal(g["sites"], O.sites(codes, inst.seq_off, inst.l, want["bg"],
+                                                  g["pwm"].astype(np.float64)))

@@ -58,3 +58,90 @@ def test_top_larger_than_candidates_refines_all(P):
     for key in ("win_index", "consensus", "loglik", "score"):
         assert a[key] == b[key]
     assert np.array_equal(a["sites"], b["sites"])
+
+
+def _oracle_top(inst, k, s, seed, m, top):
+    codes = O.encode(inst.ascii)
+    h = O.hash_trials(codes, inst.seq_off, inst.l, k, s, seed, 0, m)
+    sel = O.top_candidates(h["cand_cnt"], top)
+    mem = [h["members"][h["cand_off"][c]:h["cand_off"][c + 1]] for c in sel]
+    return h, sel, mem
+
+
+@pytest.mark.parametrize("case", ["partitioned", "rehashed", "all_kept"])
+def test_trial_hash_top_lists_bit_exact(P, chip_like, case):
+    """The capped search's lists (Algorithm 2 step 3 with the top-K cap): which
+    buckets are kept, in size order with (trial, key) ties, and every kept
+    bucket's members in ascending order, bit for bit with the oracle.  The
+    (20,5) t=200 input has x = 96,200 > 65,535 l-mers, so k = 10 takes the
+    partitioned path (members gathered from the partition); a t=20 input at
+    k = 7 rehashes each kept bucket's trial; a cap above C keeps everything."""
+    if case == "partitioned":
+        inst, k, s, m, top, seed = chip_like, 10, 3, 6, 64, 5
+    elif case == "rehashed":
+        from synth import instance_for_config
+        inst, k, s, m, top, seed = instance_for_config(1), 7, 4, 30, 100, 11
+    else:
+        inst, k, s, m, top, seed = planted_instance(9, 1, 12, 300, 11, 2), 7, 4, 10, 10**5, 3
+    packed = P.projection_pack(torch.from_numpy(inst.ascii).cuda())
+    got = P.trial_hash_top(packed, inst.seq_off, inst.l, k, s, seed, m, top)
+    h, sel, mem = _oracle_top(inst, k, s, seed, m, top)
+    assert got["n_candidates"] == h["cand_key"].size
+    assert got["n_members"] == h["members"].size
+    assert got["n_kept"] == sel.size == min(top, h["cand_key"].size)
+    if case != "all_kept":
+        assert got["n_candidates"] > top
+    assert np.array_equal(got["sel_index"].cpu().numpy(), sel)
+    assert np.array_equal(got["cand_trial"].cpu().numpy(), h["cand_trial"][sel])
+    assert np.array_equal(got["cand_key"].cpu().numpy().view(np.uint32),
+                          h["cand_key"][sel].astype(np.uint32))
+    assert np.array_equal(got["cand_cnt"].cpu().numpy(), h["cand_cnt"][sel])
+    off = got["cand_off"].cpu().numpy()
+    members = got["members"].cpu().numpy()
+    assert off[0] == 0 and off[-1] == members.size == sum(len(v) for v in mem)
+    for i, want in enumerate(mem):
+        assert np.array_equal(members[off[i]:off[i + 1]], want), i
+
+
+@pytest.mark.parametrize("prec,pwm_tol,ll_rel", [("fp32", 1e-5, 1e-6), ("bf16", 5e-5, 1e-4)])
+def test_top_search_at_full_size(P, prec, pwm_tol, ll_rel):
+    """The serving-scale input at full size (t = 2000 x n = 500, x = 962,000
+    l-mers, k = 10), 3 trials, top 1024 buckets refined by 10 EM iterations.
+    The oracle hashes the same trials; EM parity on the 16 largest buckets and
+    the search's winner, from identical starting models (the oracle's theta^0
+    rounded to float32): models and log-likelihoods within the precision's
+    tolerance; the winner is one of the oracle's kept buckets, and its
+    consensus and sites follow from its model."""
+    from synth import instance_for_config
+    inst = instance_for_config(5)
+    k, s, m, top, iters = 10, 4, 3, 1024, 10
+    precision = P.PROJ_EM_FP32 if prec == "fp32" else P.PROJ_EM_BF16_SPLIT
+    packed = P.projection_pack(torch.from_numpy(inst.ascii).cuda())
+    got = P.projection_find_packed_top(packed, inst.seq_off, inst.l, inst.d, k, s, m, seed=1005,
+                                       em_iters=iters, pseudocount=0.25, precision=precision,
+                                       top=top)
+    codes = O.encode(inst.ascii)
+    h = O.hash_trials(codes, inst.seq_off, inst.l, k, s, 1005, 0, m)
+    kept = O.top_candidates(h["cand_cnt"], top)
+    assert got["n_candidates"] == h["cand_key"].size and got["n_refined"] == top
+    w = got["win_index"]
+    assert w in set(kept.tolist())
+    sel = list(kept[:16]) + ([w] if w not in set(kept[:16].tolist()) else [])
+    th0 = np.stack([O.theta0(codes, inst.seq_off, inst.l,
+                             h["members"][h["cand_off"][c]:h["cand_off"][c + 1]], 0.25)
+                    for c in sel]).astype(np.float32)
+    bg_o = O.background(codes)
+    w_pwm, w_ll = O.em(codes, inst.seq_off, inst.l, bg_o, th0.astype(np.float64), iters, 0.25,
+                       nthreads=16)
+    bg = P.projection_background(packed, inst.seq_off[-1])
+    g_pwm, g_ll = P.em_refine(packed, inst.seq_off, inst.l, bg, torch.from_numpy(th0).cuda(),
+                              iters, 0.25, precision)
+    g_pwm, g_ll = g_pwm.cpu().numpy(), g_ll.cpu().numpy()
+    assert np.max(np.abs(g_pwm - w_pwm)) <= pwm_tol
+    assert np.all(np.abs(g_ll - w_ll) <= ll_tol(w_ll, inst.t, ll_rel))
+    q = sel.index(w)
+    assert np.max(np.abs(got["pwm"] - w_pwm[q])) <= pwm_tol
+    assert abs(got["loglik"] - w_ll[q]) <= ll_tol(w_ll[q], inst.t, ll_rel)
+    assert got["consensus"] == O.consensus(got["pwm"].astype(np.float64))
+    assert np.array_equal(got["sites"], O.sites(codes, inst.seq_off, inst.l, bg_o,
+                                                got["pwm"].astype(np.float64)))
