@@ -115,11 +115,14 @@ __device__ __forceinline__ uint32_t lmer_key(uint64_t win, const int *pos, int k
 // K = 0 falls back to the run-time k.
 template <int K>
 __device__ __forceinline__ uint32_t lmer_key_k(uint64_t win, const int *pos, int k) {
-    if (K == 0) return lmer_key(win, pos, k);
-    uint32_t key = 0u;
+    if constexpr (K == 0) {
+        return lmer_key(win, pos, k);
+    } else {
+        uint32_t key = 0u;
 #pragma unroll
-    for (int q = 0; q < K; ++q) key = (key << 2) | (uint32_t)((win >> (2 * pos[q])) & 3u);
-    return key;
+        for (int q = 0; q < K; ++q) key = (key << 2) | (uint32_t)((win >> (2 * pos[q])) & 3u);
+        return key;
+    }
 }
 
 // Block-wide exclusive scan of two ints; returns the prefixes and the totals.
@@ -233,8 +236,9 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
         words = s_words;
         nwords = nw + 2;
     }
-    const int hist_words = S.hist_bytes / 4;
-    for (int w = tid; w < hist_words; w += kThreads) hist32[w] = 0u;
+    const int hist_words = S.hist_bytes / 4;  // a multiple of 4
+    for (int w = tid; w < hist_words / 4; w += kThreads)
+        reinterpret_cast<uint4 *>(hist32)[w] = make_uint4(0u, 0u, 0u, 0u);
     if (FILL)
         for (int w = tid; w < S.bitmap_bytes / 4; w += kThreads) bitmap[w] = 0u;
     __syncthreads();
@@ -247,23 +251,23 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     // Algorithm 2 steps 2b-2c: project every l-mer and count its bucket.
     const int n_flat = P.partitioned ? s_cb[P.n_chunks] : 0;  // the unit's l-mers
     if (P.partitioned) {
-        // eight loads in flight per thread ahead of their increments (the
-        // pieces stream from HBM); u32 counters in this mode
-        int c = 0;  // piece of this thread's current entry (entries only grow)
-        for (int f0 = tid; f0 < n_flat; f0 += 8 * kThreads) {
-            uint32_t r[8];
+        // counting needs no order: warp w takes pieces w, w + 32, ..., each lane
+        // eight loads in flight ahead of their increments (the pieces stream
+        // from HBM); u32 counters in this mode
+        for (int c = warp; c < P.n_chunks; c += kWarps) {
+            const int len = s_cb[c + 1] - s_cb[c];
+            const uint16_t *src = P.prel + (s_pb[c] + s_cb[c]);
+            for (int e0 = lane; e0 < len; e0 += 8 * 32) {
+                uint32_t r[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int f = f0 + q * kThreads;
-                r[q] = 0xFFFFFFFFu;
-                if (f < n_flat) {
-                    while (s_cb[c + 1] <= f) ++c;
-                    r[q] = __ldg(P.prel + s_pb[c] + f);
+                for (int q = 0; q < 8; ++q) {
+                    const int e = e0 + 32 * q;
+                    r[q] = e < len ? (uint32_t)__ldg(src + e) : 0xFFFFFFFFu;
                 }
-            }
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (r[q] != 0xFFFFFFFFu) atomicAdd(&hist32[r[q]], 1u);
+                for (int q = 0; q < 8; ++q)
+                    if (r[q] != 0xFFFFFFFFu) atomicAdd(&hist32[r[q]], 1u);
+            }
         }
     } else {
         int i = 0;
@@ -484,6 +488,8 @@ __global__ void __launch_bounds__(kThreads, 1) hash_batch_kernel(const HashParam
 // every chunk.  No step depends on another CTA.
 // ---------------------------------------------------------------------------
 constexpr int kMaxParts = 32;
+constexpr int kPartShift = 15;                  // partitioned mode: u32 counters, 2^15 keys per part
+constexpr uint32_t kPartKeys = 1u << kPartShift;
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;  // one warp per 1024 l-mers of a chunk
 static_assert(kSortWarps * 1024 == kSortChunk, "chunk = warps x 1024 l-mers");
@@ -513,19 +519,6 @@ __device__ __forceinline__ int seq_of(const int32_t *lmer_off, int t, int g) {
         if (__ldg(lmer_off + mid) <= g) lo = mid; else hi = mid - 1;
     }
     return lo;
-}
-
-// The active lanes of this warp whose part equals this lane's (five ballots
-// over the bits of a part index below 32).
-__device__ __forceinline__ unsigned same_part(uint32_t part, bool act) {
-    unsigned eq = __ballot_sync(0xffffffffu, act);
-#pragma unroll
-    for (int b = 0; b < 5; ++b) {
-        const bool bit = (part >> b) & 1u;
-        const unsigned bal = __ballot_sync(0xffffffffu, act && bit);
-        eq &= bit ? bal : ~bal;
-    }
-    return eq;
 }
 
 template <int K>
@@ -567,7 +560,7 @@ __global__ void __launch_bounds__(kSortThreads) part_sort_kernel(const HashParam
         for (int w = tid; w < nw + 2; w += kSortThreads)
             s_words[w] = w_lo + w < P.nwords ? __ldg(P.packed + w_lo + w) : 0u;
         for (int q = tid; q <= i1 - i0 + 1; q += kSortThreads) {
-            s_soff[q] = P.seq_off[i0 + q];
+            s_soff[q] = (int32_t)(P.seq_off[i0 + q] - 16 * (int64_t)w_lo);  // base in s_words
             s_loff[q] = P.lmer_off[i0 + q];
         }
     }
@@ -575,7 +568,6 @@ __global__ void __launch_bounds__(kSortThreads) part_sort_kernel(const HashParam
     int pos[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) pos[q] = q < P.k ? s_pos[q] : 0;
-    const uint32_t hb = (uint32_t)P.hb;
     const int j0 = warp * 1024;  // this warp's l-mers of the chunk, in rounds of 32
     const unsigned below = (1u << lane) - 1u;
 
@@ -584,24 +576,31 @@ __global__ void __launch_bounds__(kSortThreads) part_sort_kernel(const HashParam
     for (int r = 0; r < 32; ++r) {
         const int j = j0 + 32 * r + lane;
         const bool act = j < n;
-        uint32_t part = 0u;
+        const unsigned amask = __ballot_sync(0xffffffffu, act);
         if (act) {
             const int g = g0 + j;
             uint32_t key;
-            if (staged) {
+            if (staged) {  // every word the chunk's l-mers touch is in s_words
                 while (s_loff[i + 1] <= g) ++i;
-                const int64_t b0 = (int64_t)s_soff[i] + (g - s_loff[i]) - 16 * (int64_t)w_lo;
-                key = lmer_key_k<K>(window64(s_words, nw + 2, b0), pos, P.k);
+                const int b = s_soff[i] + (g - s_loff[i]);
+                const int wi = b >> 4, sh = 2 * (b & 15);
+                const uint64_t lo = (uint64_t)s_words[wi] | ((uint64_t)s_words[wi + 1] << 32);
+                const uint64_t win = sh ? (lo >> sh) | ((uint64_t)s_words[wi + 2] << (64 - sh)) : lo;
+                key = lmer_key_k<K>(win, pos, P.k);
             } else {
                 while (__ldg(P.lmer_off + i0 + i + 1) <= g) ++i;
                 const int64_t b0 = (int64_t)__ldg(P.seq_off + i0 + i) + (g - __ldg(P.lmer_off + i0 + i));
                 key = lmer_key_k<K>(window64(P.packed, P.nwords, b0), pos, P.k);
             }
-            s_key[j] = key;
-            part = key / hb;
+            const uint32_t part = key >> kPartShift;
+            // lanes of this round with the same part, in lane order; this l-mer's
+            // place among its warp's l-mers of that part (keys < 2^20, places < 2^10)
+            const unsigned eq = __match_any_sync(amask, part);
+            const int before = s_cnt[warp][part];
+            s_key[j] = key | ((uint32_t)(before + __popc(eq & below)) << 20);
+            __syncwarp(amask);
+            if ((eq & below) == 0u) s_cnt[warp][part] = before + __popc(eq);
         }
-        const unsigned eq = same_part(part, act);
-        if (act && (eq & below) == 0u) s_cnt[warp][part] += __popc(eq);
         __syncwarp();
     }
     __syncthreads();
@@ -632,19 +631,14 @@ __global__ void __launch_bounds__(kSortThreads) part_sort_kernel(const HashParam
     if (tid <= P.parts)
         pstart[((int64_t)trial_local * P.n_chunks + chunk) * (P.parts + 1) + tid] = s_tot[tid];
 
-    // stable placement into shared memory: round r of warp w after rounds < r
-    // of w and all of w' < w; entry = (key - part * hb) | chunk-local id << 16
-    for (int r = 0; r < 32; ++r) {
-        const int j = j0 + 32 * r + lane;
-        const bool act = j < n;
-        const uint32_t key = act ? s_key[j] : 0u;
-        const uint32_t part = key / hb;
-        const unsigned eq = same_part(part, act);
-        if (act) s_out[s_tot[part] + s_cnt[warp][part] + __popc(eq & below)] =
-            (key - part * hb) | ((uint32_t)j << 16);
-        __syncwarp();
-        if (act && (eq & below) == 0u) s_cnt[warp][part] += __popc(eq);
-        __syncwarp();
+    // stable placement into shared memory: after all of part p of warps w' < w,
+    // at the l-mer's place among warp w's l-mers of p; entry = (key - part * hb)
+    // | chunk-local id << 16
+    for (int j = tid; j < n; j += kSortThreads) {
+        const uint32_t v = s_key[j];
+        const uint32_t key = v & 0xFFFFFu, part = key >> kPartShift;
+        s_out[s_tot[part] + s_cnt[j >> 10][part] + (int)(v >> 20)] =
+            (key & (kPartKeys - 1u)) | ((uint32_t)j << 16);
     }
     __syncthreads();
     const int64_t region = ((int64_t)trial_local * P.n_chunks + chunk) * kSortChunk;
@@ -948,6 +942,7 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
     const bool partitioned = P.parts > 1 && L.x > 65535;
     if (partitioned) {
         P.partitioned = 1;
+        PROJ_REQUIRE(P.hb == (int)kPartKeys && !P.hist16, "partitioned mode expects u32 parts");
         P.n_chunks = (int)((L.x + kSortChunk - 1) / kSortChunk);
         PROJ_REQUIRE(P.n_chunks <= kMaxSortChunks,
                      "%lld l-mers exceed the partitioned mode's %d chunks of %d",
