@@ -27,7 +27,7 @@ struct EmItem {
     int inst;        // instance index
     int seq_lo, seq_hi;
     int g;           // sequence group, selects the partial-result slot
-    int n_tiles;     // tiles of 64 l-mers over the item's sequences
+    int n_tiles;     // tiles (64 or 128 l-mers) over the item's sequences
     int64_t tile0;   // index of its first tile in the run's one-hot tile array
 };
 
@@ -46,8 +46,9 @@ struct EmInstHost {
     const int32_t *seq_off = nullptr;  // host copy of the instance's EmInst::seq_off [t+1]
 };
 
+// h = parts per candidate row of the kernel (2: tiles of 64 l-mers, 4: 128)
 int em_tc_plan(const std::vector<EmInstHost> &insts, std::vector<EmItem> &items, int &G,
-               int ctas, int waves);
+               int ctas, int waves, int h);
 
 // One tensor-core EM run split into allocation/planning (em_tc_prepare, may
 // synchronise to autotune), launches only (em_tc_enqueue, capturable in a
@@ -58,9 +59,9 @@ struct EmTcRun {
     const EmInst *inst_dev = nullptr;
     const float *theta0 = nullptr;
     int64_t C = 0;
-    int stride = 0, n_inst = 0, kp = 16, G = 1, ctas = 3, n_items = 0;
+    int stride = 0, n_inst = 0, kp = 16, G = 1, ctas = 3, n_items = 0, h = 2;
     DevBuf part, tmp, flag, items, tiles;
-    DevBuf xt, xseq;  // one-hot tiles [n_x_tiles][64][kp] BF16 (K-major core layout), their sequences
+    DevBuf xt, xseq;  // one-hot tiles [n_x_tiles][32 h][kp] BF16 (K-major core layout), their sequences
 };
 int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmInstHost> &insts,
                   const EmInst *inst_dev, const float *theta0, int64_t C, int stride,

@@ -54,8 +54,12 @@
 namespace proj {
 namespace {
 
-constexpr int kSoftThreads = 256;              // softmax warps 0-7
-constexpr int kTcThreads = kSoftThreads + 32;  // + the MMA-issuing warp
+// A CTA runs 4H softmax warps (H threads per candidate row, each taking 32
+// l-mers of a tile of 64H) and one MMA-issuing warp.  H = 2: 64-l-mer tiles,
+// 256 tensor-memory columns, two CTAs per SM; H = 4: 128-l-mer tiles (half
+// the per-tile synchronisation and MMA issue per l-mer), 512 columns, one CTA.
+template <int H> constexpr int soft_threads() { return 128 * H; }
+template <int H> constexpr int tc_threads() { return 128 * H + 32; }
 constexpr int kTcRows = 128;     // candidates per work item = tensor-memory lanes
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait on a tensor-core completion
 
@@ -82,25 +86,29 @@ struct EmTcParams {
     int *err;
 };
 
-constexpr int kNT = 64;  // l-mers per tile (N of the score MMA, K of the count MMA)
+constexpr int kNT = 64;  // l-mers per tile and part count H / 2 (N of the score MMA, K of the
+                         // count MMA is 64 H)
 // Up to this many sequence groups per candidate tile the last item of a tile
 // folds the groups' partial results itself; beyond it one CTA would serialise
 // too much of that work, and a separate grid-wide kernel does it.
 constexpr int kFoldMaxG = 4;
 
-template <int KP>
+template <int KP, int H>
 struct TcLayout {
+    static constexpr int NT = kNT * H / 2;          // l-mers per tile
     static constexpr int W_BYTES = 128 * KP * 2;   // each of W_hi, W_lo
-    static constexpr int X_BYTES = kNT * KP * 2;   // one one-hot tile
+    static constexpr int X_BYTES = NT * KP * 2;    // one one-hot tile
     static constexpr int NX = 4;                   // ring of one-hot tiles
     static constexpr int OFF_WHI = 0;
     static constexpr int OFF_WLO = OFF_WHI + W_BYTES;
     static constexpr int OFF_X = OFF_WLO + W_BYTES;
     static constexpr int TOTAL = OFF_X + NX * X_BYTES;
-    // two score buffers S[2] (kNT columns each; P = 2^(S - m) as BF16 hi + lo
+    // two score buffers S[2] (NT columns each; P = 2^(S - m) as BF16 hi + lo
     // replaces S in place) and the count accumulator O (KP)
-    static constexpr uint32_t TMEM_COLS = 256;
-    static_assert(2 * kNT + KP <= 256, "tensor-memory budget");
+    static constexpr uint32_t TMEM_COLS = H == 2 ? 256 : 512;
+    static_assert(2 * NT + KP <= (int)TMEM_COLS, "tensor-memory budget");
+    static constexpr int NCH = KP / 8;                // 8-column chunks of a row
+    static constexpr int CPT = (NCH + H - 1) / H;     // chunks per thread of a row (at most)
 };
 
 __device__ __forceinline__ float ex2(float x) {
@@ -124,6 +132,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 // Walks the l-mer tiles of an item's sequences in order: sequence seq, first
 // start j0 of the tile, ns = number of starts of the sequence, base = its
 // first base in the packed input.
+template <int NT>
 struct TileIt {
     int seq, j0, ns;
     int base;  // first base of the sequence (inputs hold < 2^31 bases)
@@ -136,9 +145,9 @@ struct TileIt {
         j0 = 0;
         load(in);
     }
-    __device__ __forceinline__ bool last() const { return j0 + kNT >= ns; }
+    __device__ __forceinline__ bool last() const { return j0 + NT >= ns; }
     __device__ __forceinline__ void advance(const EmInst &in, int seq_hi) {
-        j0 += kNT;
+        j0 += NT;
         if (j0 >= ns) {
             ++seq;
             j0 = 0;
@@ -147,27 +156,27 @@ struct TileIt {
     }
 };
 
-// One-hot tiles X[j][p*4+a] = [x_{j0+j+p} = a] of every sequence, in the
-// K-major core-matrix layout the MMAs read (KP columns, rows past the
-// sequence's last l-mer zero), one CTA per sequence: thread (row j, part)
-// writes every fourth 16-byte chunk (two positions each, BF16 1.0 = 0x3F80 in
-// the slot of the base's code) of row j, from one 64-bit window of the packed
-// sequence.
+// One-hot tiles X[j][p*4+a] = [x_{j0+j+p} = a] of every sequence (nt rows per
+// tile, nt = 64 or 128), in the K-major core-matrix layout the MMAs read (KP
+// columns, rows past the sequence's last l-mer zero), one CTA per sequence:
+// thread (row j, part) writes every (256/nt)-th 16-byte chunk (two positions
+// each, BF16 1.0 = 0x3F80 in the slot of the base's code) of row j, from one
+// 64-bit window of the packed sequence.
 __global__ void __launch_bounds__(256) em_xtiles_kernel(const uint32_t *__restrict__ packed,
                                                         int64_t nwords,
                                                         const XSeq *__restrict__ seqs, int kp,
-                                                        uint8_t *__restrict__ xt) {
+                                                        int nt, uint8_t *__restrict__ xt) {
     const XSeq sq = seqs[blockIdx.x];
-    const int j = threadIdx.x % kNT, part = threadIdx.x / kNT;
+    const int j = threadIdx.x % nt, part = threadIdx.x / nt, nparts = 256 / nt;
     const int chunks = kp / 8;
-    const size_t xbytes = (size_t)kNT * kp * 2;
-    const int ntiles = (sq.ns + kNT - 1) / kNT;
+    const size_t xbytes = (size_t)nt * kp * 2;
+    const int ntiles = (sq.ns + nt - 1) / nt;
     for (int tt = 0; tt < ntiles; ++tt) {
         uint8_t *dst = xt + (size_t)(sq.tile + tt) * xbytes;
-        const int r = tt * kNT + j;
+        const int r = tt * nt + j;
         const bool row_ok = r < sq.ns;
         const uint64_t win = row_ok ? window64(packed, nwords, sq.base + r) : 0ull;
-        for (int kb = part; kb < chunks; kb += 4) {
+        for (int kb = part; kb < chunks; kb += nparts) {
             uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
             const int p0 = 2 * kb, p1 = 2 * kb + 1;
             if (row_ok && p0 < sq.l) {
@@ -253,30 +262,33 @@ __device__ __forceinline__ float max_half(const float (&v)[32], int nv) {
 // every tile: if a half-tile sum exceeds 2^64 (or is not finite) m is raised to
 // the tile's exact maximum, the row's sums and O are rescaled and the tile
 // recomputed.
-template <int KP>
-__global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(const EmTcParams P) {
-    using LY = TcLayout<KP>;
-    constexpr int NT = kNT;
-    constexpr int KH = KP / 2;  // count columns per thread of a row
+template <int KP, int H>
+__global__ void __launch_bounds__(tc_threads<H>(), (KP <= 80 && H == 2 ? 2 : 1))
+    em_tc_kernel(const EmTcParams P) {
+    using LY = TcLayout<KP, H>;
+    constexpr int NT = LY::NT;
+    constexpr int SOFT = soft_threads<H>();
+    constexpr int THREADS = tc_threads<H>();
+    constexpr int CPT = LY::CPT;  // 8-column count chunks per thread: h, h + H, ...
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t mbSfull[2], mbSfree[2], mbXfull[LY::NX], mbPfull, mbO, mbEnd;
     __shared__ uint32_t tmem_slot;
-    __shared__ float sh_x[2][2][kTcRows];  // [slot][half][row] values exchanged by a row's two threads
+    __shared__ float sh_x[2][H][kTcRows];  // [slot][part][row] values shared by a row's H threads
     __shared__ bool s_last;
     __shared__ float s_inv[kTcRows];  // 1 / (sites + 4 pseudocount) per candidate of a fold
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool issuer = warp == kSoftThreads / 32;
-    const int quad = warp & 3, half = (warp >> 2) & 1;
+    const bool issuer = warp == SOFT / 32;
+    const int quad = warp & 3, half = (warp >> 2) % H;  // half: this thread's part of the row
     const int row = 32 * quad + lane;
     uint8_t *sWhi = smem + LY::OFF_WHI, *sWlo = smem + LY::OFF_WLO, *sX = smem + LY::OFF_X;
 
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&mbSfull[b], 1);
-            tc::mbar_init(&mbSfree[b], kSoftThreads);
+            tc::mbar_init(&mbSfree[b], SOFT);
         }
         for (int s = 0; s < LY::NX; ++s) tc::mbar_init(&mbXfull[s], 1);  // + the copy's bytes
-        tc::mbar_init(&mbPfull, kSoftThreads);
+        tc::mbar_init(&mbPfull, SOFT);
         tc::mbar_init(&mbO, 1);
         tc::mbar_init(&mbEnd, 1);
         tc::mbar_fence_init();
@@ -315,13 +327,16 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
             ++o_waited;
         }
     };
-    // the other thread of this row's value (both call it together)
-    auto exchange = [&](float mine) {
+    // the sum / maximum over this row's H threads (all of them call it together)
+    auto row_reduce = [&](float mine, bool take_max) {
         const int s = xcnt & 1;
         ++xcnt;
         sh_x[s][half][row] = mine;
-        tc::named_bar(1 + quad, 64);
-        return sh_x[s][half ^ 1][row];
+        tc::named_bar(1 + quad, 32 * H);
+        float r = sh_x[s][0][row];
+#pragma unroll
+        for (int h = 1; h < H; ++h) r = take_max ? fmaxf(r, sh_x[s][h][row]) : r + sh_x[s][h][row];
+        return r;
     };
 
     for (int it = blockIdx.x; it < P.n_items && !abort; it += gridDim.x) {
@@ -341,11 +356,11 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
         float wmax = 0.f;   // sum over this thread's positions of max_a W
         if (!issuer) {
             // W_c = log2 theta_c - log2 bg in FP32, split into BF16 hi + lo: the
-            // thread of half h writes columns [h*KP/2, (h+1)*KP/2) of its row
+            // thread of part h writes the 8-column chunks h, h + H, ... of its row
             float lbg[4];
 #pragma unroll
             for (int a = 0; a < 4; ++a) lbg[a] = log2f((float)in.bg[a]);
-            for (int k8 = half * KH; k8 < (half + 1) * KH; k8 += 8) {
+            for (int k8 = 8 * half; k8 < KP; k8 += 8 * H) {
                 float w[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
@@ -373,11 +388,11 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                     make_uint4(lo[0], lo[1], lo[2], lo[3]);
             }
         }
-        // per row: highest possible score and score range (both halves)
+        // per row: highest possible score and score range (all parts)
         float row_span = 0.f, row_top = 0.f;
         if (!issuer) {
-            row_span = span + exchange(span);
-            row_top = wmax + exchange(wmax);
+            row_span = row_reduce(span, false);
+            row_top = row_reduce(wmax, false);
         }
         const bool careful = __syncthreads_or(row_span > 200.f);
         if (!issuer) tc::fence_async_smem();
@@ -412,7 +427,7 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                     issue_scores(tm + NT, 1);
                     tc::mma_commit(&mbSfull[1]);
                 }
-                TileIt ti;
+                TileIt<NT> ti;
                 ti.start(in, item.seq_lo, item.seq_hi);
                 for (int j = 0; j < n && ok; ++j) {
                     if (P.mstep) {
@@ -452,9 +467,11 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                 }
             }
         } else {
-            float tot[KH];  // this item's normalised counts of candidate c, columns of this half
+            // this item's normalised counts of candidate c, this thread's chunks:
+            // tot[8 r + e] holds column 8 (half + H r) + e
+            float tot[8 * CPT];
 #pragma unroll
-            for (int q = 0; q < KH; ++q) tot[q] = 0.f;
+            for (int q = 0; q < 8 * CPT; ++q) tot[q] = 0.f;
             // per-sequence log-likelihoods and (ZOOPS) expected site counts, summed
             // in compensated FP32 (the FP64 pipe is narrow on this part)
             float ll_s = 0.f, ll_c = 0.f, zs_s = 0.f, zs_c = 0.f;
@@ -470,16 +487,19 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
             float o_inv = 0.f;
             auto read_o = [&]() {
 #pragma unroll
-                for (int c8 = 0; c8 < KH; c8 += 8) {
-                    float o[8];
-                    tc::tmem_ld8(tO + lane_base + half * KH + c8, o);
+                for (int r = 0; r < CPT; ++r) {
+                    const int c8 = 8 * (half + H * r);
+                    if (c8 < KP) {
+                        float o[8];
+                        tc::tmem_ld8(tO + lane_base + c8, o);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) tot[c8 + q] += o[q] * o_inv;
+                        for (int q = 0; q < 8; ++q) tot[8 * r + q] += o[q] * o_inv;
+                    }
                 }
                 o_pend = false;
             };
             o_base = o_waited;  // every count MMA of earlier items was waited for
-            TileIt tcur;
+            TileIt<NT> tcur;
             tcur.start(in, item.seq_lo, item.seq_hi);
 
             for (int i = 0; i < n; ++i) {
@@ -496,7 +516,7 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                 if (first) {
                     if (careful) {  // the first tile's exact maximum
                         const float mh = max_half(v, nv);
-                        m = fmaxf(mh, exchange(mh));
+                        m = row_reduce(mh, true);
                     } else {
                         // every score of the row lies in [top - 200, top], so
                         // P = 2^(S - m) stays within [2^-100, 2^100]
@@ -508,11 +528,11 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                 if (careful) {
                     const float bigf = !(add <= 18446744073709551616.f) ? 1.f : 0.f;  // 2^64
                     // both warps of the lane group take the same branch (named barriers)
-                    if (__any_sync(0xffffffffu, fmaxf(bigf, exchange(bigf)) > 0.f)) {
+                    if (__any_sync(0xffffffffu, row_reduce(bigf, true) > 0.f)) {
                         // redo the tile with m raised to its exact maximum
                         tc::tmem_ld32(tS, v);
                         const float mh = max_half(v, nv);
-                        const float tmax = fmaxf(fmaxf(mh, exchange(mh)), m);
+                        const float tmax = fmaxf(row_reduce(mh, true), m);
                         const float sc = ex2(m - tmax);
                         Ssum = s0 * sc;
                         Scmp = c0s * sc;
@@ -521,12 +541,15 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                             wait_o((uint32_t)i);  // O holds every count MMA issued so far
                             tc::fence_after_sync();
 #pragma unroll
-                            for (int c8 = 0; c8 < KH; c8 += 8) {
-                                float o[8];
-                                tc::tmem_ld8(tO + lane_base + half * KH + c8, o);
+                            for (int r = 0; r < CPT; ++r) {
+                                const int c8 = 8 * (half + H * r);
+                                if (c8 < KP) {
+                                    float o[8];
+                                    tc::tmem_ld8(tO + lane_base + c8, o);
 #pragma unroll
-                                for (int q = 0; q < 8; ++q) o[q] *= sc;
-                                tc::tmem_st8(tO + lane_base + half * KH + c8, o);
+                                    for (int q = 0; q < 8; ++q) o[q] *= sc;
+                                    tc::tmem_st8(tO + lane_base + c8, o);
+                                }
                             }
                         }
                         add = exp_half(v, m, nv);
@@ -574,7 +597,7 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                 first = false;
                 if (tcur.last()) {
                     const float Sh = Ssum - Scmp;
-                    const float Sf = Sh + exchange(Sh);
+                    const float Sf = row_reduce(Sh, false);
                     float w = 1.f;  // posterior probability that the sequence holds a site
                     if (zoops) {
                         // ZOOPS: L_i = log[(1 - gamma) + (gamma / ns) sum_j e^r], in FP32
@@ -614,10 +637,14 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                     // FP32 (the counts are FP32 sums; FP64 is a narrow pipe here)
                     const float inv =
                         1.f / (float)((in.gamma < 1.0 ? zs : (double)in.t) + 4.0 * (double)P.beta);
-                    float *dst = P.theta_out + c * P.stride + half * KH;
+                    float *dst = P.theta_out + c * P.stride;
 #pragma unroll
-                    for (int q = 0; q < KH; ++q)
-                        if (half * KH + q < L4) dst[q] = (tot[q] + P.beta) * inv;
+                    for (int r = 0; r < CPT; ++r)
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int col = 8 * (half + H * r) + q;
+                            if (col < L4) dst[col] = (tot[8 * r + q] + P.beta) * inv;
+                        }
                 }
             } else if (ok && valid) {
                 if (half == 0) {
@@ -625,10 +652,14 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
                     P.part_zs[(int64_t)item.g * P.C + c] = zs;
                 }
                 if (P.mstep) {
-                    float *dst = P.part_acc + ((int64_t)item.g * P.C + c) * P.stride + half * KH;
+                    float *dst = P.part_acc + ((int64_t)item.g * P.C + c) * P.stride;
 #pragma unroll
-                    for (int q = 0; q < KH; ++q)
-                        if (half * KH + q < L4) dst[q] = tot[q];
+                    for (int r = 0; r < CPT; ++r)
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int col = 8 * (half + H * r) + q;
+                            if (col < L4) dst[col] = tot[8 * r + q];
+                        }
                 }
             }
         }
@@ -656,7 +687,7 @@ __global__ void __launch_bounds__(kTcThreads, (KP <= 80 ? 2 : 1)) em_tc_kernel(c
             }
             __syncthreads();
             const int width = P.mstep ? L4 : 0;
-            for (int e = tid; e < item.nc * (width + 1); e += kTcThreads) {
+            for (int e = tid; e < item.nc * (width + 1); e += THREADS) {
                 const int cc = e / (width + 1), q = e - cc * (width + 1);
                 const int64_t cg = item.c0 + cc;
                 if (q < width) {
@@ -725,30 +756,30 @@ __global__ void em_tc_reduce_kernel(const float *__restrict__ part_acc,
     }
 }
 
-template <int KP>
+template <int KP, int H>
 int launch_tc(const EmTcParams &P, int grid, cudaStream_t st) {
-    using LY = TcLayout<KP>;
-    PROJ_CUDA_TRY(cudaFuncSetAttribute(em_tc_kernel<KP>,
+    using LY = TcLayout<KP, H>;
+    PROJ_CUDA_TRY(cudaFuncSetAttribute(em_tc_kernel<KP, H>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, LY::TOTAL));
     {
         TraceSpan ts_("em_tc", st);
-        em_tc_kernel<KP><<<grid, kTcThreads, LY::TOTAL, st>>>(P);
+        em_tc_kernel<KP, H><<<grid, tc_threads<H>(), LY::TOTAL, st>>>(P);
     }
     PROJ_LAUNCH_CHECK("em_tc_kernel");
     return PROJ_OK;
 }
 
-template <int KP>
+template <int KP, int H>
 int ctas_per_sm_kp() {
-    using LY = TcLayout<KP>;
+    using LY = TcLayout<KP, H>;
     const int by_tmem = 512 / (int)LY::TMEM_COLS;
     // shared memory: 228 KB per SM, 1 KB reserved per CTA, plus the static part
     int by_smem = 1, by_regs = 1;
     cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, em_tc_kernel<KP>) == cudaSuccess) {
+    if (cudaFuncGetAttributes(&fa, em_tc_kernel<KP, H>) == cudaSuccess) {
         by_smem = 228 * 1024 / (LY::TOTAL + (int)fa.sharedSizeBytes + 1024);
         // registers are granted per pair of warps
-        const int threads = (kTcThreads + 63) / 64 * 64;
+        const int threads = (tc_threads<H>() + 63) / 64 * 64;
         by_regs = 65536 / std::max(1, fa.numRegs * threads);
     } else {
         (void)cudaGetLastError();
@@ -756,48 +787,58 @@ int ctas_per_sm_kp() {
     return std::max(1, std::min(std::min(by_smem, by_regs), by_tmem));
 }
 
-int ctas_per_sm(int kp) {
+template <int H>
+int ctas_per_sm_h(int kp) {
     switch (kp) {
-        case 16: return ctas_per_sm_kp<16>();
-        case 32: return ctas_per_sm_kp<32>();
-        case 48: return ctas_per_sm_kp<48>();
-        case 64: return ctas_per_sm_kp<64>();
-        case 80: return ctas_per_sm_kp<80>();
-        case 96: return ctas_per_sm_kp<96>();
-        case 112: return ctas_per_sm_kp<112>();
-        default: return ctas_per_sm_kp<128>();
+        case 16: return ctas_per_sm_kp<16, H>();
+        case 32: return ctas_per_sm_kp<32, H>();
+        case 48: return ctas_per_sm_kp<48, H>();
+        case 64: return ctas_per_sm_kp<64, H>();
+        case 80: return ctas_per_sm_kp<80, H>();
+        case 96: return ctas_per_sm_kp<96, H>();
+        case 112: return ctas_per_sm_kp<112, H>();
+        default: return ctas_per_sm_kp<128, H>();
     }
 }
 
-int dispatch(int kp, const EmTcParams &P, int grid, cudaStream_t st) {
+int ctas_per_sm(int kp, int h) { return h == 4 ? ctas_per_sm_h<4>(kp) : ctas_per_sm_h<2>(kp); }
+
+template <int H>
+int dispatch_h(int kp, const EmTcParams &P, int grid, cudaStream_t st) {
     switch (kp) {
-        case 16: return launch_tc<16>(P, grid, st);
-        case 32: return launch_tc<32>(P, grid, st);
-        case 48: return launch_tc<48>(P, grid, st);
-        case 64: return launch_tc<64>(P, grid, st);
-        case 80: return launch_tc<80>(P, grid, st);
-        case 96: return launch_tc<96>(P, grid, st);
-        case 112: return launch_tc<112>(P, grid, st);
-        default: return launch_tc<128>(P, grid, st);
+        case 16: return launch_tc<16, H>(P, grid, st);
+        case 32: return launch_tc<32, H>(P, grid, st);
+        case 48: return launch_tc<48, H>(P, grid, st);
+        case 64: return launch_tc<64, H>(P, grid, st);
+        case 80: return launch_tc<80, H>(P, grid, st);
+        case 96: return launch_tc<96, H>(P, grid, st);
+        case 112: return launch_tc<112, H>(P, grid, st);
+        default: return launch_tc<128, H>(P, grid, st);
     }
+}
+
+int dispatch(int kp, int h, const EmTcParams &P, int grid, cudaStream_t st) {
+    return h == 4 ? dispatch_h<4>(kp, P, grid, st) : dispatch_h<2>(kp, P, grid, st);
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Work plan and autotuning.  A schedule is (ctas, waves): CTAs per SM of the
-// persistent grid (<= what shared memory, registers and tensor memory allow)
-// and, when there are fewer candidate tiles than CTA slots, how many rounds of
-// the slots the sequence-group split fills.  The first search of each shape
-// class times one M-step launch of every candidate schedule on its own data
-// and keeps the fastest (per process); PROJ_AUTOTUNE=0 turns this off (default
-// schedule) and PROJ_EM_SCHED="ctas,waves" forces one.
+// Work plan and autotuning.  A schedule is (ctas, waves, h): CTAs per SM of the
+// persistent grid (<= what shared memory, registers and tensor memory allow),
+// when there are fewer candidate tiles than CTA slots how many rounds of the
+// slots the sequence-group split fills, and the kernel's parts per row h (2:
+// tiles of 64 l-mers, 4: tiles of 128).  The first search of each shape class
+// times one M-step launch of every candidate schedule on its own data and keeps
+// the fastest (per process); PROJ_AUTOTUNE=0 turns this off (default schedule)
+// and PROJ_EM_SCHED="ctas,waves[,h]" forces one.
 // ---------------------------------------------------------------------------
 namespace {
 
-struct Sched { int ctas, waves; };
-const Sched kScheds[] = {{2, 1}, {2, 2}, {2, 3}, {2, 4}};
-constexpr Sched kDefaultSched = {2, 1};
+struct Sched { int ctas, waves, h; };
+const Sched kScheds[] = {{2, 1, 2}, {2, 2, 2}, {2, 3, 2}, {2, 4, 2},
+                         {1, 1, 4}, {1, 2, 4}, {1, 3, 4}};
+constexpr Sched kDefaultSched = {2, 1, 2};
 
 std::mutex g_tune_mu;
 std::map<uint64_t, Sched> g_tuned;
@@ -810,46 +851,76 @@ uint64_t shape_key(int kp, int64_t C, int tmin, int64_t lmers) {
            (uint64_t)xb;
 }
 
+// the one-hot tiles (nt rows each) of every sequence of the run
+int build_xtiles(const uint32_t *packed, int64_t nwords, const std::vector<EmInstHost> &insts,
+                 int kp, int nt, DevBuf &xt, DevBuf &xseq, cudaStream_t st) {
+    std::vector<XSeq> xs;
+    int64_t nx = 0;
+    for (const EmInstHost &h : insts)
+        for (int q = 0; q < h.t; ++q) {
+            XSeq v;
+            v.base = h.seq_off[q];
+            v.tile = nx;
+            v.ns = h.seq_off[q + 1] - h.seq_off[q] - h.l + 1;
+            v.l = h.l;
+            xs.push_back(v);
+            nx += (v.ns + nt - 1) / nt;
+        }
+    const size_t xbytes = (size_t)nt * kp * 2;
+    PROJ_TRY(xt.alloc(std::max<int64_t>(1, nx) * xbytes, st));
+    PROJ_TRY(xseq.alloc(xs.size() * sizeof(XSeq), st));
+    PROJ_CUDA_TRY(cudaMemcpyAsync(xseq.as<XSeq>(), xs.data(), xs.size() * sizeof(XSeq),
+                                  cudaMemcpyHostToDevice, st));
+    {
+        TraceSpan ts_("em_xtiles", st);
+        em_xtiles_kernel<<<(unsigned)xs.size(), 256, 0, st>>>(packed, nwords, xseq.as<XSeq>(), kp, nt,
+                                                              xt.as<uint8_t>());
+    }
+    PROJ_LAUNCH_CHECK("em_xtiles_kernel");
+    return PROJ_OK;
+}
+
 }  // namespace
 
 int em_tc_plan(const std::vector<EmInstHost> &insts, std::vector<EmItem> &items, int &G,
-               int ctas, int waves) {
+               int ctas, int waves, int h) {
     // split each instance's candidates into tiles of 128; when there are fewer
     // tiles than CTA slots, split the sequences into G groups so that the items
     // fill `waves` rounds of the slots without a partial round
+    const int nt = kNT * h / 2;
     int kp = 16;
     int64_t tiles = 0;
-    for (const EmInstHost &h : insts) {
-        kp = std::max(kp, 16 * ((4 * h.l + 15) / 16));
-        tiles += (h.C + kTcRows - 1) / kTcRows;
+    for (const EmInstHost &hi : insts) {
+        kp = std::max(kp, 16 * ((4 * hi.l + 15) / 16));
+        tiles += (hi.C + kTcRows - 1) / kTcRows;
     }
-    const int64_t slots = (int64_t)sm_count() * std::min(ctas, ctas_per_sm(kp));
+    const int64_t slots = (int64_t)sm_count() * std::min(ctas, ctas_per_sm(kp, h));
     int tmin = 1 << 30;
-    for (const EmInstHost &h : insts) tmin = std::min(tmin, h.t);
+    for (const EmInstHost &hi : insts) tmin = std::min(tmin, hi.t);
     G = 1;
     if (tiles > 0 && tiles < slots)
         G = (int)std::min<int64_t>(std::max(1, tmin), std::max<int64_t>(1, waves * slots / tiles));
     items.clear();
     int64_t tb = 0;  // one-hot tiles of the earlier instances
     for (size_t ii = 0; ii < insts.size(); ++ii) {
-        const EmInstHost &h = insts[ii];
-        std::vector<int64_t> pre(h.t + 1, 0);  // tiles of the instance's first q sequences
-        for (int q = 0; q < h.t; ++q)
-            pre[q + 1] = pre[q] + (h.seq_off[q + 1] - h.seq_off[q] - h.l + 1 + kNT - 1) / kNT;
-        for (int64_t c0 = 0; c0 < h.C; c0 += kTcRows)
+        const EmInstHost &hi = insts[ii];
+        std::vector<int64_t> pre(hi.t + 1, 0);  // tiles of the instance's first q sequences
+        for (int q = 0; q < hi.t; ++q)
+            pre[q + 1] = pre[q] + (hi.seq_off[q + 1] - hi.seq_off[q] - hi.l + 1 + nt - 1) / nt;
+        for (int64_t c0 = 0; c0 < hi.C; c0 += kTcRows)
             for (int g = 0; g < G; ++g) {
                 EmItem it;
-                it.c0 = h.cand_begin + c0;
-                it.nc = (int)std::min<int64_t>(kTcRows, h.C - c0);
+                it.c0 = hi.cand_begin + c0;
+                it.nc = (int)std::min<int64_t>(kTcRows, hi.C - c0);
                 it.inst = (int)ii;
-                it.seq_lo = (int)((int64_t)h.t * g / G);
-                it.seq_hi = (int)((int64_t)h.t * (g + 1) / G);
+                it.seq_lo = (int)((int64_t)hi.t * g / G);
+                it.seq_hi = (int)((int64_t)hi.t * (g + 1) / G);
                 it.g = g;
                 it.n_tiles = (int)(pre[it.seq_hi] - pre[it.seq_lo]);
                 it.tile0 = tb + pre[it.seq_lo];
                 items.push_back(it);
             }
-        tb += pre[h.t];
+        tb += pre[hi.t];
     }
     return kp;
 }
@@ -885,11 +956,12 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
     }
     const char *env = getenv("PROJ_AUTOTUNE");
     bool tune = !known && !(env && env[0] == '0');
-    // PROJ_EM_SCHED="ctas,waves" forces one schedule (no tuning, no cache)
+    // PROJ_EM_SCHED="ctas,waves[,h]" forces one schedule (no tuning, no cache)
     if (const char *fs = getenv("PROJ_EM_SCHED")) {
-        int c = 0, g = 0;
-        if (sscanf(fs, "%d,%d", &c, &g) == 2 && c >= 1 && c <= 3 && g >= 1 && g <= 8) {
-            sched = {c, g};
+        int c = 0, g = 0, h = 2;
+        const int nf = sscanf(fs, "%d,%d,%d", &c, &g, &h);
+        if (nf >= 2 && c >= 1 && c <= 3 && g >= 1 && g <= 8 && (h == 2 || h == 4)) {
+            sched = {c, g, h};
             tune = false;
         }
     }
@@ -899,12 +971,12 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
     std::vector<EmItem> items;
     for (const Sched &sc : kScheds) {
         int G = 1;
-        em_tc_plan(insts, items, G, sc.ctas, sc.waves);
+        em_tc_plan(insts, items, G, sc.ctas, sc.waves, sc.h);
         Gmax = std::max(Gmax, G);
     }
     {
         int G = 1;
-        em_tc_plan(insts, items, G, sched.ctas, sched.waves);
+        em_tc_plan(insts, items, G, sched.ctas, sched.waves, sched.h);
         Gmax = std::max(Gmax, G);
     }
     // part_ll, part_zs [G][C] double, then part_acc [G][C][stride] float
@@ -918,47 +990,23 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
     PROJ_CUDA_TRY(cudaMemsetAsync(run.tiles.as<uint32_t>(), 0,
                                   (size_t)std::max<int64_t>(1, n_tiles) * sizeof(uint32_t), st));
 
-    // the one-hot tiles of every sequence, built once for all iterations
-    {
-        std::vector<XSeq> xs;
-        int64_t nx = 0;
-        for (const EmInstHost &h : insts)
-            for (int q = 0; q < h.t; ++q) {
-                XSeq v;
-                v.base = h.seq_off[q];
-                v.tile = nx;
-                v.ns = h.seq_off[q + 1] - h.seq_off[q] - h.l + 1;
-                v.l = h.l;
-                xs.push_back(v);
-                nx += (v.ns + kNT - 1) / kNT;
-            }
-        const size_t xbytes = (size_t)kNT * kp * 2;
-        PROJ_TRY(run.xt.alloc(std::max<int64_t>(1, nx) * xbytes, st));
-        PROJ_TRY(run.xseq.alloc(xs.size() * sizeof(XSeq), st));
-        PROJ_CUDA_TRY(cudaMemcpyAsync(run.xseq.as<XSeq>(), xs.data(), xs.size() * sizeof(XSeq),
-                                      cudaMemcpyHostToDevice, st));
-        {
-            TraceSpan ts_("em_xtiles", st);
-            em_xtiles_kernel<<<(unsigned)xs.size(), 256, 0, st>>>(packed, nwords, run.xseq.as<XSeq>(),
-                                                                  kp, run.xt.as<uint8_t>());
-        }
-        PROJ_LAUNCH_CHECK("em_xtiles_kernel");
-    }
-
     if (tune) {
         // time one M-step launch per schedule on this data (the model copy it
-        // updates in place is restored before the real iterations)
+        // updates in place is restored before the real iterations); the one-hot
+        // tiles are built once per tile height
         PROJ_CUDA_TRY(cudaMemcpyAsync(run.tmp.as<float>(), theta0, (size_t)C * stride * sizeof(float),
                                       cudaMemcpyDeviceToDevice, st));
-        DevBuf ll_scratch;
+        DevBuf ll_scratch, xt2, xs2, xt4, xs4;
         PROJ_TRY(ll_scratch.alloc((size_t)C * sizeof(double), st));
+        PROJ_TRY(build_xtiles(packed, nwords, insts, kp, kNT, xt2, xs2, st));
+        PROJ_TRY(build_xtiles(packed, nwords, insts, kp, 2 * kNT, xt4, xs4, st));
         cudaEvent_t e0, e1;
         PROJ_CUDA_TRY(cudaEventCreate(&e0));
         PROJ_CUDA_TRY(cudaEventCreate(&e1));
         float best_ms = 1e30f;
         for (const Sched &sc : kScheds) {
             int G = 1;
-            const int kpp = em_tc_plan(insts, items, G, sc.ctas, sc.waves);
+            const int kpp = em_tc_plan(insts, items, G, sc.ctas, sc.waves, sc.h);
             DevBuf ib;
             PROJ_TRY(ib.alloc(items.size() * sizeof(EmItem), st));
             PROJ_CUDA_TRY(cudaMemcpyAsync(ib.as<EmItem>(), items.data(), items.size() * sizeof(EmItem),
@@ -971,11 +1019,11 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
             P.C = C; P.err = run.flag.as<int>(); P.mstep = 1; P.G = G; P.beta = 0.25f;
             P.theta_out = run.tmp.as<float>(); P.ll_out = ll_scratch.as<double>();
             P.tile_done = run.tiles.as<uint32_t>();
-            P.xt = run.xt.as<uint8_t>();
-            const int grid = (int)std::min<int64_t>((int64_t)items.size(),
-                                                    (int64_t)sm_count() * std::min(sc.ctas, ctas_per_sm(kpp)));
+            P.xt = (sc.h == 4 ? xt4 : xt2).as<uint8_t>();
+            const int grid = (int)std::min<int64_t>(
+                (int64_t)items.size(), (int64_t)sm_count() * std::min(sc.ctas, ctas_per_sm(kpp, sc.h)));
             PROJ_CUDA_TRY(cudaEventRecord(e0, st));
-            PROJ_TRY(dispatch(kpp, P, grid, st));
+            PROJ_TRY(dispatch(kpp, sc.h, P, grid, st));
             if (G > kFoldMaxG) {  // the separate fold is part of this schedule's cost
                 const int64_t nq = C * stride;
                 em_tc_reduce_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(
@@ -995,14 +1043,18 @@ int em_tc_prepare(const uint32_t *packed, int64_t nwords, const std::vector<EmIn
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tuned[key] = sched;
     }
-    run.kp = em_tc_plan(insts, items, run.G, sched.ctas, sched.waves);
+    run.kp = em_tc_plan(insts, items, run.G, sched.ctas, sched.waves, sched.h);
     run.ctas = sched.ctas;
+    run.h = sched.h;
+    // the one-hot tiles of every sequence for the chosen tile height, built once
+    // for all iterations
+    PROJ_TRY(build_xtiles(packed, nwords, insts, kp, kNT * run.h / 2, run.xt, run.xseq, st));
     if (const char *dbg = getenv("PROJ_DEBUG"))
         if (dbg[0] == '1')
-            fprintf(stderr, "[projection] em_tc schedule: KP=%d ctas=%d (fit %d) waves=%d G=%d "
+            fprintf(stderr, "[projection] em_tc schedule: KP=%d ctas=%d (fit %d) waves=%d h=%d G=%d "
                             "items=%zu tuned=%d\n",
-                    run.kp, sched.ctas, ctas_per_sm(run.kp), sched.waves, run.G, items.size(),
-                    (int)tune);
+                    run.kp, sched.ctas, ctas_per_sm(run.kp, run.h), sched.waves, run.h, run.G,
+                    items.size(), (int)tune);
     PROJ_TRY(run.items.alloc(items.size() * sizeof(EmItem), st));
     PROJ_CUDA_TRY(cudaMemcpyAsync(run.items.as<EmItem>(), items.data(), items.size() * sizeof(EmItem),
                                   cudaMemcpyHostToDevice, st));
@@ -1036,11 +1088,11 @@ int em_tc_enqueue(EmTcRun &run, int iters, float beta, float *theta_out, double 
     P.tile_done = run.tiles.as<uint32_t>();
     P.xt = run.xt.as<uint8_t>();
     P.err = run.flag.as<int>();
-    const int grid = (int)std::min<int64_t>((int64_t)run.n_items,
-                                            (int64_t)sm_count() * std::min(run.ctas, ctas_per_sm(run.kp)));
+    const int grid = (int)std::min<int64_t>(
+        (int64_t)run.n_items, (int64_t)sm_count() * std::min(run.ctas, ctas_per_sm(run.kp, run.h)));
     for (int it = 0; it <= iters; ++it) {
         P.mstep = it < iters;
-        PROJ_TRY(dispatch(run.kp, P, grid, st));
+        PROJ_TRY(dispatch(run.kp, run.h, P, grid, st));
         if (G > kFoldMaxG) {
             const int64_t n = P.mstep ? C * stride : C;
             {

@@ -53,8 +53,12 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("h", [2, 4])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_em_bf16_split_matches_oracle(P, name):
+def test_em_bf16_split_matches_oracle(P, name, h, monkeypatch):
+    """Both kernel shapes: h = 2 (tiles of 64 l-mers, two CTAs per SM) and h = 4
+    (tiles of 128 l-mers, four threads per candidate row, one CTA per SM)."""
+    monkeypatch.setenv("PROJ_EM_SCHED", f"{2 if h == 2 else 1},1,{h}")
     make, k, s, n, iters = CASES[name]
     inst = make()
     codes = O.encode(inst.ascii)
@@ -130,7 +134,8 @@ def _peaked_models(rng, inst, n_peaked, n_flat, hi=0.997):
     return th.astype(np.float32)
 
 
-def test_em_bf16_split_careful_rows(P):
+@pytest.mark.parametrize("h", [2, 4])
+def test_em_bf16_split_careful_rows(P, h, monkeypatch):
     """Rows whose score range sum_p (max_a W - min_a W) exceeds 200 (log2 units)
     switch their CTA to careful mode: exact first-tile maxima and a per-tile
     overflow check with rescaling.  Peaked models (0.997 / 0.001 per column,
@@ -140,6 +145,7 @@ def test_em_bf16_split_careful_rows(P):
     the planted-workload one for a ~3x margin (the BF16-split score error bound
     2^-16 sum_p |W_p| grows with the range).  A wrong rescale would be off by
     powers of two or non-finite."""
+    monkeypatch.setenv("PROJ_EM_SCHED", f"{2 if h == 2 else 1},1,{h}")
     inst = planted_instance(21, 0, 20, 400, 24, 4)
     rng = np.random.default_rng(5)
     th0 = _peaked_models(rng, inst, 100, 60)

@@ -88,10 +88,11 @@ def test_graph_reuse_across_shapes(P):
     assert got[2]["l"] == 15 and len(got[2]["consensus"]) == 15
 
 
-@pytest.mark.parametrize("sched", ["2,1", "2,2", "2,3", "2,4", "1,1", "1,4"])
+@pytest.mark.parametrize("sched", ["2,1", "2,2", "2,3", "2,4", "1,1", "1,4", "1,1,4", "1,2,4",
+                                   "1,3,4"])
 def test_every_em_schedule_matches_oracle(P, sched, monkeypatch):
     """Each schedule (CTAs per SM, rounds of CTA slots filled by the sequence
-    groups) splits the work differently; each must stay within the BF16-split
+    groups, and the kernel's 64- or 128-l-mer tiles) splits the work differently; each must stay within the BF16-split
     tolerances of the FP64 oracle."""
     import oracle as O
     from synth import planted_instance
