@@ -12,18 +12,19 @@
 // range of its sequences); a CTA (128 candidate rows = the 128 lanes of tensor
 // memory) takes items in turn from the list (persistent over the list when the
 // grid is smaller than it), so one launch serves one motif search or a batch of
-// many instances of different t, n and l.  Per tile of 64 l-mers of a sequence:
-//   1. one thread copies the one-hot tile X [64 x 4l] into shared memory with a
+// many instances of different t, n and l.  Per tile of NT l-mers of a sequence
+// (NT = 64, or 128 in the four-parts-per-row form of the kernel):
+//   1. one thread copies the one-hot tile X [NT x 4l] into shared memory with a
 //      bulk asynchronous copy (the tiles depend only on the sequences and are
 //      built once per EM run, in the MMA operand layout, by em_xtiles_kernel);
-//   2. one thread issues S = W_hi X^T + W_lo X^T (M=128, N=64, K=16*ceil(4l/16),
+//   2. one thread issues S = W_hi X^T + W_lo X^T (M=128, N=NT, K=16*ceil(4l/16),
 //      FP32 accumulation in tensor memory; W split into BF16 hi + lo parts so
 //      the product carries ~16 mantissa bits of W);
-//   3. the two threads of row i read its scores S, add 2^(S - m) to a
+//   3. the threads of row i (32 l-mers each) read its scores S, add 2^(S - m) to a
 //      compensated running sum for the candidate (m a reference maximum, see
 //      below) and write P = 2^(S - m) as BF16 hi + lo parts over their own
 //      columns of S in tensor memory;
-//   4. one thread issues O += P_hi X + P_lo X (M=128, N=16*ceil(4l/16), K=64)
+//   4. one thread issues O += P_hi X + P_lo X (M=128, N=16*ceil(4l/16), K=NT)
 //      with P read from tensor memory and X in MN-major form from the same
 //      shared-memory tile.
 // The steps of consecutive tiles overlap (two score buffers in tensor memory,
@@ -233,13 +234,14 @@ __device__ __forceinline__ float max_half(const float (&v)[32], int nv) {
     return mx[0];
 }
 
-// The CTA has 288 threads.  Warps 0-7 compute the softmax: warps w and w + 4
-// share the tensor-memory lanes 32*(w%4) .. +31 (candidate rows), warp w
-// taking the first 32 l-mers of each tile and warp w + 4 the last 32; the two
-// threads of a row share one reference maximum m, keep their own compensated
-// sums (added together through shared memory at a sequence end), and each
-// reads and accumulates half of the row's count columns.  Warp 8 issues the
-// MMAs (one elected thread), so issuing never stalls the softmax warps.
+// The CTA has 128 H + 32 threads (H = 2: 288, two CTAs per SM; H = 4: 544, one
+// CTA per SM).  Warps 0 .. 4H-1 compute the softmax: warps w, w + 4, ... share
+// the tensor-memory lanes 32*(w%4) .. +31 (candidate rows), warp w taking
+// l-mers 32*(w/4) .. +31 of each tile; the H threads of a row share one
+// reference maximum m, keep their own compensated sums (added together through
+// shared memory at a sequence end), and each reads and accumulates the 8-column
+// chunks h, h + H, ... of the row's count columns.  Warp 4H issues the MMAs
+// (one elected thread), so issuing never stalls the softmax warps.
 //
 // Pipeline over the tiles j = 0 .. n-1 of an item, linked by mbarriers:
 //   issuer: S(0), S(1); then per j: [P(j) written] O (+)= P X(j);
@@ -258,8 +260,8 @@ __device__ __forceinline__ float max_half(const float (&v)[32], int nv) {
 // - min_a W) is <= 200 every score lies in [top - 200, top], so every P is in
 // [2^-100, 2^100]: nothing overflows or leaves the normal FP32 (and BF16)
 // range.  Rows with a wider range (careful mode, CTA-wide) use the exact
-// maximum of each sequence's first tile and the two threads of a row compare
-// every tile: if a half-tile sum exceeds 2^64 (or is not finite) m is raised to
+// maximum of each sequence's first tile and the threads of a row compare
+// every tile: if a part's sum exceeds 2^64 (or is not finite) m is raised to
 // the tile's exact maximum, the row's sums and O are rescaled and the tile
 // recomputed.
 template <int KP, int H>
