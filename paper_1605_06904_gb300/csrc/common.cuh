@@ -102,6 +102,7 @@ int launch_positions(uint64_t seed, int64_t trial_begin, int64_t n_trials, int l
 struct HashState {
     DevBuf meta, part_buf;
     DevBuf emit_buf;     // the counting pass's per-unit enriched (key, size) lists
+    DevBuf pos_buf;      // every trial's projected positions [n_trials][k]
     bool valid = false;
     bool emitted = false;  // emit_buf holds the lists (counting call had want_emit)
     // what the member gather of selected buckets needs from the counting call
@@ -110,6 +111,7 @@ struct HashState {
     const uint16_t *prel = nullptr;    // partitioned mode: keys grouped by part per chunk
     const uint16_t *plid = nullptr;    //                   chunk-local l-mer ids
     const int32_t *pstart = nullptr;   //                   part starts per (trial, chunk)
+    const uint8_t *pos_tab = nullptr;  // positions of the call's trials (null: drawn in-kernel)
 };
 
 struct HashOut {

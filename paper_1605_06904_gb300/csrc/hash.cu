@@ -50,6 +50,8 @@ struct HashParams {
     int stage_words;          // packed words staged in smem (0 = read global)
     int fixed_pos;            // positions given by the caller
     int pos_in[16];
+    const uint8_t *pos_tab;   // [n_trials][k] positions drawn once for the call, or null
+                              // (each CTA draws its trial's positions)
     uint8_t *pos_out;
     uint32_t *counts_out;
     // pass 1 outputs
@@ -182,6 +184,22 @@ __device__ inline void unit_walk_setup(const HashParams &P, int trial_local, int
 
 // One (trial, key-range part) unit of the bucket kernels; `unit` indexes the
 // per-unit arrays of P (part_nb, part_nm, cand_base, mem_base).
+// Projected positions of trial trial_local (Algorithm 2 step 2a) into s_pos;
+// the caller synchronises before reading them.  From the call's table when
+// there is one, else the caller's fixed positions or a draw by thread 0.
+__device__ __forceinline__ void trial_positions(const HashParams &P, int trial_local, int *s_pos) {
+    if (P.pos_tab) {
+        if ((int)threadIdx.x < P.k)
+            s_pos[threadIdx.x] = P.pos_tab[(int64_t)trial_local * P.k + threadIdx.x];
+    } else if (threadIdx.x == 0) {
+        if (P.fixed_pos) {
+            for (int q = 0; q < P.k; ++q) s_pos[q] = P.pos_in[q];
+        } else {
+            draw_positions(P.seed, (uint64_t)(P.trial_begin + trial_local), P.l, P.k, s_pos);
+        }
+    }
+}
+
 template <bool FILL, int K>
 __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, uint8_t *smem,
                                           int *s_pos, int2 *s_warp, int *s_round) {
@@ -206,15 +224,7 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     const uint32_t hb = (uint32_t)P.hb;
 
     // projection positions of this trial (Algorithm 2 step 2a)
-    if (tid == 0) {
-        if (P.fixed_pos) {
-            for (int q = 0; q < P.k; ++q) s_pos[q] = P.pos_in[q];
-        } else {
-            draw_positions(P.seed, trial, P.l, P.k, s_pos);
-        }
-        if (!FILL && P.pos_out && part == 0)
-            for (int q = 0; q < P.k; ++q) P.pos_out[(int64_t)trial_local * P.k + q] = (uint8_t)s_pos[q];
-    }
+    trial_positions(P, trial_local, s_pos);
     if (!P.partitioned)
         for (int i = tid; i <= P.t; i += kThreads) {
             s_seq[i] = P.seq_off[i];
@@ -242,6 +252,8 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     if (FILL)
         for (int w = tid; w < S.bitmap_bytes / 4; w += kThreads) bitmap[w] = 0u;
     __syncthreads();
+    if (!FILL && P.pos_out && part == 0 && tid < P.k)
+        P.pos_out[(int64_t)trial_local * P.k + tid] = (uint8_t)s_pos[tid];
     if (P.partitioned) unit_walk_setup(P, trial_local, part, s_cb, s_pb, s_warp);
 
     int pos[16];
@@ -501,13 +513,7 @@ constexpr int kStageSeqs = (kSortChunk - kStageWords - 2) / 2 - 1;
 constexpr int kSortSmem = 2 * kSortChunk * 4;
 
 __device__ __forceinline__ void part_setup(const HashParams &P, int trial_local, int *s_pos) {
-    if (threadIdx.x == 0) {
-        if (P.fixed_pos) {
-            for (int q = 0; q < P.k; ++q) s_pos[q] = P.pos_in[q];
-        } else {
-            draw_positions(P.seed, (uint64_t)(P.trial_begin + trial_local), P.l, P.k, s_pos);
-        }
-    }
+    trial_positions(P, trial_local, s_pos);
     __syncthreads();
 }
 
@@ -839,13 +845,7 @@ __global__ void __launch_bounds__(kThreads) gather_sel_kernel(
         n_iter = s_cb[P.n_chunks];
     } else {
         n_iter = P.x;
-        if (tid == 0) {
-            if (P.fixed_pos) {
-                for (int q = 0; q < P.k; ++q) s_pos[q] = P.pos_in[q];
-            } else {
-                draw_positions(P.seed, (uint64_t)(P.trial_begin + trial_local), P.l, P.k, s_pos);
-            }
-        }
+        trial_positions(P, trial_local, s_pos);
         __syncthreads();
     }
     int pos[16];
@@ -964,6 +964,17 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
     }
     PROJ_REQUIRE(n_units < (int64_t)1 << 31, "too many (trial, part) units");
     const bool reuse = out.state && out.state->valid;
+    // every trial's positions drawn once for all of this call's kernels (and the
+    // filling call and member gather of the same search)
+    DevBuf pos_own;  // freed (stream-ordered) after this call's launches
+    if (!P.fixed_pos) {
+        DevBuf &pos_buf = out.state ? out.state->pos_buf : pos_own;
+        if (!reuse) {
+            PROJ_TRY(pos_buf.alloc((size_t)n_trials * k, st));
+            PROJ_TRY(launch_positions(seed, trial_begin, n_trials, L.l, k, pos_buf.as<uint8_t>(), st));
+        }
+        P.pos_tab = pos_buf.as<uint8_t>();
+    }
     DevBuf meta_own, part_own;
     DevBuf &meta = out.state ? out.state->meta : meta_own;
     DevBuf &part_buf = out.state ? out.state->part_buf : part_own;
@@ -1022,6 +1033,7 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
         hs->prel = P.prel;
         hs->plid = P.plid;
         hs->pstart = P.pstart;
+        hs->pos_tab = P.pos_tab;
     }
     if (!reuse) {
         {
@@ -1096,6 +1108,7 @@ int run_gather_members(const uint32_t *packed, const Layout &L, const HashState 
     P.parts = hs.parts;
     P.hb = hs.hb;
     P.n_chunks = hs.n_chunks;
+    P.pos_tab = hs.pos_tab;
     int smem = 0;
     if (hs.partitioned) {
         P.partitioned = 1;
