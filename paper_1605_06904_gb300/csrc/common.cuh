@@ -107,6 +107,7 @@ struct HashState {
     bool emitted = false;  // emit_buf holds the lists (counting call had want_emit)
     // what the member gather of selected buckets needs from the counting call
     int parts = 1, hb = 0, n_chunks = 0;
+    int nt = 0;                      // threads per bucket-kernel CTA chosen by the counting call
     bool partitioned = false;
     const uint16_t *prel = nullptr;    // partitioned mode: keys grouped by part per chunk
     const uint16_t *plid = nullptr;    //                   chunk-local l-mer ids

@@ -19,7 +19,10 @@
 // (block-wide ballot scan), and places each one at its bucket's cursor with a
 // single warp walking that list (match_any ranks equal keys within a step), so
 // members come out ascending within every bucket.
+#include <stdlib.h>
+
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -128,8 +131,10 @@ __device__ __forceinline__ uint32_t lmer_key_k(uint64_t win, const int *pos, int
 }
 
 // Block-wide exclusive scan of two ints; returns the prefixes and the totals.
+template <int NT = kThreads>
 __device__ inline void block_scan2(int a, int b, int &pa, int &pb, int &ta, int &tb,
                                    int2 *warp_tot) {
+    constexpr int kWarps = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int ia = a, ib = b;
 #pragma unroll
@@ -163,6 +168,7 @@ __device__ inline void block_scan2(int a, int b, int &pa, int &pb, int &ta, int 
 // Partitioned mode: the pieces of unit (trial, part) in chunk order.  Piece c
 // holds the unit's flat entries [cb[c], cb[c+1]), entry f of it at
 // prel/plid[pb[c] + f].  Ends with a CTA barrier.
+template <int NT = kThreads>
 __device__ inline void unit_walk_setup(const HashParams &P, int trial_local, int part,
                                        int32_t *cb, long long *pb, int2 *s_warp) {
     const int per = (P.n_chunks + (int)blockDim.x - 1) / (int)blockDim.x;
@@ -171,7 +177,7 @@ __device__ inline void unit_walk_setup(const HashParams &P, int trial_local, int
     int sum = 0;
     for (int c = c0; c < c1; ++c) sum += ps[c * (P.parts + 1) + part + 1] - ps[c * (P.parts + 1) + part];
     int pre, pz, tot, tz;
-    block_scan2(sum, 0, pre, pz, tot, tz, s_warp);
+    block_scan2<NT>(sum, 0, pre, pz, tot, tz, s_warp);
     for (int c = c0; c < c1; ++c) {
         const int a = ps[c * (P.parts + 1) + part];
         cb[c] = pre;
@@ -200,9 +206,10 @@ __device__ __forceinline__ void trial_positions(const HashParams &P, int trial_l
     }
 }
 
-template <bool FILL, int K>
+template <bool FILL, int K, int NT = kThreads>
 __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, uint8_t *smem,
                                           int *s_pos, int2 *s_warp, int *s_round) {
+    constexpr int kThreads = NT, kWarps = NT / 32;  // this CTA's size
 
     const SmemLayout S = smem_layout(P, FILL);
     uint32_t *hist32 = reinterpret_cast<uint32_t *>(smem);
@@ -254,7 +261,7 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     __syncthreads();
     if (!FILL && P.pos_out && part == 0 && tid < P.k)
         P.pos_out[(int64_t)trial_local * P.k + tid] = (uint8_t)s_pos[tid];
-    if (P.partitioned) unit_walk_setup(P, trial_local, part, s_cb, s_pb, s_warp);
+    if (P.partitioned) unit_walk_setup<NT>(P, trial_local, part, s_cb, s_pb, s_warp);
 
     int pos[16];
 #pragma unroll
@@ -318,7 +325,7 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
         nm += __shfl_xor_sync(0xffffffffu, nm, o);
     }
     int rb, rm, NB, NM;  // this warp's first enriched bucket and member offset; unit totals
-    block_scan2(lane == 0 ? nb : 0, lane == 0 ? nm : 0, rb, rm, NB, NM, s_warp);
+    block_scan2<NT>(lane == 0 ? nb : 0, lane == 0 ? nm : 0, rb, rm, NB, NM, s_warp);
     rb = __shfl_sync(0xffffffffu, rb, 0);
     rm = __shfl_sync(0xffffffffu, rm, 0);
 
@@ -461,13 +468,13 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     }
 }
 
-template <bool FILL, int K>
-__global__ void __launch_bounds__(kThreads, 1) hash_kernel(const HashParams P) {
+template <bool FILL, int K, int NT>
+__global__ void __launch_bounds__(NT, kThreads / NT) hash_kernel(const HashParams P) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_pos[16];
-    __shared__ int2 s_warp[kWarps + 1];
-    __shared__ int s_round[kWarps + 1];
-    hash_unit<FILL, K>(P, (int)blockIdx.x, smem, s_pos, s_warp, s_round);
+    __shared__ int2 s_warp[NT / 32 + 1];
+    __shared__ int s_round[NT / 32 + 1];
+    hash_unit<FILL, K, NT>(P, (int)blockIdx.x, smem, s_pos, s_warp, s_round);
 }
 
 // Many instances in one launch: block u runs unit u - unit_begin[i] of the
@@ -727,27 +734,34 @@ __global__ void cand_end_kernel(const int64_t *__restrict__ totals, int64_t cap_
 
 // Launches of the bucket kernels specialised on k.
 template <bool FILL, int K>
-int launch_hash_k(const HashParams &P, unsigned grid, int smem, cudaStream_t st) {
-    PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<FILL, K>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
-    hash_kernel<FILL, K><<<grid, kThreads, smem, st>>>(P);
+int launch_hash_k(const HashParams &P, unsigned grid, int smem, int nt, cudaStream_t st) {
+    if (nt == 512) {
+        PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<FILL, K, 512>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        hash_kernel<FILL, K, 512><<<grid, 512, smem, st>>>(P);
+    } else {
+        PROJ_CUDA_TRY(cudaFuncSetAttribute(hash_kernel<FILL, K, kThreads>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        hash_kernel<FILL, K, kThreads><<<grid, kThreads, smem, st>>>(P);
+    }
     PROJ_LAUNCH_CHECK(FILL ? "hash_kernel<fill>" : "hash_kernel<count>");
     return PROJ_OK;
 }
 
+// nt: threads per CTA (1024, or 512 so that two or three units share an SM)
 template <bool FILL>
-int launch_hash(const HashParams &P, unsigned grid, int smem, cudaStream_t st) {
+int launch_hash(const HashParams &P, unsigned grid, int smem, cudaStream_t st, int nt = kThreads) {
     switch (P.k) {
-        case 1: return launch_hash_k<FILL, 1>(P, grid, smem, st);
-        case 2: return launch_hash_k<FILL, 2>(P, grid, smem, st);
-        case 3: return launch_hash_k<FILL, 3>(P, grid, smem, st);
-        case 4: return launch_hash_k<FILL, 4>(P, grid, smem, st);
-        case 5: return launch_hash_k<FILL, 5>(P, grid, smem, st);
-        case 6: return launch_hash_k<FILL, 6>(P, grid, smem, st);
-        case 7: return launch_hash_k<FILL, 7>(P, grid, smem, st);
-        case 8: return launch_hash_k<FILL, 8>(P, grid, smem, st);
-        case 9: return launch_hash_k<FILL, 9>(P, grid, smem, st);
-        default: return launch_hash_k<FILL, 10>(P, grid, smem, st);
+        case 1: return launch_hash_k<FILL, 1>(P, grid, smem, nt, st);
+        case 2: return launch_hash_k<FILL, 2>(P, grid, smem, nt, st);
+        case 3: return launch_hash_k<FILL, 3>(P, grid, smem, nt, st);
+        case 4: return launch_hash_k<FILL, 4>(P, grid, smem, nt, st);
+        case 5: return launch_hash_k<FILL, 5>(P, grid, smem, nt, st);
+        case 6: return launch_hash_k<FILL, 6>(P, grid, smem, nt, st);
+        case 7: return launch_hash_k<FILL, 7>(P, grid, smem, nt, st);
+        case 8: return launch_hash_k<FILL, 8>(P, grid, smem, nt, st);
+        case 9: return launch_hash_k<FILL, 9>(P, grid, smem, nt, st);
+        default: return launch_hash_k<FILL, 10>(P, grid, smem, nt, st);
     }
 }
 
@@ -893,6 +907,39 @@ __global__ void __launch_bounds__(kThreads) gather_sel_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------
+// Hash-tile autotuning: the bucket kernels run as 1024-thread CTAs or, when a
+// unit's shared memory lets several share an SM, as 512-thread CTAs.  The first
+// search of each shape class (k, counter layout, parts, ceil(log2) of l-mers and
+// of units, sequences) times its counting pass both ways on its own data (the
+// pass is idempotent) and keeps the faster for both passes (per process);
+// PROJ_AUTOTUNE=0 keeps 1024 and PROJ_HASH_NT=512|1024 forces one.
+// ---------------------------------------------------------------------------
+std::mutex g_hash_tune_mu;
+std::map<uint64_t, int> g_hash_tuned;
+
+uint64_t hash_shape_key(const HashParams &P, int64_t n_units) {
+    int xb = 0, ub = 0;
+    while (((int64_t)1 << xb) < (int64_t)P.x) ++xb;
+    while (((int64_t)1 << ub) < n_units) ++ub;
+    return ((uint64_t)P.k << 56) | ((uint64_t)P.hist16 << 55) | ((uint64_t)P.parts << 48) |
+           ((uint64_t)xb << 40) | ((uint64_t)ub << 32) | (uint64_t)std::min(P.t, 1 << 20);
+}
+
+// 0 = not decided (tune), else the CTA size to use
+int hash_nt_choice(const HashParams &P, int64_t n_units, int fill_smem) {
+    if (P.partitioned || fill_smem > 113 * 1024) return kThreads;  // one unit per SM anyway
+    if (const char *f = getenv("PROJ_HASH_NT")) {
+        const int v = atoi(f);
+        if (v == 512 || v == 1024) return v;
+    }
+    const char *env = getenv("PROJ_AUTOTUNE");
+    if (env && env[0] == '0') return kThreads;
+    std::lock_guard<std::mutex> lk(g_hash_tune_mu);
+    auto it = g_hash_tuned.find(hash_shape_key(P, n_units));
+    return it == g_hash_tuned.end() ? 0 : it->second;
+}
+
 }  // namespace
 
 int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64_t seed,
@@ -1027,6 +1074,7 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
     }
     if (hs) {
         hs->parts = P.parts;
+        if (!reuse) hs->nt = 0;  // set once the counting pass has chosen
         hs->hb = P.hb;
         hs->n_chunks = P.n_chunks;
         hs->partitioned = partitioned;
@@ -1035,10 +1083,32 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
         hs->pstart = P.pstart;
         hs->pos_tab = P.pos_tab;
     }
+    int nt = hs && reuse ? hs->nt : hash_nt_choice(P, n_units, S2.total);
+    if (nt == 0 && !hs) nt = kThreads;  // plain calls do not synchronise to tune
     if (!reuse) {
-        {
+        if (nt == 0) {
+            // time the (idempotent) counting pass with both CTA sizes, keep the faster
+            cudaEvent_t e[3];
+            for (int q = 0; q < 3; ++q) PROJ_CUDA_TRY(cudaEventCreate(&e[q]));
+            PROJ_CUDA_TRY(cudaEventRecord(e[0], st));
+            {
+                TraceSpan ts_("hash_count", st);
+                PROJ_TRY(launch_hash<false>(P, (unsigned)n_units, S1.total, st, kThreads));
+            }
+            PROJ_CUDA_TRY(cudaEventRecord(e[1], st));
+            PROJ_TRY(launch_hash<false>(P, (unsigned)n_units, S1.total, st, 512));
+            PROJ_CUDA_TRY(cudaEventRecord(e[2], st));
+            PROJ_CUDA_TRY(cudaEventSynchronize(e[2]));
+            float t1024 = 0.f, t512 = 0.f;
+            PROJ_CUDA_TRY(cudaEventElapsedTime(&t1024, e[0], e[1]));
+            PROJ_CUDA_TRY(cudaEventElapsedTime(&t512, e[1], e[2]));
+            for (int q = 0; q < 3; ++q) cudaEventDestroy(e[q]);
+            nt = t512 < 0.97f * t1024 ? 512 : kThreads;
+            std::lock_guard<std::mutex> lk(g_hash_tune_mu);
+            g_hash_tuned[hash_shape_key(P, n_units)] = nt;
+        } else {
             TraceSpan ts_("hash_count", st);
-            PROJ_TRY(launch_hash<false>(P, (unsigned)n_units, S1.total, st));
+            PROJ_TRY(launch_hash<false>(P, (unsigned)n_units, S1.total, st, nt));
         }
         {
             TraceSpan ts_("hash_scan", st);
@@ -1051,6 +1121,7 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
         cand_end_kernel<<<1, 1, 0, st>>>(out.totals, out.cap_cand, out.cand_off);
         PROJ_LAUNCH_CHECK("cand_end_kernel");
     }
+    if (hs) hs->nt = nt;  // the filling call of this search uses the same CTA size
     if (out.count_only) {
         if (out.state) out.state->valid = true;
         return PROJ_OK;
@@ -1086,7 +1157,7 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
     P.pos_out = nullptr;
     {
         TraceSpan ts_("hash_fill", st);
-        PROJ_TRY(launch_hash<true>(P, (unsigned)n_units, S2.total, st));
+        PROJ_TRY(launch_hash<true>(P, (unsigned)n_units, S2.total, st, nt));
     }
     return PROJ_OK;
 }

@@ -124,9 +124,13 @@ def test_worked_example_bucket(P, fig1):
     assert np.array_equal(h["counts"].cpu().numpy().view(np.uint32), want["counts"])
 
 
+@pytest.mark.parametrize("nt", [1024, 512])
 @pytest.mark.parametrize("cfg,trials", [(1, (0, 100)), (2, (0, 172)), (3, (0, 150)),
                                         (3, (1850, 150)), (5, (0, 3)), (5, (497, 3))])
-def test_hash_configs_bit_exact(P, cfg, trials):
+def test_hash_configs_bit_exact(P, cfg, trials, nt, monkeypatch):
+    """Both CTA sizes of the bucket kernels (the hash-tile autotuner's choices;
+    the serving-scale input keeps 1024, its units need a whole SM)."""
+    monkeypatch.setenv("PROJ_HASH_NT", str(nt))
     inst = instance_for_config(cfg)
     prm = inst.params
     codes, off = inst_arrays(inst)
@@ -166,7 +170,9 @@ def _random_case(seed, t, nmin, nmax, alphabet=b"ACGT"):
     dict(seed=10, t=4, nmin=100000, nmax=100000, l=12, k=8, s=4),  # input not staged in smem
     dict(seed=11, t=12, nmin=40, nmax=200, l=32, k=10, s=2),  # l = 32
 ])
-def test_hash_edge_cases_bit_exact(P, case):
+@pytest.mark.parametrize("nt", [1024, 512])
+def test_hash_edge_cases_bit_exact(P, case, nt, monkeypatch):
+    monkeypatch.setenv("PROJ_HASH_NT", str(nt))
     ascii_, off = _random_case(case["seed"], case["t"], case["nmin"], case["nmax"])
     l, k, s = case["l"], case["k"], case["s"]
     codes = O.encode(ascii_)
@@ -413,3 +419,18 @@ def test_em_refine_zoops_sites_of_every_candidate(P):
     obg = O.background(codes)
     for c in range(th.shape[0]):
         assert np.array_equal(st[c], O.sites(codes, inst.seq_off, inst.l, obg, th[c])), c
+
+
+@pytest.mark.parametrize("nt", ["1024", "512"])
+def test_find_with_each_hash_cta_size(P, nt, monkeypatch):
+    """A whole search with each bucket-kernel CTA size gives the same result."""
+    monkeypatch.setenv("PROJ_HASH_NT", nt)
+    inst = instance_for_config(1)
+    prm = inst.params
+    r = P.projection_find(inst.ascii, inst.seq_off, inst.l, inst.d, prm["k"], prm["s"], 30,
+                          seed=5, em_iters=3, pseudocount=0.25)
+    monkeypatch.setenv("PROJ_HASH_NT", "1024")
+    q = P.projection_find(inst.ascii, inst.seq_off, inst.l, inst.d, prm["k"], prm["s"], 30,
+                          seed=5, em_iters=3, pseudocount=0.25)
+    for key in ("n_candidates", "n_members", "win_index", "consensus", "loglik", "score"):
+        assert r[key] == q[key], key
