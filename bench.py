@@ -381,20 +381,35 @@ def em_roofline(P, cfg, inst, R, iters, steps, em_ms, em_launches, pk, pk_kind):
                           "peak_source": "projection_ex2_peak() measured in this run"}}
 
 
-def hash_roofline(P, k, m, x, steps, phases):
+def hash_roofline(P, k, m, x, steps, phases, pk=None, pk_kind=None):
     """The bucket-counting pass against the shared-memory histogram rate, and
-    the whole hashing phase's time."""
+    the whole hashing phase's time.  With a key-range partition (phase
+    `hash_partition` present), also the partition and counting passes' HBM
+    bytes as implemented (4 B per (trial, l-mer) written by the partition, the
+    2-byte keys read back by the counting pass) against the measured HBM
+    bandwidth: the hashing phase's memory roofline."""
     hc_ms, hc_launches = P.projection_trace_read("hash_count")
     hist_peak = P.projection_hist_peak(k)
     rate = m * x * steps / (hc_ms / 1e3) if hc_ms > 0 else None
-    return {"kernel": "hash_kernel<count>", "bound": "smem_atomic", "achieved": rate,
-            "peak": hist_peak, "unit": "updates/s", "frac": rate / hist_peak if rate else None,
-            "avg_launch_ms": hc_ms / max(1, hc_launches),
-            "hash_phase_ms_per_step": sum(phases.get(n, 0.0) for n in
-                                          ("hash_partition", "hash_count", "hash_scan",
-                                           "hash_fill", "hash_table", "select", "hash_gather",
-                                           "positions")),
-            "peak_source": f"projection_hist_peak({k}) measured in this run"}
+    out = {"kernel": "hash_kernel<count>", "bound": "smem_atomic", "achieved": rate,
+           "peak": hist_peak, "unit": "updates/s", "frac": rate / hist_peak if rate else None,
+           "avg_launch_ms": hc_ms / max(1, hc_launches),
+           "hash_phase_ms_per_step": sum(phases.get(n, 0.0) for n in
+                                         ("hash_partition", "hash_count", "hash_scan",
+                                          "hash_fill", "hash_table", "select", "hash_gather",
+                                          "positions")),
+           "peak_source": f"projection_hist_peak({k}) measured in this run"}
+    part_ms = phases.get("hash_partition", 0.0) + phases.get("hash_count", 0.0)
+    if phases.get("hash_partition") and pk:
+        nbytes = m * x * (4 + 2)
+        gbs = nbytes / (part_ms / 1e3) / 1e9
+        out["partition_hbm"] = {"bound": "hbm", "bytes_per_step": nbytes,
+                                "ms_per_step": part_ms, "achieved": gbs,
+                                "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                                "frac": gbs / pk["hbm_gbs"] if pk.get("hbm_gbs") else None,
+                                "peak_source": f"hbm_gbs ({pk_kind})",
+                                "note": "partition writes + counting-pass reads, as implemented"}
+    return out
 
 
 def measure_search(P, cfg, inst, packed, k, s, m, seed, iters, beta, top, steps, warmup, flush,
@@ -460,7 +475,7 @@ def sub_workload(P, cfg, dev, stream, flush, steps, pk, pk_kind, with_extras=Fal
                res["n_candidates"], "n_refined": R, "ms_per_step_by_phase": r["phases"],
            "gpu_launches": r["launches"],
            "roofline": em_roofline(P, cfg, inst, R, iters, steps, em_ms, em_launches, pk, pk_kind),
-           "hash_roofline": hash_roofline(P, k, m, inst.n_lmers, steps, r["phases"]),
+           "hash_roofline": hash_roofline(P, k, m, inst.n_lmers, steps, r["phases"], pk, pk_kind),
            "motif_found": res["consensus"], "motif_planted": inst.motif,
            "planted_recovered": res["consensus"] == inst.motif,
            "errors_vs_fp64_oracle": em_error_report(P, inst, packed, k, s, seed, iters, beta, dev,
@@ -745,7 +760,7 @@ def main():
                 "note": "the FP32 path is bound by shared-memory gathers; timed for comparison"}
     else:
         roof = em_roofline(P, cfg, inst, R, iters, args.steps, em_ms, em_launches, pk, pk_kind)
-    hroof = hash_roofline(P, k, m, x, args.steps, r["phases"])
+    hroof = hash_roofline(P, k, m, x, args.steps, r["phases"], pk, pk_kind)
     dominant = max((v, n) for n, v in r["phases"].items() if n != "all_kernels")[1]
 
     # ---- end to end through the public API: host ASCII in, result out
