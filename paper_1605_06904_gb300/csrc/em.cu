@@ -58,6 +58,58 @@ __global__ void theta0_kernel(const uint32_t *__restrict__ packed, int64_t nword
     for (int q = 0; q < L4; ++q) theta0[c * L4 + q] = (cnt[q * nt + tid] + beta) / den;
 }
 
+// theta0 with one warp per candidate, for searches that keep a few large
+// buckets: the lanes split the bucket's members (each finds its sequence and
+// window on its own) and count their bases in packed 8-bit counters, four
+// codes of one position per register, folded across the warp after at most
+// 255 members per lane.  The counts are integers, so the result is the same
+// as the thread-per-candidate form's, bit for bit.
+__global__ void __launch_bounds__(256) theta0_warp_kernel(
+    const uint32_t *__restrict__ packed, int64_t nwords, const int32_t *__restrict__ seq_off,
+    const int32_t *__restrict__ lmer_off, int t, int l, const int64_t *__restrict__ cand_off,
+    const int32_t *__restrict__ members, int64_t C, float beta, float *__restrict__ theta0) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (c >= C) return;  // c is the same for the whole warp
+    const int64_t e0 = cand_off[c], e1 = cand_off[c + 1];
+    uint32_t tot[4] = {0u, 0u, 0u, 0u};  // lane q: entries q, q + 32, q + 64, q + 96
+    for (int64_t base = e0; base < e1; base += 32 * 255) {
+        uint32_t acc[32];
+#pragma unroll
+        for (int p = 0; p < 32; ++p) acc[p] = 0u;
+        const int64_t end = min(e1, base + 32 * 255);
+        for (int64_t e = base + lane; e < end; e += 32) {
+            const int g = members[e];
+            int lo = 0, hi = t - 1;  // last i with lmer_off[i] <= g
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(lmer_off + mid) <= g) lo = mid; else hi = mid - 1;
+            }
+            const int64_t b0 = (int64_t)__ldg(seq_off + lo) + (g - __ldg(lmer_off + lo));
+            const uint64_t win = window64(packed, nwords, b0);
+#pragma unroll
+            for (int p = 0; p < 32; ++p) acc[p] += 1u << (((uint32_t)(win >> (2 * p)) & 3u) << 3);
+        }
+#pragma unroll
+        for (int p = 0; p < 32; ++p) {
+            if (p < l) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const uint32_t v = __reduce_add_sync(0xffffffffu, (acc[p] >> (8 * a)) & 255u);
+                    if (lane == ((4 * p + a) & 31)) tot[(4 * p + a) >> 5] += v;
+                }
+            }
+        }
+    }
+    const float den = (float)(e1 - e0) + 4.f * beta;
+    const int L4 = 4 * l;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int q = 32 * r + lane;
+        if (q < L4) theta0[c * L4 + q] = ((float)tot[r] + beta) / den;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // One EM iteration (E-step + optional M-step) in FP32 for a tile of
 // candidates and one group of sequences.
@@ -478,9 +530,24 @@ int launch_em_fp32_iter(const EmParams &P, cudaStream_t st) {
 
 }  // namespace
 
+// Up to this many candidates theta0 takes one warp per candidate (searches that
+// keep a few large buckets); beyond it one thread per candidate, whose buckets
+// hold a few l-mers each.
+constexpr int64_t kTheta0WarpMaxC = 65536;
+
 int launch_theta0(const uint32_t *packed, const Layout &L, const int64_t *cand_off,
                   const int32_t *members, int64_t C, float beta, float *theta0, cudaStream_t st) {
     if (C == 0) return PROJ_OK;
+    if (C <= kTheta0WarpMaxC) {  // few candidates: one warp each
+        {
+            TraceSpan ts_("theta0", st);
+            theta0_warp_kernel<<<(unsigned)((C + 7) / 8), 256, 0, st>>>(
+                packed, L.nwords, L.seq_off_dev(), L.lmer_off_dev(), L.t, L.l, cand_off, members, C,
+                beta, theta0);
+        }
+        PROJ_LAUNCH_CHECK("theta0_warp_kernel");
+        return PROJ_OK;
+    }
     const int nt = 128;
     const size_t smem = (size_t)4 * L.l * nt * sizeof(float);
     PROJ_CUDA_TRY(cudaFuncSetAttribute(theta0_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -270,13 +270,33 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     // Algorithm 2 steps 2b-2c: project every l-mer and count its bucket.
     const int n_flat = P.partitioned ? s_cb[P.n_chunks] : 0;  // the unit's l-mers
     if (P.partitioned) {
-        // counting needs no order: warp w takes pieces w, w + 32, ..., each lane
-        // eight loads in flight ahead of their increments (the pieces stream
-        // from HBM); u32 counters in this mode
+        // counting needs no order: warp w takes pieces w, w + W, ... (W warps),
+        // the first 256 entries of four pieces at a time, each lane 32 loads in
+        // flight ahead of their increments (the pieces stream from HBM), then
+        // what long pieces hold beyond that; u32 counters in this mode
+        for (int c0 = warp; c0 < P.n_chunks; c0 += 4 * kWarps) {
+            uint32_t r[4][8];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = c0 + j * kWarps;
+                const int len = c < P.n_chunks ? min(s_cb[c + 1] - s_cb[c], 256) : 0;
+                const uint16_t *src = P.prel + (c < P.n_chunks ? s_pb[c] + s_cb[c] : 0);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int e = lane + 32 * q;
+                    r[j][q] = e < len ? (uint32_t)__ldg(src + e) : 0xFFFFFFFFu;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (r[j][q] != 0xFFFFFFFFu) atomicAdd(&hist32[r[j][q]], 1u);
+        }
         for (int c = warp; c < P.n_chunks; c += kWarps) {
             const int len = s_cb[c + 1] - s_cb[c];
             const uint16_t *src = P.prel + (s_pb[c] + s_cb[c]);
-            for (int e0 = lane; e0 < len; e0 += 8 * 32) {
+            for (int e0 = 256 + lane; e0 < len; e0 += 8 * 32) {
                 uint32_t r[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
@@ -308,9 +328,61 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     }
 
     // Algorithm 2 step 3: enriched buckets (count >= s) of this key range.
-    // Warp w takes buckets [w*span, (w+1)*span) in rows of 32 consecutive
-    // buckets, lane i reading bucket row + i (consecutive words: no bank
-    // conflicts); a row's ballot and lane scan keep key order.
+    if (!FILL && !P.hist16) {
+        // counting pass, u32 counters: warp w takes buckets [w*span, (w+1)*span)
+        // in rows of 128, lane i reading buckets row + 4i .. row + 4i + 3 (one
+        // 16-byte load, no bank conflicts); the lanes' counts, scanned in lane
+        // order, keep key order
+        const int span = (((P.hb + kWarps - 1) / kWarps) + 127) & ~127;
+        const int wb = min(warp * span, P.hb), we = min(wb + span, P.hb);
+        int nb = 0, nm = 0;
+        for (int r = wb; r < we; r += 128) {
+            const int b = r + 4 * lane;
+            const uint4 v = b < we ? *reinterpret_cast<const uint4 *>(hist32 + b) : make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t c4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+                if ((int)c4[h] >= P.s) { ++nb; nm += (int)c4[h]; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            nb += __shfl_xor_sync(0xffffffffu, nb, o);
+            nm += __shfl_xor_sync(0xffffffffu, nm, o);
+        }
+        int rb, rm, NB, NM;  // this warp's first enriched bucket; unit totals
+        block_scan2<NT>(lane == 0 ? nb : 0, lane == 0 ? nm : 0, rb, rm, NB, NM, s_warp);
+        rb = __shfl_sync(0xffffffffu, rb, 0);
+        if (P.emit) {  // this unit's enriched buckets, in key order
+            uint2 *dst = P.emit + P.emit_off[unit];
+            for (int r = wb; r < we; r += 128) {
+                const int b = r + 4 * lane;
+                const uint4 v = b < we ? *reinterpret_cast<const uint4 *>(hist32 + b) : make_uint4(0u, 0u, 0u, 0u);
+                const uint32_t c4[4] = {v.x, v.y, v.z, v.w};
+                int k4 = 0;
+#pragma unroll
+                for (int h = 0; h < 4; ++h) k4 += (int)c4[h] >= P.s;
+                int sc = k4;  // inclusive lane scan of the enriched counts
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, sc, o);
+                    if (lane >= o) sc += u;
+                }
+                int at = rb + sc - k4;
+#pragma unroll
+                for (int h = 0; h < 4; ++h)
+                    if ((int)c4[h] >= P.s) dst[at++] = make_uint2((uint32_t)(b + h), c4[h]);
+                rb += __shfl_sync(0xffffffffu, sc, 31);
+            }
+        }
+        if (tid == 0) {
+            P.part_nb[unit] = NB;
+            P.part_nm[unit] = NM;
+        }
+        return;
+    }
+    // Otherwise warp w takes buckets [w*span, (w+1)*span) in rows of 32
+    // consecutive buckets, lane i reading bucket row + i (consecutive words: no
+    // bank conflicts); a row's ballot and lane scan keep key order.
     const int span = (((P.hb + kWarps - 1) / kWarps) + 31) & ~31;
     const int wb = min(warp * span, P.hb), we = min(wb + span, P.hb);
     int nb = 0, nm = 0;

@@ -169,6 +169,9 @@ def _random_case(seed, t, nmin, nmax, alphabet=b"ACGT"):
     dict(seed=9, t=40, nmin=400, nmax=600, l=20, k=10, s=2),  # u16, 16 parts
     dict(seed=10, t=4, nmin=100000, nmax=100000, l=12, k=8, s=4),  # input not staged in smem
     dict(seed=11, t=12, nmin=40, nmax=200, l=32, k=10, s=2),  # l = 32
+    # partitioned mode over many short sequences: staged and unstaged chunks
+    dict(seed=12, t=12000, nmin=24, nmax=30, l=20, k=10, s=2),
+    dict(seed=13, t=30000, nmin=21, nmax=22, l=20, k=10, s=2),
 ])
 @pytest.mark.parametrize("nt", [1024, 512])
 def test_hash_edge_cases_bit_exact(P, case, nt, monkeypatch):
@@ -245,6 +248,33 @@ def test_theta0_matches_oracle(P, cfg):
     co = torch.from_numpy(oh["cand_off"].astype(np.int64)).cuda()
     mem = torch.from_numpy(oh["members"].astype(np.int32)).cuda()
     th = P.theta0_build(packed, inst.seq_off, inst.l, co, mem, oh["cand_key"].size, 0.25)
+    assert np.max(np.abs(th.cpu().numpy() - want)) <= 1e-6
+
+
+@pytest.mark.parametrize("form", ["warp", "thread"])
+def test_theta0_large_and_many_buckets(P, form):
+    """theta0 (Example 1, Figure 4) in both kernel forms: a few large buckets
+    (one warp per candidate; a bucket of every l-mer passes the 255-per-lane
+    fold of the 8-bit counters, plus an empty and a one-member bucket) and more
+    than 65,536 small ones (one thread per candidate)."""
+    inst = instance_for_config(2)
+    codes = O.encode(inst.ascii)
+    x = int((inst.lens - inst.l + 1).sum())
+    rng = np.random.default_rng(5)
+    if form == "warp":
+        lists = [np.arange(x), np.zeros(0, np.int64), np.array([5]),
+                 np.sort(rng.choice(x, 300, replace=False))]
+    else:
+        lists = [np.sort(rng.choice(x, int(rng.integers(1, 5)), replace=False))
+                 for _ in range(70_000)]
+    cand_off = np.zeros(len(lists) + 1, np.int64)
+    cand_off[1:] = np.cumsum([len(a) for a in lists])
+    members = np.concatenate(lists).astype(np.int32)
+    want = O.theta0_all(codes, inst.seq_off, inst.l, cand_off, members, 0.25)
+    packed = upload(P, inst.ascii)
+    co = torch.from_numpy(cand_off).cuda()
+    mem = torch.from_numpy(members).cuda()
+    th = P.theta0_build(packed, inst.seq_off, inst.l, co, mem, len(lists), 0.25)
     assert np.max(np.abs(th.cpu().numpy() - want)) <= 1e-6
 
 
