@@ -81,6 +81,7 @@ struct HashParams {
     const uint16_t *plid;
     const int32_t *pstart;
     int n_chunks;
+    const int *chunk_info;    // [n_chunks][8]: see chunk_info_kernel
     // counting pass: each unit's enriched buckets as (key - part * hb, size), in
     // key order, at emit[emit_off[unit] ..] (capacity: every enriched bucket
     // holds >= s of the unit's l-mers)
@@ -581,20 +582,30 @@ __global__ void __launch_bounds__(kThreads, 1) hash_batch_kernel(const HashParam
 constexpr int kMaxParts = 32;
 constexpr int kPartShift = 15;                  // partitioned mode: u32 counters, 2^15 keys per part
 constexpr uint32_t kPartKeys = 1u << kPartShift;
-constexpr int kSortThreads = 256;
-constexpr int kSortWarps = kSortThreads / 32;  // one warp per 1024 l-mers of a chunk
-static_assert(kSortWarps * 1024 == kSortChunk, "chunk = warps x 1024 l-mers");
+// Nine warps: dense chunks give each warp 32 blocks of 32 bases (so a chunk may
+// span up to 288 blocks); other chunks give warps 0-7 1024 l-mers each.
+constexpr int kSortWarps = 9;
+constexpr int kSortThreads = 32 * kSortWarps;
+static_assert((kSortWarps - 1) * 1024 == kSortChunk, "chunk = 8 warps x 1024 l-mers");
 // a chunk's packed words and sequence offsets are staged in shared memory
 // when they fit (kSortChunk l-mers of length <= 32 always span fewer than
 // 2^18 bases, but long runs of short sequences can exceed these)
 constexpr int kStageWords = 4096;
 constexpr int kStageSeqs = (kSortChunk - kStageWords - 2) / 2 - 1;
-constexpr int kSortSmem = 2 * kSortChunk * 4;
-
-__device__ __forceinline__ void part_setup(const HashParams &P, int trial_local, int *s_pos) {
-    trial_positions(P, trial_local, s_pos);
-    __syncthreads();
-}
+// Dense chunks (l-mers spread over at most kDenseBlocks blocks of 32 bases and
+// kDenseSeqs sequences, i.e. sequences much longer than l) build their keys 32
+// at a time from bit planes into a table indexed by base, one pad word per 32
+// keys (conflict-free stores of a lane's 32 consecutive keys).
+constexpr int kDenseBlocks = 32 * kSortWarps;
+constexpr int kDenseSeqs = 255;
+// shared memory: region A (base-indexed keys of a dense chunk, later the
+// grouped output; other chunks stage words and offsets there first) | region B
+// (keys and places by l-mer; a dense chunk's packed words first) | region C
+// (a dense chunk's sequence offsets)
+constexpr int kRegionA = kDenseBlocks * 33;
+constexpr int kSortSmem = (kRegionA + kSortChunk + 2 * (kDenseSeqs + 1)) * 4;
+static_assert(kRegionA >= kSortChunk && kStageWords + 2 + 2 * (kStageSeqs + 1) <= kRegionA,
+              "region A holds the grouped output and the staged input");
 
 // sequence holding global l-mer id g (last i with lmer_off[i] <= g)
 __device__ __forceinline__ int seq_of(const int32_t *lmer_off, int t, int g) {
@@ -606,46 +617,104 @@ __device__ __forceinline__ int seq_of(const int32_t *lmer_off, int t, int g) {
     return lo;
 }
 
+// bits 0, 2, 4, .. 30 of w moved to bits 0 .. 15
+__device__ __forceinline__ uint32_t even_bits(uint32_t w) {
+    w &= 0x55555555u;
+    w = (w | (w >> 1)) & 0x33333333u;
+    w = (w | (w >> 2)) & 0x0F0F0F0Fu;
+    w = (w | (w >> 4)) & 0x00FF00FFu;
+    return (w | (w >> 8)) & 0x0000FFFFu;
+}
+
+// Low (lo) and high (hi) code bits of the 32 bases of packed words w0, w1.
+__device__ __forceinline__ void bit_planes(uint32_t w0, uint32_t w1, uint32_t &lo, uint32_t &hi) {
+    lo = even_bits(w0) | (even_bits(w1) << 16);
+    hi = even_bits(w0 >> 1) | (even_bits(w1 >> 1) << 16);
+}
+
+// One level of a 32 x 32 bit-matrix transpose: rows r and r + J (bit J of r
+// clear) exchange the block of columns with bit J set in row r for the block
+// with it clear in row r + J.  The five levels together map bit c of a[r] to
+// bit r of a[c]; they commute.
+template <int J, uint32_t M>
+__device__ __forceinline__ void transpose_level(uint32_t (&a)[32]) {
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        if ((r & J) == 0) {
+            const uint32_t x = ((a[r] >> J) ^ a[r + J]) & M;
+            a[r + J] ^= x;
+            a[r] ^= x << J;
+        }
+    }
+}
+
+// What every trial's CTA of chunk c needs to know about the chunk, worked out
+// once per call: [0] first and [1] last sequence, [2] first packed word,
+// [3] words to stage for the l-mer-by-l-mer key build (-1: read global memory),
+// [4] dense (bit-plane keys), [5] a dense chunk's last 32-base block.
+__global__ void chunk_info_kernel(const HashParams P, int *__restrict__ info) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P.n_chunks) return;
+    const int g0 = c * kSortChunk, n = min(kSortChunk, P.x - g0);
+    const int i0 = seq_of(P.lmer_off, P.t, g0), i1 = seq_of(P.lmer_off, P.t, g0 + n - 1);
+    const int64_t b_lo = (int64_t)P.seq_off[i0] + (g0 - P.lmer_off[i0]);
+    const int64_t b_last = (int64_t)P.seq_off[i1] + (g0 + n - 1 - P.lmer_off[i1]);
+    const int64_t w_lo = b_lo >> 4, w_hi = (b_last + P.l + 15) >> 4;
+    const int nst = (w_hi - w_lo <= kStageWords && i1 - i0 + 2 <= kStageSeqs) ? (int)(w_hi - w_lo) + 2
+                                                                               : -1;
+    // 32-base blocks from base 16 * w_lo (the chunk's first l-mer is in block 0)
+    const int64_t vb = (b_last - 16 * w_lo) >> 5;
+    int *o = info + 8 * (int64_t)c;
+    o[0] = i0;
+    o[1] = i1;
+    o[2] = (int)w_lo;
+    o[3] = nst;
+    o[4] = (vb < kDenseBlocks && i1 - i0 + 1 <= kDenseSeqs) ? 1 : 0;
+    o[5] = (int)(vb < kDenseBlocks ? vb : kDenseBlocks);
+}
+
 template <int K>
-__global__ void __launch_bounds__(kSortThreads) part_sort_kernel(const HashParams P,
-                                                                 uint16_t *__restrict__ orel,
-                                                                 uint16_t *__restrict__ olid,
-                                                                 int32_t *__restrict__ pstart) {
-    // dynamic shared memory: keys [kSortChunk] | grouped output [kSortChunk]; the
-    // output area first holds the chunk's packed words and sequence offsets
+__global__ void __launch_bounds__(kSortThreads, 3) part_sort_kernel(const HashParams P,
+                                                                    uint16_t *__restrict__ orel,
+                                                                    uint16_t *__restrict__ olid,
+                                                                    int32_t *__restrict__ pstart) {
     extern __shared__ __align__(16) uint32_t s_dyn[];
-    uint32_t *s_key = s_dyn;
-    uint32_t *s_out = s_dyn + kSortChunk;
-    uint32_t *s_words = s_out;                                       // [kStageWords + 2]
-    int32_t *s_soff = reinterpret_cast<int32_t *>(s_out + kStageWords + 2);  // [kStageSeqs + 1]
-    int32_t *s_loff = s_soff + kStageSeqs + 1;
+    uint32_t *s_a = s_dyn;                    // region A
+    uint32_t *s_key = s_dyn + kRegionA;       // region B: key | place << 20 of chunk l-mer j at [j]
+    int32_t *s_doff = reinterpret_cast<int32_t *>(s_key + kSortChunk);  // region C [kDenseSeqs + 1]
+    int32_t *s_dlm = s_doff + kDenseSeqs + 1;                             // [kDenseSeqs + 1]
+    uint32_t *s_out = s_a;                    // grouped output, once the keys are ranked
     __shared__ int s_pos[16];
     __shared__ int s_cnt[kSortWarps][kMaxParts];  // per warp: sizes, then output offsets
     __shared__ int s_tot[kMaxParts + 1];
-    __shared__ int s_rng[4];                       // first / last sequence, first word, staged
+    __shared__ int s_wn[kSortWarps];              // dense: l-mers per warp
     const int trial_local = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
+    const unsigned below = (1u << lane) - 1u;
     const int g0 = chunk * kSortChunk;
     const int n = min(kSortChunk, P.x - g0);
-    for (int q = tid; q < kSortWarps * kMaxParts; q += kSortThreads) (&s_cnt[0][0])[q] = 0;
-    if (tid == 32) {  // the chunk's sequences and packed words
-        const int i0 = seq_of(P.lmer_off, P.t, g0), i1 = seq_of(P.lmer_off, P.t, g0 + n - 1);
-        const int64_t b_lo = (int64_t)P.seq_off[i0] + (g0 - P.lmer_off[i0]);
-        const int64_t b_hi = (int64_t)P.seq_off[i1] + (g0 + n - 1 - P.lmer_off[i1]) + P.l;
-        const int64_t w_lo = b_lo >> 4, w_hi = (b_hi + 15) >> 4;
-        s_rng[0] = i0;
-        s_rng[1] = i1;
-        s_rng[2] = (int)w_lo;
-        s_rng[3] = (w_hi - w_lo <= kStageWords && i1 - i0 + 2 <= kStageSeqs) ? (int)(w_hi - w_lo) : -1;
-    }
-    part_setup(P, trial_local, s_pos);  // ends with a barrier
-    const int i0 = s_rng[0], i1 = s_rng[1], w_lo = s_rng[2], nw = s_rng[3];
-    const bool staged = nw >= 0;
-    if (staged) {
-        for (int w = tid; w < nw + 2; w += kSortThreads)
+    const int *ci = P.chunk_info + 8 * (int64_t)chunk;
+    const int i0 = ci[0], i1 = ci[1], w_lo = ci[2], nst = ci[3], vb1 = ci[5];
+    const bool dense = K > 0 && ci[4] != 0;
+    const bool staged = !dense && nst >= 0;
+    const int nq = i1 - i0 + 1;  // sequences the chunk touches
+    trial_positions(P, trial_local, s_pos);
+    // l-mer-by-l-mer key build: words and offsets staged in region A
+    uint32_t *s_words = s_a;                                               // [kStageWords + 2]
+    int32_t *s_soff = reinterpret_cast<int32_t *>(s_a + kStageWords + 2);  // [kStageSeqs + 1]
+    int32_t *s_loff = s_soff + kStageSeqs + 1;
+    if (dense) {  // words of blocks 0 .. vb1 + 1 into region B, offsets into region C
+        for (int w = tid; w < 2 * vb1 + 4; w += kSortThreads)
+            s_key[w] = w_lo + w < P.nwords ? __ldg(P.packed + w_lo + w) : 0u;
+        for (int q = tid; q <= nq; q += kSortThreads) {
+            s_doff[q] = (int32_t)(P.seq_off[i0 + q] - 16 * (int64_t)w_lo);  // base from 16 * w_lo
+            s_dlm[q] = P.lmer_off[i0 + q];
+        }
+    } else if (staged) {
+        for (int w = tid; w < nst; w += kSortThreads)
             s_words[w] = w_lo + w < P.nwords ? __ldg(P.packed + w_lo + w) : 0u;
-        for (int q = tid; q <= i1 - i0 + 1; q += kSortThreads) {
-            s_soff[q] = (int32_t)(P.seq_off[i0 + q] - 16 * (int64_t)w_lo);  // base in s_words
+        for (int q = tid; q <= nq; q += kSortThreads) {
+            s_soff[q] = (int32_t)(P.seq_off[i0 + q] - 16 * (int64_t)w_lo);
             s_loff[q] = P.lmer_off[i0 + q];
         }
     }
@@ -653,40 +722,130 @@ __global__ void __launch_bounds__(kSortThreads) part_sort_kernel(const HashParam
     int pos[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) pos[q] = q < P.k ? s_pos[q] : 0;
-    const int j0 = warp * 1024;  // this warp's l-mers of the chunk, in rounds of 32
-    const unsigned below = (1u << lane) - 1u;
 
-    // keys into shared memory; sizes of the parts per warp
-    int i = 0;  // sequence of this lane's l-mer, relative to i0
-    for (int r = 0; r < 32; ++r) {
-        const int j = j0 + 32 * r + lane;
-        const bool act = j < n;
-        const unsigned amask = __ballot_sync(0xffffffffu, act);
-        if (act) {
-            const int g = g0 + j;
-            uint32_t key;
-            if (staged) {  // every word the chunk's l-mers touch is in s_words
-                while (s_loff[i + 1] <= g) ++i;
-                const int b = s_soff[i] + (g - s_loff[i]);
-                const int wi = b >> 4, sh = 2 * (b & 15);
-                const uint64_t lo = (uint64_t)s_words[wi] | ((uint64_t)s_words[wi + 1] << 32);
-                const uint64_t win = sh ? (lo >> sh) | ((uint64_t)s_words[wi + 2] << (64 - sh)) : lo;
-                key = lmer_key_k<K>(win, pos, P.k);
-            } else {
-                while (__ldg(P.lmer_off + i0 + i + 1) <= g) ++i;
-                const int64_t b0 = (int64_t)__ldg(P.seq_off + i0 + i) + (g - __ldg(P.lmer_off + i0 + i));
-                key = lmer_key_k<K>(window64(P.packed, P.nwords, b0), pos, P.k);
+    if constexpr (K > 0) {
+        if (dense) {
+            // Keys of every base of block v = 32 warp + lane.  Row 2(K-1-q) of a
+            // 32 x 32 bit matrix holds the low code bits of projected position q
+            // for the block's 32 starts, row 2(K-1-q)+1 the high bits; transposed,
+            // word i is the key of the l-mer starting at base 32v + i, first
+            // projected position most significant (Section 6).
+            const int v = 32 * warp + lane;
+            if (v <= vb1) {
+                uint32_t a[32];
+                const uint2 w01 = *reinterpret_cast<const uint2 *>(s_key + 2 * v);
+                const uint2 w23 = *reinterpret_cast<const uint2 *>(s_key + 2 * v + 2);
+                uint32_t lo0, hi0, lo1, hi1;
+                bit_planes(w01.x, w01.y, lo0, hi0);
+                bit_planes(w23.x, w23.y, lo1, hi1);
+#pragma unroll
+                for (int r = 0; r < 32; ++r) a[r] = 0u;
+#pragma unroll
+                for (int q = 0; q < K; ++q) {
+                    a[2 * (K - 1 - q)] = __funnelshift_r(lo0, lo1, pos[q]);
+                    a[2 * (K - 1 - q) + 1] = __funnelshift_r(hi0, hi1, pos[q]);
+                }
+                transpose_level<16, 0x0000FFFFu>(a);
+                transpose_level<8, 0x00FF00FFu>(a);
+                transpose_level<4, 0x0F0F0F0Fu>(a);
+                transpose_level<2, 0x33333333u>(a);
+                transpose_level<1, 0x55555555u>(a);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) s_a[33 * v + i] = a[i];  // base 32v + i at 33v + i
+            }
+            __syncthreads();  // region B's words are read; it now takes the ranked keys
+
+            // Ranking, warp by warp over its 1024 bases in rounds of 32 (lane i:
+            // base 1024 warp + 32r + i); inactive lanes are bases where no l-mer
+            // of the chunk starts.  Five ballots on the part bits give every lane
+            // the lanes of its round with the same part, and lane p the lanes of
+            // part p, whose running count it keeps: each l-mer's place among its
+            // warp's l-mers of its part keeps l-mer order, with no shared-memory
+            // round trip (match_any, measured, was 16% slower).
+            const int lb0 = 1024 * warp + lane;
+            int q = 0, hi = nq - 1;  // last sequence starting at or before base lb0
+            while (q < hi) {
+                const int mid = (q + hi + 1) >> 1;
+                if (s_doff[mid] <= lb0) q = mid; else hi = mid - 1;
+            }
+            // sequence q's first base, the next sequence's, its first l-mer and l-mer count
+            int soff = s_doff[q], snext = q + 1 < nq ? s_doff[q + 1] : INT_MAX;
+            int lmq = s_dlm[q], nsq = s_dlm[q + 1] - lmq;
+            uint32_t run = 0u;  // lane p: this warp's l-mers of part p so far
+            int nvalid = 0;
+            const int rounds = min(32, vb1 + 1 - 32 * warp);
+            for (int r = 0; r < rounds; ++r) {
+                const int lb = lb0 + 32 * r;
+                while (snext <= lb) {
+                    ++q;
+                    soff = snext;
+                    snext = q + 1 < nq ? s_doff[q + 1] : INT_MAX;
+                    lmq = s_dlm[q];
+                    nsq = s_dlm[q + 1] - lmq;
+                }
+                const int jl = lb - soff;
+                const int e = lmq - g0 + jl;
+                const bool act = jl >= 0 && jl < nsq && e >= 0 && e < n;
+                const unsigned amask = __ballot_sync(0xffffffffu, act);
+                const uint32_t key = s_a[lb + (lb >> 5)];  // every base of the blocks has one
+                const uint32_t part = key >> kPartShift;
+                unsigned mine = amask;  // active lanes whose part is this lane's index
+                unsigned same = amask;  // active lanes with this lane's part
+#pragma unroll
+                for (int bit = 0; bit < 5; ++bit) {
+                    const unsigned B = __ballot_sync(0xffffffffu, (part >> bit) & 1u);
+                    same &= ~(B ^ (0u - ((part >> bit) & 1u)));
+                    mine &= ~(B ^ (0u - ((uint32_t)(lane >> bit) & 1u)));
+                }
+                const uint32_t before = __shfl_sync(0xffffffffu, run, (int)(part & 31u));
+                // keys < 2^20, places < 2^10
+                if (act) s_key[e] = key | ((before + __popc(same & below)) << 20);
+                run += __popc(mine);
+                nvalid += __popc(amask);
+            }
+            s_cnt[warp][lane] = (int)run;
+            if (lane == 0) s_wn[warp] = nvalid;
+        }
+    }
+    if (!dense) {
+        // warps 0-7: 1024 l-mers each in rounds of 32 (lane i: l-mer j0 + 32r + i),
+        // keys built here
+        const int j0 = warp * 1024, j1 = min(j0 + 1024, n);
+        int i = 0;  // sequence of this lane's l-mer, relative to i0
+        uint32_t run = 0u;  // lane p: this warp's l-mers of part p so far
+        for (int r = 0; r < 32; ++r) {
+            const int j = j0 + 32 * r + lane;
+            const bool act = j < j1;
+            const unsigned amask = __ballot_sync(0xffffffffu, act);
+            uint32_t key = 0u;
+            if (act) {
+                const int g = g0 + j;
+                if (staged) {  // every word the chunk's l-mers touch is in s_words
+                    while (s_loff[i + 1] <= g) ++i;
+                    const int b = s_soff[i] + (g - s_loff[i]);
+                    const int wi = b >> 4, sh = 2 * (b & 15);
+                    const uint64_t lo = (uint64_t)s_words[wi] | ((uint64_t)s_words[wi + 1] << 32);
+                    const uint64_t win = sh ? (lo >> sh) | ((uint64_t)s_words[wi + 2] << (64 - sh)) : lo;
+                    key = lmer_key_k<K>(win, pos, P.k);
+                } else {
+                    while (__ldg(P.lmer_off + i0 + i + 1) <= g) ++i;
+                    const int64_t b0 = (int64_t)__ldg(P.seq_off + i0 + i) + (g - __ldg(P.lmer_off + i0 + i));
+                    key = lmer_key_k<K>(window64(P.packed, P.nwords, b0), pos, P.k);
+                }
             }
             const uint32_t part = key >> kPartShift;
-            // lanes of this round with the same part, in lane order; this l-mer's
-            // place among its warp's l-mers of that part (keys < 2^20, places < 2^10)
-            const unsigned eq = __match_any_sync(amask, part);
-            const int before = s_cnt[warp][part];
-            s_key[j] = key | ((uint32_t)(before + __popc(eq & below)) << 20);
-            __syncwarp(amask);
-            if ((eq & below) == 0u) s_cnt[warp][part] = before + __popc(eq);
+            unsigned same = amask, mine = amask;  // as in the dense ranking
+#pragma unroll
+            for (int bit = 0; bit < 5; ++bit) {
+                const unsigned B = __ballot_sync(0xffffffffu, (part >> bit) & 1u);
+                same &= ~(B ^ (0u - ((part >> bit) & 1u)));
+                mine &= ~(B ^ (0u - ((uint32_t)(lane >> bit) & 1u)));
+            }
+            const uint32_t before = __shfl_sync(0xffffffffu, run, (int)(part & 31u));
+            if (act) s_key[j] = key | ((before + __popc(same & below)) << 20);
+            run += __popc(mine);
         }
-        __syncwarp();
+        s_cnt[warp][lane] = (int)run;
     }
     __syncthreads();
     // part p starts at s_tot[p] in the chunk; warp w's entries of part p follow
@@ -719,15 +878,36 @@ __global__ void __launch_bounds__(kSortThreads) part_sort_kernel(const HashParam
     // stable placement into shared memory: after all of part p of warps w' < w,
     // at the l-mer's place among warp w's l-mers of p; entry = (key - part * hb)
     // | chunk-local id << 16
-    for (int j = tid; j < n; j += kSortThreads) {
-        const uint32_t v = s_key[j];
-        const uint32_t key = v & 0xFFFFFu, part = key >> kPartShift;
-        s_out[s_tot[part] + s_cnt[j >> 10][part] + (int)(v >> 20)] =
-            (key & (kPartKeys - 1u)) | ((uint32_t)j << 16);
+    if (dense) {  // warp w ranked the l-mers [e0, e0 + s_wn[w]) of its bases
+        int e0 = 0;
+        for (int w = 0; w < warp; ++w) e0 += s_wn[w];
+        const int e1 = e0 + s_wn[warp];
+        for (int j = e0 + lane; j < e1; j += 32) {
+            const uint32_t v = s_key[j];
+            const uint32_t key = v & 0xFFFFFu, part = key >> kPartShift;
+            s_out[s_tot[part] + s_cnt[warp][part] + (int)(v >> 20)] =
+                (key & (kPartKeys - 1u)) | ((uint32_t)j << 16);
+        }
+    } else {
+        for (int j = tid; j < n; j += kSortThreads) {
+            const uint32_t v = s_key[j];
+            const uint32_t key = v & 0xFFFFFu, part = key >> kPartShift;
+            s_out[s_tot[part] + s_cnt[j >> 10][part] + (int)(v >> 20)] =
+                (key & (kPartKeys - 1u)) | ((uint32_t)j << 16);
+        }
     }
     __syncthreads();
+    // the grouped entries, four per thread: keys to orel, ids to olid
     const int64_t region = ((int64_t)trial_local * P.n_chunks + chunk) * kSortChunk;
-    for (int e = tid; e < n; e += kSortThreads) {
+    const int n4 = n >> 2;
+    uint2 *rel4 = reinterpret_cast<uint2 *>(orel + region);
+    uint2 *lid4 = reinterpret_cast<uint2 *>(olid + region);
+    for (int e4 = tid; e4 < n4; e4 += kSortThreads) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(s_out + 4 * e4);
+        rel4[e4] = make_uint2(__byte_perm(v.x, v.y, 0x5410), __byte_perm(v.z, v.w, 0x5410));
+        lid4[e4] = make_uint2(__byte_perm(v.x, v.y, 0x7632), __byte_perm(v.z, v.w, 0x7632));
+    }
+    for (int e = 4 * n4 + tid; e < n; e += kSortThreads) {
         const uint32_t v = s_out[e];
         orel[region + e] = (uint16_t)(v & 0xFFFFu);
         olid[region + e] = (uint16_t)(v >> 16);
@@ -850,8 +1030,15 @@ int launch_partition_k(const HashParams &P, dim3 grid, uint16_t *orel, uint16_t 
     return PROJ_OK;
 }
 
-int launch_partition(const HashParams &P, dim3 grid, uint16_t *orel, uint16_t *olid,
-                     int32_t *pstart, cudaStream_t st) {
+int launch_partition(const HashParams &P0, dim3 grid, uint16_t *orel, uint16_t *olid,
+                     int32_t *pstart, int *info, cudaStream_t st) {
+    HashParams P = P0;
+    P.chunk_info = info;
+    {
+        TraceSpan ts_("hash_partition", st);
+        chunk_info_kernel<<<(unsigned)((P.n_chunks + 127) / 128), 128, 0, st>>>(P, info);
+    }
+    PROJ_LAUNCH_CHECK("chunk_info_kernel");
     switch (P.k) {
         case 9: return launch_partition_k<9>(P, grid, orel, olid, pstart, st);
         case 10: return launch_partition_k<10>(P, grid, orel, olid, pstart, st);
@@ -1112,7 +1299,8 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
         const int64_t n_pst = n_trials * P.n_chunks * (P.parts + 1);
         const int64_t n_ent = n_trials * P.n_chunks * kSortChunk;
         if (!reuse)
-            PROJ_TRY(part_buf.alloc((size_t)n_pst * 4 + 16 + (size_t)n_ent * 4, st));
+            PROJ_TRY(part_buf.alloc((size_t)n_pst * 4 + 16 + (size_t)n_ent * 4 +
+                                        (size_t)P.n_chunks * 32, st));
         int32_t *pst = part_buf.as<int32_t>();
         uint16_t *rel = reinterpret_cast<uint16_t *>(
             (reinterpret_cast<uintptr_t>(pst + n_pst) + 15) & ~(uintptr_t)15);
@@ -1121,7 +1309,8 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
         P.plid = rel + n_ent;
         if (!reuse) {
             const dim3 grid((unsigned)P.n_chunks, (unsigned)n_trials);
-            PROJ_TRY(launch_partition(P, grid, rel, rel + n_ent, pst, st));
+            int *info = reinterpret_cast<int *>(rel + 2 * n_ent);  // [n_chunks][8]
+            PROJ_TRY(launch_partition(P, grid, rel, rel + n_ent, pst, info, st));
         }
     }
     // each unit's enriched (key, size) list kept by the counting pass (a search
