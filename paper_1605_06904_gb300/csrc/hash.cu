@@ -100,7 +100,8 @@ __host__ __device__ inline SmemLayout smem_layout(const HashParams &P, bool fill
     SmemLayout S;
     S.hist_bytes = (P.hist16 ? 2 : 4) * P.hb;
     S.hist_bytes = (S.hist_bytes + 15) & ~15;
-    S.bitmap_bytes = fill ? (((P.hb + 31) / 32) * 4 + 15) & ~15 : 0;
+    // enriched-bucket bitmap: the fill pass's, and the u32 counting pass's
+    S.bitmap_bytes = (fill || !P.hist16) ? (((P.hb + 31) / 32) * 4 + 15) & ~15 : 0;
     S.cb_bytes = P.partitioned ? (((P.n_chunks + 1) * 4 + 15) & ~15) + P.n_chunks * 8 : 0;
     S.off_bytes = P.partitioned ? 0 : ((2 * (P.t + 1) * 4) + 15) & ~15;
     S.words_bytes = P.stage_words ? ((P.stage_words + 2) * 4 + 15) & ~15 : 0;
@@ -257,7 +258,7 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     const int hist_words = S.hist_bytes / 4;  // a multiple of 4
     for (int w = tid; w < hist_words / 4; w += kThreads)
         reinterpret_cast<uint4 *>(hist32)[w] = make_uint4(0u, 0u, 0u, 0u);
-    if (FILL)
+    if (FILL || !P.hist16)
         for (int w = tid; w < S.bitmap_bytes / 4; w += kThreads) bitmap[w] = 0u;
     __syncthreads();
     if (!FILL && P.pos_out && part == 0 && tid < P.k)
@@ -268,7 +269,16 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
 #pragma unroll
     for (int q = 0; q < 16; ++q) pos[q] = q < P.k ? s_pos[q] : 0;
 
-    // Algorithm 2 steps 2b-2c: project every l-mer and count its bucket.
+    // Algorithm 2 steps 2b-2c: project every l-mer and count its bucket.  With
+    // u32 counters the counting pass also marks, in the bitmap, each bucket at
+    // the increment that brings it to s l-mers: the enriched buckets.
+    auto bump = [&](uint32_t r) {
+        if (!FILL) {
+            if (atomicAdd(&hist32[r], 1u) == (uint32_t)(P.s - 1)) atomicOr(&bitmap[r >> 5], 1u << (r & 31u));
+        } else {
+            atomicAdd(&hist32[r], 1u);
+        }
+    };
     const int n_flat = P.partitioned ? s_cb[P.n_chunks] : 0;  // the unit's l-mers
     if (P.partitioned) {
         // counting needs no order: warp w takes pieces w, w + W, ... (W warps),
@@ -292,7 +302,7 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
             for (int j = 0; j < 4; ++j)
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
-                    if (r[j][q] != 0xFFFFFFFFu) atomicAdd(&hist32[r[j][q]], 1u);
+                    if (r[j][q] != 0xFFFFFFFFu) bump(r[j][q]);
         }
         for (int c = warp; c < P.n_chunks; c += kWarps) {
             const int len = s_cb[c + 1] - s_cb[c];
@@ -306,7 +316,7 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
                 }
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
-                    if (r[q] != 0xFFFFFFFFu) atomicAdd(&hist32[r[q]], 1u);
+                    if (r[q] != 0xFFFFFFFFu) bump(r[q]);
             }
         }
     } else {
@@ -317,7 +327,7 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
             const uint32_t rel = lmer_key_k<K>(window64(words, nwords, b0), pos, P.k) - lo_key;
             if (rel < hb) {
                 if (P.hist16) atomicAdd(&hist32[rel >> 1], 1u << (16 * (rel & 1u)));
-                else atomicAdd(&hist32[rel], 1u);
+                else bump(rel);
             }
         }
     }
@@ -330,49 +340,33 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
 
     // Algorithm 2 step 3: enriched buckets (count >= s) of this key range.
     if (!FILL && !P.hist16) {
-        // counting pass, u32 counters: warp w takes buckets [w*span, (w+1)*span)
-        // in rows of 128, lane i reading buckets row + 4i .. row + 4i + 3 (one
-        // 16-byte load, no bank conflicts); the lanes' counts, scanned in lane
-        // order, keep key order
-        const int span = (((P.hb + kWarps - 1) / kWarps) + 127) & ~127;
-        const int wb = min(warp * span, P.hb), we = min(wb + span, P.hb);
+        // counting pass, u32 counters: the enriched buckets are the bitmap's
+        // bits; thread i takes a run of its words (key order), and block-scanned
+        // offsets keep key order in the unit's list
+        const int nwb = (P.hb + 31) >> 5;
+        const int per = (nwb + kThreads - 1) / kThreads;
+        const int w0 = min(tid * per, nwb), w1 = min(w0 + per, nwb);
         int nb = 0, nm = 0;
-        for (int r = wb; r < we; r += 128) {
-            const int b = r + 4 * lane;
-            const uint4 v = b < we ? *reinterpret_cast<const uint4 *>(hist32 + b) : make_uint4(0u, 0u, 0u, 0u);
-            const uint32_t c4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int h = 0; h < 4; ++h)
-                if ((int)c4[h] >= P.s) { ++nb; nm += (int)c4[h]; }
+        for (int w = w0; w < w1; ++w) {
+            uint32_t bits = bitmap[w];
+            nb += __popc(bits);
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                nm += (int)hist32[32 * w + b];
+            }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            nb += __shfl_xor_sync(0xffffffffu, nb, o);
-            nm += __shfl_xor_sync(0xffffffffu, nm, o);
-        }
-        int rb, rm, NB, NM;  // this warp's first enriched bucket; unit totals
-        block_scan2<NT>(lane == 0 ? nb : 0, lane == 0 ? nm : 0, rb, rm, NB, NM, s_warp);
-        rb = __shfl_sync(0xffffffffu, rb, 0);
+        int rb, rm, NB, NM;  // this thread's first enriched bucket; unit totals
+        block_scan2<NT>(nb, nm, rb, rm, NB, NM, s_warp);
         if (P.emit) {  // this unit's enriched buckets, in key order
             uint2 *dst = P.emit + P.emit_off[unit];
-            for (int r = wb; r < we; r += 128) {
-                const int b = r + 4 * lane;
-                const uint4 v = b < we ? *reinterpret_cast<const uint4 *>(hist32 + b) : make_uint4(0u, 0u, 0u, 0u);
-                const uint32_t c4[4] = {v.x, v.y, v.z, v.w};
-                int k4 = 0;
-#pragma unroll
-                for (int h = 0; h < 4; ++h) k4 += (int)c4[h] >= P.s;
-                int sc = k4;  // inclusive lane scan of the enriched counts
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int u = __shfl_up_sync(0xffffffffu, sc, o);
-                    if (lane >= o) sc += u;
+            for (int w = w0; w < w1; ++w) {
+                uint32_t bits = bitmap[w];
+                while (bits) {
+                    const uint32_t key = 32u * w + (uint32_t)(__ffs(bits) - 1);
+                    bits &= bits - 1u;
+                    dst[rb++] = make_uint2(key, hist32[key]);
                 }
-                int at = rb + sc - k4;
-#pragma unroll
-                for (int h = 0; h < 4; ++h)
-                    if ((int)c4[h] >= P.s) dst[at++] = make_uint2((uint32_t)(b + h), c4[h]);
-                rb += __shfl_sync(0xffffffffu, sc, 31);
             }
         }
         if (tid == 0) {
@@ -757,9 +751,9 @@ __global__ void __launch_bounds__(kSortThreads, 3) part_sort_kernel(const HashPa
 
             // Ranking, warp by warp over its 1024 bases in rounds of 32 (lane i:
             // base 1024 warp + 32r + i); inactive lanes are bases where no l-mer
-            // of the chunk starts.  Five ballots on the part bits give every lane
-            // the lanes of its round with the same part, and lane p the lanes of
-            // part p, whose running count it keeps: each l-mer's place among its
+            // of the chunk starts.  Five ballots on the part bits give lane p the
+            // active lanes of part p, whose running count it keeps; every lane
+            // reads both from the lane of its part.  Each l-mer's place among its
             // warp's l-mers of its part keeps l-mer order, with no shared-memory
             // round trip (match_any, measured, was 16% slower).
             const int lb0 = 1024 * warp + lane;
@@ -790,13 +784,14 @@ __global__ void __launch_bounds__(kSortThreads, 3) part_sort_kernel(const HashPa
                 const uint32_t key = s_a[lb + (lb >> 5)];  // every base of the blocks has one
                 const uint32_t part = key >> kPartShift;
                 unsigned mine = amask;  // active lanes whose part is this lane's index
-                unsigned same = amask;  // active lanes with this lane's part
 #pragma unroll
                 for (int bit = 0; bit < 5; ++bit) {
                     const unsigned B = __ballot_sync(0xffffffffu, (part >> bit) & 1u);
-                    same &= ~(B ^ (0u - ((part >> bit) & 1u)));
                     mine &= ~(B ^ (0u - ((uint32_t)(lane >> bit) & 1u)));
                 }
+                // lane `part` holds the active lanes with this lane's part and
+                // their count in the warp's earlier rounds
+                const unsigned same = __shfl_sync(0xffffffffu, mine, (int)(part & 31u));
                 const uint32_t before = __shfl_sync(0xffffffffu, run, (int)(part & 31u));
                 // keys < 2^20, places < 2^10
                 if (act) s_key[e] = key | ((before + __popc(same & below)) << 20);
@@ -834,13 +829,13 @@ __global__ void __launch_bounds__(kSortThreads, 3) part_sort_kernel(const HashPa
                 }
             }
             const uint32_t part = key >> kPartShift;
-            unsigned same = amask, mine = amask;  // as in the dense ranking
+            unsigned mine = amask;  // as in the dense ranking
 #pragma unroll
             for (int bit = 0; bit < 5; ++bit) {
                 const unsigned B = __ballot_sync(0xffffffffu, (part >> bit) & 1u);
-                same &= ~(B ^ (0u - ((part >> bit) & 1u)));
                 mine &= ~(B ^ (0u - ((uint32_t)(lane >> bit) & 1u)));
             }
+            const unsigned same = __shfl_sync(0xffffffffu, mine, (int)(part & 31u));
             const uint32_t before = __shfl_sync(0xffffffffu, run, (int)(part & 31u));
             if (act) s_key[j] = key | ((before + __popc(same & below)) << 20);
             run += __popc(mine);
