@@ -170,21 +170,31 @@ __device__ inline void block_scan2(int a, int b, int &pa, int &pb, int &ta, int 
 // Partitioned mode: the pieces of unit (trial, part) in chunk order.  Piece c
 // holds the unit's flat entries [cb[c], cb[c+1]), entry f of it at
 // prel/plid[pb[c] + f].  Ends with a CTA barrier.
+// With n_chunks <= blockDim.x the caller may pass thread i's piece bounds
+// (pf.x, pf.y) of chunk i, loaded ahead of time.
 template <int NT = kThreads>
 __device__ inline void unit_walk_setup(const HashParams &P, int trial_local, int part,
-                                       int32_t *cb, long long *pb, int2 *s_warp) {
+                                       int32_t *cb, long long *pb, int2 *s_warp,
+                                       const int2 *pf = nullptr) {
     const int per = (P.n_chunks + (int)blockDim.x - 1) / (int)blockDim.x;
     const int c0 = min((int)threadIdx.x * per, P.n_chunks), c1 = min(c0 + per, P.n_chunks);
     const int32_t *ps = P.pstart + (int64_t)trial_local * P.n_chunks * (P.parts + 1);
+    auto bounds = [&](int c) {
+        return (pf && per == 1) ? *pf
+                                : make_int2(ps[c * (P.parts + 1) + part], ps[c * (P.parts + 1) + part + 1]);
+    };
     int sum = 0;
-    for (int c = c0; c < c1; ++c) sum += ps[c * (P.parts + 1) + part + 1] - ps[c * (P.parts + 1) + part];
+    for (int c = c0; c < c1; ++c) {
+        const int2 ab = bounds(c);
+        sum += ab.y - ab.x;
+    }
     int pre, pz, tot, tz;
     block_scan2<NT>(sum, 0, pre, pz, tot, tz, s_warp);
     for (int c = c0; c < c1; ++c) {
-        const int a = ps[c * (P.parts + 1) + part];
+        const int2 ab = bounds(c);
         cb[c] = pre;
-        pb[c] = ((long long)trial_local * P.n_chunks + c) * kSortChunk + a - pre;
-        pre += ps[c * (P.parts + 1) + part + 1] - a;
+        pb[c] = ((long long)trial_local * P.n_chunks + c) * kSortChunk + ab.x - pre;
+        pre += ab.y - ab.x;
     }
     if (threadIdx.x == 0) cb[P.n_chunks] = tot;
     __syncthreads();
@@ -232,8 +242,17 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     const uint32_t lo_key = (uint32_t)part * (uint32_t)P.hb;
     const uint32_t hb = (uint32_t)P.hb;
 
-    // projection positions of this trial (Algorithm 2 step 2a)
-    trial_positions(P, trial_local, s_pos);
+    // the unit's piece bounds in chunk tid, loaded before the clear so that
+    // their latency overlaps it (partitioned mode, one chunk per thread)
+    int2 pf = make_int2(0, 0);
+    if (P.partitioned && tid < P.n_chunks && P.n_chunks <= kThreads) {
+        const int32_t *ps = P.pstart + ((int64_t)trial_local * P.n_chunks + tid) * (P.parts + 1) + part;
+        pf = make_int2(ps[0], ps[1]);
+    }
+    // projection positions of this trial (Algorithm 2 step 2a); partitioned
+    // mode reads keys that are already built and needs them only to report
+    // them
+    if (!P.partitioned || (!FILL && P.pos_out && part == 0)) trial_positions(P, trial_local, s_pos);
     if (!P.partitioned)
         for (int i = tid; i <= P.t; i += kThreads) {
             s_seq[i] = P.seq_off[i];
@@ -263,11 +282,11 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
     __syncthreads();
     if (!FILL && P.pos_out && part == 0 && tid < P.k)
         P.pos_out[(int64_t)trial_local * P.k + tid] = (uint8_t)s_pos[tid];
-    if (P.partitioned) unit_walk_setup<NT>(P, trial_local, part, s_cb, s_pb, s_warp);
+    if (P.partitioned) unit_walk_setup<NT>(P, trial_local, part, s_cb, s_pb, s_warp, &pf);
 
     int pos[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) pos[q] = q < P.k ? s_pos[q] : 0;
+    for (int q = 0; q < 16; ++q) pos[q] = (q < P.k && !P.partitioned) ? s_pos[q] : 0;
 
     // Algorithm 2 steps 2b-2c: project every l-mer and count its bucket.  With
     // u32 counters the counting pass also marks, in the bitmap, each bucket at
