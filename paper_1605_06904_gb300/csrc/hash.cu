@@ -50,6 +50,7 @@ struct HashParams {
     int parts;                // CTAs per trial
     int hb;                   // buckets per part
     int hist16;               // u16 counters
+    int count16;              // partitioned counting pass in 64 KB (see hash_unit)
     int stage_words;          // packed words staged in smem (0 = read global)
     int fixed_pos;            // positions given by the caller
     int pos_in[16];
@@ -98,7 +99,7 @@ struct SmemLayout {
 // l-mer offsets, staged packed words
 __host__ __device__ inline SmemLayout smem_layout(const HashParams &P, bool fill) {
     SmemLayout S;
-    S.hist_bytes = (P.hist16 ? 2 : 4) * P.hb;
+    S.hist_bytes = (P.hist16 || (!fill && P.count16) ? 2 : 4) * P.hb;
     S.hist_bytes = (S.hist_bytes + 15) & ~15;
     // enriched-bucket bitmap: the fill pass's, and the u32 counting pass's
     S.bitmap_bytes = (fill || !P.hist16) ? (((P.hb + 31) / 32) * 4 + 15) & ~15 : 0;
@@ -299,11 +300,11 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
         }
     };
     const int n_flat = P.partitioned ? s_cb[P.n_chunks] : 0;  // the unit's l-mers
-    if (P.partitioned) {
-        // counting needs no order: warp w takes pieces w, w + W, ... (W warps),
-        // the first 256 entries of four pieces at a time, each lane 32 loads in
-        // flight ahead of their increments (the pieces stream from HBM), then
-        // what long pieces hold beyond that; u32 counters in this mode
+    // the unit's keys (relative to its part) in any order: warp w takes pieces
+    // w, w + W, ... (W warps), the first 256 entries of four pieces at a time,
+    // each lane 32 loads in flight ahead of their increments (the pieces stream
+    // from HBM), then what long pieces hold beyond that
+    auto walk = [&](auto &&f) {
         for (int c0 = warp; c0 < P.n_chunks; c0 += 4 * kWarps) {
             uint32_t r[4][8];
 #pragma unroll
@@ -321,7 +322,7 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
             for (int j = 0; j < 4; ++j)
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
-                    if (r[j][q] != 0xFFFFFFFFu) bump(r[j][q]);
+                    if (r[j][q] != 0xFFFFFFFFu) f(r[j][q]);
         }
         for (int c = warp; c < P.n_chunks; c += kWarps) {
             const int len = s_cb[c + 1] - s_cb[c];
@@ -335,9 +336,87 @@ __device__ __forceinline__ void hash_unit(const HashParams &P, const int unit, u
                 }
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
-                    if (r[q] != 0xFFFFFFFFu) bump(r[q]);
+                    if (r[q] != 0xFFFFFFFFu) f(r[q]);
             }
         }
+    };
+    if constexpr (!FILL) {
+        if (P.count16) {
+            // Partitioned counting pass in 64 KB of counters, so that several
+            // units share an SM: u16 counters over the part's 2^15 keys when the
+            // unit holds at most 65,535 l-mers (no counter can overflow), else two
+            // rounds of u32 counters over 2^14 keys each, both walking all the
+            // unit's l-mers.  A bucket is marked in the bitmap at the increment
+            // that brings it to s; the marks, in key order, are the unit's list.
+            const bool wide = n_flat > 65535;  // block-uniform
+            const int rounds = wide ? 2 : 1;
+            const uint32_t span = wide ? hb / 2 : hb;
+            int NBt = 0, NMt = 0;
+            for (int rd = 0; rd < rounds; ++rd) {
+                const uint32_t k0 = (uint32_t)rd * span;
+                if (rd > 0) {
+                    for (int w = tid; w < hist_words / 4; w += kThreads)
+                        reinterpret_cast<uint4 *>(hist32)[w] = make_uint4(0u, 0u, 0u, 0u);
+                    for (int w = tid; w < S.bitmap_bytes / 4; w += kThreads) bitmap[w] = 0u;
+                    __syncthreads();
+                }
+                walk([&](uint32_t r) {
+                    const uint32_t q = r - k0;
+                    if (q >= span) return;
+                    uint32_t c;
+                    if (wide) {
+                        c = atomicAdd(&hist32[q], 1u);
+                    } else {
+                        const uint32_t sh = 16u * (q & 1u);
+                        c = (atomicAdd(&hist32[q >> 1], 1u << sh) >> sh) & 0xFFFFu;
+                    }
+                    if (c == (uint32_t)(P.s - 1)) atomicOr(&bitmap[q >> 5], 1u << (q & 31u));
+                });
+                __syncthreads();
+                const int nwb = (int)((span + 31) >> 5);
+                const int per = (nwb + kThreads - 1) / kThreads;
+                const int w0 = min(tid * per, nwb), w1 = min(w0 + per, nwb);
+                auto cnt = [&](uint32_t q) { return wide ? hist32[q] : (uint32_t)hist16[q]; };
+                if (P.counts_out) {
+                    uint32_t *dst = P.counts_out + (((int64_t)trial_local) << (2 * P.k)) + lo_key + k0;
+                    for (uint32_t q = tid; q < span; q += kThreads) dst[q] = cnt(q);
+                }
+                int nb = 0, nm = 0;
+                for (int w = w0; w < w1; ++w) {
+                    uint32_t bits = bitmap[w];
+                    nb += __popc(bits);
+                    while (bits) {
+                        const uint32_t q = 32u * w + (uint32_t)(__ffs(bits) - 1);
+                        bits &= bits - 1u;
+                        nm += (int)cnt(q);
+                    }
+                }
+                int rb, rm, NB, NM;
+                block_scan2<NT>(nb, nm, rb, rm, NB, NM, s_warp);
+                if (P.emit) {
+                    uint2 *dst = P.emit + P.emit_off[unit] + NBt;
+                    for (int w = w0; w < w1; ++w) {
+                        uint32_t bits = bitmap[w];
+                        while (bits) {
+                            const uint32_t q = 32u * w + (uint32_t)(__ffs(bits) - 1);
+                            bits &= bits - 1u;
+                            dst[rb++] = make_uint2(k0 + q, cnt(q));
+                        }
+                    }
+                }
+                NBt += NB;
+                NMt += NM;
+                __syncthreads();  // the next round clears what this one read
+            }
+            if (tid == 0) {
+                P.part_nb[unit] = NBt;
+                P.part_nm[unit] = NMt;
+            }
+            return;
+        }
+    }
+    if (P.partitioned) {
+        walk(bump);  // u32 counters in this mode
     } else {
         int i = 0;
         for (int gid = tid; gid < P.x; gid += kThreads) {
@@ -1263,6 +1342,7 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
     if (partitioned) {
         P.partitioned = 1;
         PROJ_REQUIRE(P.hb == (int)kPartKeys && !P.hist16, "partitioned mode expects u32 parts");
+        P.count16 = 1;  // the counting pass in 64 KB (two units per SM)
         P.n_chunks = (int)((L.x + kSortChunk - 1) / kSortChunk);
         PROJ_REQUIRE(P.n_chunks <= kMaxSortChunks,
                      "%lld l-mers exceed the partitioned mode's %d chunks of %d",
@@ -1382,8 +1462,16 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
             std::lock_guard<std::mutex> lk(g_hash_tune_mu);
             g_hash_tuned[hash_shape_key(P, n_units)] = nt;
         } else {
+            // a partitioned counting pass runs two 512-thread units per SM
+            // (measured: 1024 threads, one unit per SM, 24% slower; 256 threads 6%)
+            int cnt_nt = nt;
+            if (P.count16) {
+                cnt_nt = 512;
+                if (const char *f = getenv("PROJ_HASH_NT"))
+                    if (atoi(f) == 1024) cnt_nt = 1024;
+            }
             TraceSpan ts_("hash_count", st);
-            PROJ_TRY(launch_hash<false>(P, (unsigned)n_units, S1.total, st, nt));
+            PROJ_TRY(launch_hash<false>(P, (unsigned)n_units, S1.total, st, cnt_nt));
         }
         {
             TraceSpan ts_("hash_scan", st);

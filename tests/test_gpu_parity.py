@@ -199,6 +199,24 @@ def test_hash_degenerate_single_base_input(P):
     assert int(want["cand_cnt"].max()) == 2 * (1500 - 10 + 1)
 
 
+def test_hash_partitioned_unit_beyond_u16(P):
+    """A key-range part of one trial holding more than 65,535 l-mers (a long run
+    of one base puts them all in bucket 0): the counting pass counts that unit in
+    two rounds of u32 counters instead of u16 ones; lists and counts stay
+    bit-exact (Algorithm 2 steps 2c-3)."""
+    rng = np.random.default_rng(14)
+    tail = np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, 3000)].tobytes()
+    ascii_ = b"A" * 90000 + tail
+    off = np.array([0, 90000, 93000], np.int64)
+    codes = O.encode(ascii_)
+    packed = upload(P, ascii_)
+    h = P.trial_hash(packed, off, 16, 9, 2, 14, 0, 2, want_counts=True)
+    want = O.hash_trials(codes, off, 16, 9, 2, 14, 0, 2, with_counts=True)
+    assert_hash_equal(hash_np(h), want)
+    assert np.array_equal(h["counts"].cpu().numpy().view(np.uint32), want["counts"])
+    assert int(want["cand_cnt"].max()) == 90000 - 16 + 1
+
+
 def test_hash_capacity_overflow_reports_totals(P, native_lib):
     inst = instance_for_config(1)
     packed = upload(P, inst.ascii)
