@@ -741,21 +741,26 @@ __global__ void em_tc_reduce_kernel(const float *__restrict__ part_acc,
         const int mid = (lo + hi + 1) >> 1;
         if (inst[mid].cand_begin <= (int64_t)c) lo = mid; else hi = mid - 1;
     }
-    if (mstep && (int)q < 4 * inst[lo].l) {
-        float s = 0.f;
-        double sites = (double)inst[lo].t;  // OOPS: one site per sequence
-        for (int g = 0; g < G; ++g) s += part_acc[((int64_t)g * C + c) * stride + q];
-        if (inst[lo].gamma < 1.0) {
-            sites = 0.0;
-            for (int g = 0; g < G; ++g) sites += part_zs[(int64_t)g * C + c];
+    // group sums in group order, the loads of eight groups in flight at a time
+    // (adding the zero that pads the last batch changes no sum)
+    auto fold = [&](auto load, auto zero) {
+        auto s = zero;
+        for (int g0 = 0; g0 < G; g0 += 8) {
+            decltype(zero) v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = g0 + u < G ? load(g0 + u) : zero;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += v[u];
         }
+        return s;
+    };
+    if (mstep && (int)q < 4 * inst[lo].l) {
+        const float s = fold([&](int g) { return part_acc[((int64_t)g * C + c) * stride + q]; }, 0.f);
+        double sites = (double)inst[lo].t;  // OOPS: one site per sequence
+        if (inst[lo].gamma < 1.0) sites = fold([&](int g) { return part_zs[(int64_t)g * C + c]; }, 0.0);
         theta_out[idx] = (s + beta) / (float)(sites + 4.0 * (double)beta);
     }
-    if (q == 0) {
-        double s = 0.0;
-        for (int g = 0; g < G; ++g) s += part_ll[(int64_t)g * C + c];
-        ll_out[c] = s;
-    }
+    if (q == 0) ll_out[c] = fold([&](int g) { return part_ll[(int64_t)g * C + c]; }, 0.0);
 }
 
 template <int KP, int H>
