@@ -690,12 +690,17 @@ constexpr int kStageSeqs = (kSortChunk - kStageWords - 2) / 2 - 1;
 // keys (conflict-free stores of a lane's 32 consecutive keys).
 constexpr int kDenseBlocks = 32 * kSortWarps;
 constexpr int kDenseSeqs = 255;
-// shared memory: region A (base-indexed keys of a dense chunk, later the
-// grouped output; other chunks stage words and offsets there first) | region B
-// (keys and places by l-mer; a dense chunk's packed words first) | region C
-// (a dense chunk's sequence offsets)
+// shared memory: region A (a dense chunk's part masks per block; other chunks
+// stage words and offsets there, then the grouped output) | region B (other
+// chunks: keys and places by l-mer; a dense chunk: its packed words, then the
+// part counts and offsets per block) | region C (a dense chunk's sequence
+// offsets) | region D (a dense chunk's grouped output)
 constexpr int kRegionA = kDenseBlocks * 33;
-constexpr int kSortSmem = (kRegionA + kSortChunk + 2 * (kDenseSeqs + 1)) * 4;
+constexpr int kDenseCountOff = 1024;  // words of region B before a dense chunk's part counts
+constexpr int kSortSmem = (kRegionA + kSortChunk + 2 * (kDenseSeqs + 1) + kSortChunk) * 4;
+static_assert(kMaxParts * kDenseBlocks <= kRegionA && 2 * kDenseBlocks + 4 <= kDenseCountOff &&
+                  kDenseCountOff + kMaxParts * kDenseBlocks / 2 <= kSortChunk,
+              "dense chunk layout: part masks in region A, words and part counts in region B");
 static_assert(kRegionA >= kSortChunk && kStageWords + 2 + 2 * (kStageSeqs + 1) <= kRegionA,
               "region A holds the grouped output and the staged input");
 
@@ -761,12 +766,14 @@ __global__ void chunk_info_kernel(const HashParams P, int *__restrict__ info) {
     o[1] = i1;
     o[2] = (int)w_lo;
     o[3] = nst;
-    o[4] = (vb < kDenseBlocks && i1 - i0 + 1 <= kDenseSeqs) ? 1 : 0;
+    bool dense = vb < kDenseBlocks && i1 - i0 + 1 <= kDenseSeqs;
+    for (int q = i0; dense && q <= i1; ++q) dense = P.seq_off[q + 1] - P.seq_off[q] >= 32;
+    o[4] = dense ? 1 : 0;  // (a block of 32 bases then meets at most two sequences)
     o[5] = (int)(vb < kDenseBlocks ? vb : kDenseBlocks);
 }
 
 template <int K>
-__global__ void __launch_bounds__(kSortThreads, 3) part_sort_kernel(const HashParams P,
+__global__ void __launch_bounds__(kSortThreads, 2) part_sort_kernel(const HashParams P,
                                                                     uint16_t *__restrict__ orel,
                                                                     uint16_t *__restrict__ olid,
                                                                     int32_t *__restrict__ pstart) {
@@ -775,11 +782,10 @@ __global__ void __launch_bounds__(kSortThreads, 3) part_sort_kernel(const HashPa
     uint32_t *s_key = s_dyn + kRegionA;       // region B: key | place << 20 of chunk l-mer j at [j]
     int32_t *s_doff = reinterpret_cast<int32_t *>(s_key + kSortChunk);  // region C [kDenseSeqs + 1]
     int32_t *s_dlm = s_doff + kDenseSeqs + 1;                             // [kDenseSeqs + 1]
-    uint32_t *s_out = s_a;                    // grouped output, once the keys are ranked
+    uint32_t *s_dout = reinterpret_cast<uint32_t *>(s_dlm + kDenseSeqs + 1);  // region D
     __shared__ int s_pos[16];
     __shared__ int s_cnt[kSortWarps][kMaxParts];  // per warp: sizes, then output offsets
     __shared__ int s_tot[kMaxParts + 1];
-    __shared__ int s_wn[kSortWarps];              // dense: l-mers per warp
     const int trial_local = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const unsigned below = (1u << lane) - 1u;
@@ -789,6 +795,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) part_sort_kernel(const HashPa
     const int i0 = ci[0], i1 = ci[1], w_lo = ci[2], nst = ci[3], vb1 = ci[5];
     const bool dense = K > 0 && ci[4] != 0;
     const bool staged = !dense && nst >= 0;
+    uint32_t *s_out = dense ? s_dout : s_a;  // the grouped output
     const int nq = i1 - i0 + 1;  // sequences the chunk touches
     trial_positions(P, trial_local, s_pos);
     // l-mer-by-l-mer key build: words and offsets staged in region A
@@ -817,14 +824,44 @@ __global__ void __launch_bounds__(kSortThreads, 3) part_sort_kernel(const HashPa
 
     if constexpr (K > 0) {
         if (dense) {
-            // Keys of every base of block v = 32 warp + lane.  Row 2(K-1-q) of a
-            // 32 x 32 bit matrix holds the low code bits of projected position q
-            // for the block's 32 starts, row 2(K-1-q)+1 the high bits; transposed,
-            // word i is the key of the l-mer starting at base 32v + i, first
-            // projected position most significant (Section 6).
+            // Lane i of warp w takes the 32 bases of block v = 32w + i.  Row
+            // 2(K-1-q) of a 32 x 32 bit matrix holds the low code bits of
+            // projected position q for the block's 32 starts, row 2(K-1-q)+1 the
+            // high bits.  Before the transpose, the rows of the part bits (key
+            // bits 15 ..) give by a tree of ANDs the mask of the block's l-mers of
+            // every part; transposed, word i is the key of the l-mer starting at
+            // base 32v + i, first projected position most significant (Section
+            // 6).  An l-mer's place in its part's group is the part's start + the
+            // part's l-mers of earlier blocks + those below it in its block's
+            // mask: a stable grouping with no ranking rounds.
+            uint32_t *s_mask = s_a;  // [kMaxParts][kDenseBlocks]
+            uint16_t *s_pc = reinterpret_cast<uint16_t *>(s_key + kDenseCountOff);  // same shape
             const int v = 32 * warp + lane;
-            if (v <= vb1) {
-                uint32_t a[32];
+            const bool has = v <= vb1;
+            uint32_t a[32];
+            uint32_t valid = 0u;  // bases of the block where an l-mer of the chunk starts
+            int c1 = 0, c2 = 0, split = 32;  // id = base + c1 below split, + c2 from it
+            if (has) {
+                const int lb0 = 32 * v;
+                int q = 0, hi = nq - 1;  // last sequence starting at or before base lb0
+                while (q < hi) {
+                    const int mid = (q + hi + 1) >> 1;
+                    if (s_doff[mid] <= lb0) q = mid; else hi = mid - 1;
+                }
+                auto starts = [&](int qq, int &cq) {  // sequence qq's bits of the block
+                    const int sb = s_doff[qq];
+                    cq = s_dlm[qq] - g0 - sb;  // chunk-local id = base + cq
+                    const int lo = max(sb, -cq), hi2 = min(sb + (s_dlm[qq + 1] - s_dlm[qq]), n - cq);
+                    const int l0 = min(max(lo - lb0, 0), 32), h0 = min(max(hi2 - lb0, 0), 32);
+                    const uint32_t mh = h0 >= 32 ? 0xFFFFFFFFu : ((1u << h0) - 1u);
+                    const uint32_t ml = l0 >= 32 ? 0xFFFFFFFFu : ((1u << l0) - 1u);
+                    return mh & ~ml;
+                };
+                valid = starts(q, c1);
+                if (q + 1 < nq && s_doff[q + 1] < lb0 + 32) {
+                    split = s_doff[q + 1] - lb0;
+                    valid |= starts(q + 1, c2);
+                }
                 const uint2 w01 = *reinterpret_cast<const uint2 *>(s_key + 2 * v);
                 const uint2 w23 = *reinterpret_cast<const uint2 *>(s_key + 2 * v + 2);
                 uint32_t lo0, hi0, lo1, hi1;
@@ -833,76 +870,98 @@ __global__ void __launch_bounds__(kSortThreads, 3) part_sort_kernel(const HashPa
 #pragma unroll
                 for (int r = 0; r < 32; ++r) a[r] = 0u;
 #pragma unroll
-                for (int q = 0; q < K; ++q) {
-                    a[2 * (K - 1 - q)] = __funnelshift_r(lo0, lo1, pos[q]);
-                    a[2 * (K - 1 - q) + 1] = __funnelshift_r(hi0, hi1, pos[q]);
+                for (int qq = 0; qq < K; ++qq) {
+                    a[2 * (K - 1 - qq)] = __funnelshift_r(lo0, lo1, pos[qq]);
+                    a[2 * (K - 1 - qq) + 1] = __funnelshift_r(hi0, hi1, pos[qq]);
+                }
+                // part masks: part bit j is key bit kPartShift + j (zero rows past 2K)
+                const uint32_t b0 = a[kPartShift], b1 = a[kPartShift + 1], b2 = a[kPartShift + 2],
+                               b3 = a[kPartShift + 3], b4 = a[kPartShift + 4];
+                uint32_t t1[2], t2[4], t3[8], t4[16];
+                t1[0] = valid & ~b4;
+                t1[1] = valid & b4;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) t2[u] = t1[u >> 1] & ((u & 1) ? b3 : ~b3);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) t3[u] = t2[u >> 1] & ((u & 1) ? b2 : ~b2);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) t4[u] = t3[u >> 1] & ((u & 1) ? b1 : ~b1);
+#pragma unroll
+                for (int u = 0; u < 32; ++u) {
+                    const uint32_t mk = t4[u >> 1] & ((u & 1) ? b0 : ~b0);
+                    s_mask[u * kDenseBlocks + v] = mk;
+                    s_pc[u * kDenseBlocks + v] = (uint16_t)__popc(mk);
                 }
                 transpose_level<16, 0x0000FFFFu>(a);
                 transpose_level<8, 0x00FF00FFu>(a);
                 transpose_level<4, 0x0F0F0F0Fu>(a);
                 transpose_level<2, 0x33333333u>(a);
                 transpose_level<1, 0x55555555u>(a);
+            }
+            __syncthreads();
+            // per part: exclusive prefix of the blocks' counts (nine per lane) and
+            // the part's size
+            const int nb = vb1 + 1;
+            for (int p = warp; p < kMaxParts; p += kSortWarps) {
+                uint16_t *row = s_pc + p * kDenseBlocks;
+                int c9[9], run = 0;
 #pragma unroll
-                for (int i = 0; i < 32; ++i) s_a[33 * v + i] = a[i];  // base 32v + i at 33v + i
-            }
-            __syncthreads();  // region B's words are read; it now takes the ranked keys
-
-            // Ranking, warp by warp over its 1024 bases in rounds of 32 (lane i:
-            // base 1024 warp + 32r + i); inactive lanes are bases where no l-mer
-            // of the chunk starts.  Five ballots on the part bits give lane p the
-            // active lanes of part p, whose running count it keeps; every lane
-            // reads both from the lane of its part.  Each l-mer's place among its
-            // warp's l-mers of its part keeps l-mer order, with no shared-memory
-            // round trip (match_any, measured, was 16% slower).
-            const int lb0 = 1024 * warp + lane;
-            int q = 0, hi = nq - 1;  // last sequence starting at or before base lb0
-            while (q < hi) {
-                const int mid = (q + hi + 1) >> 1;
-                if (s_doff[mid] <= lb0) q = mid; else hi = mid - 1;
-            }
-            // sequence q's first base, the next sequence's, its first l-mer and l-mer count
-            int soff = s_doff[q], snext = q + 1 < nq ? s_doff[q + 1] : INT_MAX;
-            int lmq = s_dlm[q], nsq = s_dlm[q + 1] - lmq;
-            uint32_t run = 0u;  // lane p: this warp's l-mers of part p so far
-            int nvalid = 0;
-            const int rounds = min(32, vb1 + 1 - 32 * warp);
-            for (int r = 0; r < rounds; ++r) {
-                const int lb = lb0 + 32 * r;
-                while (snext <= lb) {
-                    ++q;
-                    soff = snext;
-                    snext = q + 1 < nq ? s_doff[q + 1] : INT_MAX;
-                    lmq = s_dlm[q];
-                    nsq = s_dlm[q + 1] - lmq;
+                for (int j = 0; j < 9; ++j) {
+                    const int vv = 9 * lane + j;
+                    c9[j] = vv < nb ? (int)row[vv] : 0;
+                    run += c9[j];
                 }
-                const int jl = lb - soff;
-                const int e = lmq - g0 + jl;
-                const bool act = jl >= 0 && jl < nsq && e >= 0 && e < n;
-                const unsigned amask = __ballot_sync(0xffffffffu, act);
-                const uint32_t key = s_a[lb + (lb >> 5)];  // every base of the blocks has one
-                const uint32_t part = key >> kPartShift;
-                unsigned mine = amask;  // active lanes whose part is this lane's index
+                int sc = run;
 #pragma unroll
-                for (int bit = 0; bit < 5; ++bit) {
-                    const unsigned B = __ballot_sync(0xffffffffu, (part >> bit) & 1u);
-                    mine &= ~(B ^ (0u - ((uint32_t)(lane >> bit) & 1u)));
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, sc, o);
+                    if (lane >= o) sc += u;
                 }
-                // lane `part` holds the active lanes with this lane's part and
-                // their count in the warp's earlier rounds
-                const unsigned same = __shfl_sync(0xffffffffu, mine, (int)(part & 31u));
-                const uint32_t before = __shfl_sync(0xffffffffu, run, (int)(part & 31u));
-                // keys < 2^20, places < 2^10
-                if (act) s_key[e] = key | ((before + __popc(same & below)) << 20);
-                run += __popc(mine);
-                nvalid += __popc(amask);
+                int at = sc - run;
+#pragma unroll
+                for (int j = 0; j < 9; ++j) {
+                    const int vv = 9 * lane + j;
+                    if (vv < nb) row[vv] = (uint16_t)at;
+                    at += c9[j];
+                }
+                if (lane == 31) s_tot[p] = sc;
             }
-            s_cnt[warp][lane] = (int)run;
-            if (lane == 0) s_wn[warp] = nvalid;
+            __syncthreads();
+            if (warp == 0) {
+                const int tv = s_tot[lane];
+                int sc = tv;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, sc, o);
+                    if (lane >= o) sc += u;
+                }
+                s_tot[lane] = sc - tv;
+                if (lane == 31) s_tot[kMaxParts] = sc;
+            }
+            __syncthreads();
+            if (tid <= P.parts)
+                pstart[((int64_t)trial_local * P.n_chunks + chunk) * (P.parts + 1) + tid] = s_tot[tid];
+            if (has) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    if ((valid >> i) & 1u) {
+                        const uint32_t key = a[i], part = key >> kPartShift;
+                        const uint32_t mk = s_mask[part * kDenseBlocks + v];
+                        const int d = s_tot[part] + (int)s_pc[part * kDenseBlocks + v] +
+                                      __popc(mk & ((1u << i) - 1u));
+                        const int e = 32 * v + i + (i < split ? c1 : c2);
+                        s_dout[d] = (key & (kPartKeys - 1u)) | ((uint32_t)e << 16);
+                    }
+                }
+            }
         }
     }
     if (!dense) {
         // warps 0-7: 1024 l-mers each in rounds of 32 (lane i: l-mer j0 + 32r + i),
-        // keys built here
+        // keys built here.  Five ballots on the part bits give lane p the active
+        // lanes of part p, whose running count it keeps; every lane reads both
+        // from the lane of its part, so each l-mer's place among its warp's
+        // l-mers of its part keeps l-mer order with no shared-memory round trip.
         const int j0 = warp * 1024, j1 = min(j0 + 1024, n);
         int i = 0;  // sequence of this lane's l-mer, relative to i0
         uint32_t run = 0u;  // lane p: this warp's l-mers of part p so far
@@ -927,7 +986,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) part_sort_kernel(const HashPa
                 }
             }
             const uint32_t part = key >> kPartShift;
-            unsigned mine = amask;  // as in the dense ranking
+            unsigned mine = amask;
 #pragma unroll
             for (int bit = 0; bit < 5; ++bit) {
                 const unsigned B = __ballot_sync(0xffffffffu, (part >> bit) & 1u);
@@ -939,49 +998,36 @@ __global__ void __launch_bounds__(kSortThreads, 3) part_sort_kernel(const HashPa
             run += __popc(mine);
         }
         s_cnt[warp][lane] = (int)run;
-    }
-    __syncthreads();
-    // part p starts at s_tot[p] in the chunk; warp w's entries of part p follow
-    // those of warps w' < w
-    if (tid < kMaxParts) {
-        int a = 0;
-        for (int w = 0; w < kSortWarps; ++w) {
-            const int v = s_cnt[w][tid];
-            s_cnt[w][tid] = a;
-            a += v;
+        __syncthreads();
+        // part p starts at s_tot[p] in the chunk; warp w's entries of part p follow
+        // those of warps w' < w
+        if (tid < kMaxParts) {
+            int a = 0;
+            for (int w = 0; w < kSortWarps; ++w) {
+                const int v = s_cnt[w][tid];
+                s_cnt[w][tid] = a;
+                a += v;
+            }
+            s_tot[tid] = a;
         }
-        s_tot[tid] = a;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int v = s_tot[lane];
-        int sc = v;
+        __syncthreads();
+        if (warp == 0) {
+            const int v = s_tot[lane];
+            int sc = v;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, sc, o);
-            if (lane >= o) sc += u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, sc, o);
+                if (lane >= o) sc += u;
+            }
+            s_tot[lane] = sc - v;
+            if (lane == 31) s_tot[kMaxParts] = sc;
         }
-        s_tot[lane] = sc - v;
-        if (lane == 31) s_tot[kMaxParts] = sc;
-    }
-    __syncthreads();
-    if (tid <= P.parts)
-        pstart[((int64_t)trial_local * P.n_chunks + chunk) * (P.parts + 1) + tid] = s_tot[tid];
-
-    // stable placement into shared memory: after all of part p of warps w' < w,
-    // at the l-mer's place among warp w's l-mers of p; entry = (key - part * hb)
-    // | chunk-local id << 16
-    if (dense) {  // warp w ranked the l-mers [e0, e0 + s_wn[w]) of its bases
-        int e0 = 0;
-        for (int w = 0; w < warp; ++w) e0 += s_wn[w];
-        const int e1 = e0 + s_wn[warp];
-        for (int j = e0 + lane; j < e1; j += 32) {
-            const uint32_t v = s_key[j];
-            const uint32_t key = v & 0xFFFFFu, part = key >> kPartShift;
-            s_out[s_tot[part] + s_cnt[warp][part] + (int)(v >> 20)] =
-                (key & (kPartKeys - 1u)) | ((uint32_t)j << 16);
-        }
-    } else {
+        __syncthreads();
+        if (tid <= P.parts)
+            pstart[((int64_t)trial_local * P.n_chunks + chunk) * (P.parts + 1) + tid] = s_tot[tid];
+        // stable placement into shared memory: after all of part p of warps
+        // w' < w, at the l-mer's place among warp w's l-mers of p; entry =
+        // (key - part * hb) | chunk-local id << 16
         for (int j = tid; j < n; j += kSortThreads) {
             const uint32_t v = s_key[j];
             const uint32_t key = v & 0xFFFFFu, part = key >> kPartShift;
