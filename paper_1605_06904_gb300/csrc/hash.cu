@@ -1255,6 +1255,60 @@ __global__ void __launch_bounds__(kThreads) gather_sel_kernel(
     if (P.partitioned) {
         unit_walk_setup(P, trial_local, (int)part, s_cb, s_pb, s_warp);
         n_iter = s_cb[P.n_chunks];
+        // Warp w takes the unit's entries [w W, w W + W) in rounds of 32, eight
+        // rounds' loads in flight; an entry matches when its key is the
+        // bucket's.  A first walk counts each warp's matches, a scan places the
+        // warps, and a second walk writes the matches' l-mer ids in entry order
+        // (the unit's entries are in l-mer order), ranked by ballots.
+        const unsigned below = (1u << lane) - 1u;
+        const int W = (int)(((n_iter + kWarps - 1) / kWarps + 31) & ~31);
+        const int f0 = min((int)n_iter, warp * W), f1 = min((int)n_iter, f0 + W);
+        auto walk = [&](bool write, int64_t at) {
+            int cnt = 0, c = 0;
+            for (int fb = f0; fb < f1; fb += 8 * 32) {
+                uint32_t rv[8];
+                int cc[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int f = fb + 32 * u + lane;
+                    rv[u] = 0xFFFFFFFFu;
+                    cc[u] = 0;
+                    if (f < f1) {
+                        while (s_cb[c + 1] <= f) ++c;
+                        cc[u] = c;
+                        rv[u] = P.prel[s_pb[c] + f];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const bool e = rv[u] == rel;
+                    const uint32_t bal = __ballot_sync(0xffffffffu, e);
+                    if (write && e) {
+                        const int f = fb + 32 * u + lane;
+                        const int64_t q = at + cnt + __popc(bal & below);
+                        if (q < len) out[o0 + q] = cc[u] * kSortChunk + (int)P.plid[s_pb[cc[u]] + f];
+                    }
+                    cnt += __popc(bal);
+                }
+            }
+            return cnt;
+        };
+        const int found = walk(false, 0);
+        if (lane == 0) s_round[warp] = found;
+        __syncthreads();
+        if (warp == 0) {
+            const int v = lane < kWarps ? s_round[lane] : 0;
+            int sc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, sc, o);
+                if (lane >= o) sc += u;
+            }
+            if (lane < kWarps) s_round[lane] = sc - v;
+        }
+        __syncthreads();
+        walk(true, s_round[warp]);
+        return;
     } else {
         n_iter = P.x;
         trial_positions(P, trial_local, s_pos);
@@ -1262,24 +1316,18 @@ __global__ void __launch_bounds__(kThreads) gather_sel_kernel(
     }
     int pos[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) pos[q] = (!P.partitioned && q < P.k) ? s_pos[q] : 0;
-    int i = 0, c = 0;
+    for (int q = 0; q < 16; ++q) pos[q] = q < P.k ? s_pos[q] : 0;
+    int i = 0;
     int64_t running = 0;
     for (int64_t base = 0; base < n_iter; base += kThreads) {
         const int64_t it = base + tid;
         bool e = false;
         int gid = 0;
         if (it < n_iter) {
-            if (P.partitioned) {
-                while (s_cb[c + 1] <= it) ++c;
-                e = P.prel[s_pb[c] + it] == rel;
-                if (e) gid = c * kSortChunk + (int)P.plid[s_pb[c] + it];
-            } else {
-                gid = (int)it;
-                while (__ldg(P.lmer_off + i + 1) <= gid) ++i;
-                const int64_t b0 = (int64_t)__ldg(P.seq_off + i) + (gid - __ldg(P.lmer_off + i));
-                e = lmer_key(window64(P.packed, P.nwords, b0), pos, P.k) == key;
-            }
+            gid = (int)it;
+            while (__ldg(P.lmer_off + i + 1) <= gid) ++i;
+            const int64_t b0 = (int64_t)__ldg(P.seq_off + i) + (gid - __ldg(P.lmer_off + i));
+            e = lmer_key(window64(P.packed, P.nwords, b0), pos, P.k) == key;
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, e);
         if (lane == 0) s_round[warp] = __popc(bal);
