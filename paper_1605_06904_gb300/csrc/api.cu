@@ -406,6 +406,7 @@ static int hash_and_select(const uint32_t *packed, const Layout &L, int k, int s
             int32_t *nm = reinterpret_cast<int32_t *>(sd + n);
             PROJ_CUDA_TRY(cudaMemcpyAsync(no, no_h.data(), (n + 1) * 8, cudaMemcpyHostToDevice, st));
             PROJ_CUDA_TRY(cudaMemcpyAsync(sd, H.sel.data(), n * 8, cudaMemcpyHostToDevice, st));
+            PROJ_TRY(run_kept_table(H.hstate, sd, n, ho.cand_trial, ho.cand_key, st));
             PROJ_TRY(run_gather_members(packed, L, H.hstate, k, seed, sd, n, ho.cand_trial,
                                         ho.cand_key, no, nm, st));
             H.r_off = no;

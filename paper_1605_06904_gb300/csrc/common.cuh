@@ -113,6 +113,9 @@ struct HashState {
     const uint16_t *plid = nullptr;    //                   chunk-local l-mer ids
     const int32_t *pstart = nullptr;   //                   part starts per (trial, chunk)
     const uint8_t *pos_tab = nullptr;  // positions of the call's trials (null: drawn in-kernel)
+    // a table-only filling call: each unit's first candidate index, and the units
+    int64_t n_units = 0, trial_begin = 0;
+    const int64_t *cand_base = nullptr;
 };
 
 struct HashOut {
@@ -128,8 +131,10 @@ struct HashOut {
     int64_t *totals = nullptr;      // device int64[2]
     bool count_only = false;        // stop after the totals (sizing probe)
     bool want_emit = false;         // counting call: also keep each unit's enriched lists
-    bool table_only = false;        // filling call: candidate table from those lists, no
-                                    // members (the caller gathers the ones it keeps)
+    bool table_only = false;        // filling call: only the candidates' sizes, from those
+                                    // lists, and no members (the caller fills in the
+                                    // trials and keys of the ones it keeps and gathers
+                                    // their members)
 };
 
 // Both passes of the bucket kernels plus the scan between them.
@@ -140,6 +145,10 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
 // Members (ascending l-mer ids) of n selected candidates of a search whose
 // counting call kept its state: candidate sel[i] = (cand_trial, cand_key) of
 // the full list; its members go to new_members[new_off[i] .. new_off[i+1]).
+// Trials and keys of the kept candidates sel[0..n) (indices into the list of
+// all enriched buckets) after a table-only filling call, written at those indices.
+int run_kept_table(const HashState &hs, const int64_t *sel, int64_t n, int32_t *cand_trial,
+                   uint32_t *cand_key, cudaStream_t st);
 int run_gather_members(const uint32_t *packed, const Layout &L, const HashState &hs, int k,
                        uint64_t seed, const int64_t *sel, int64_t n, const int32_t *cand_trial,
                        const uint32_t *cand_key, const int64_t *new_off, int32_t *new_members,

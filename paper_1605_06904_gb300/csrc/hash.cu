@@ -1204,31 +1204,38 @@ __global__ void emit_cap_kernel(const int32_t *__restrict__ pstart, int n_chunks
     cap[u] = n / s;
 }
 
-// Candidate table from the counting pass's lists (no recount): unit u's
-// (key, size) entries go to cand_base[u] .., their member offsets continue
-// from mem_base[u] in key order.
-__global__ void __launch_bounds__(kThreads) hash_table_kernel(const HashParams P) {
-    __shared__ int2 s_warp[kWarps + 1];
-    const int unit = blockIdx.x, tid = threadIdx.x;
-    const int trial = (int)(P.trial_begin + unit / P.parts);
-    const uint32_t lo_key = (uint32_t)(unit % P.parts) * (uint32_t)P.hb;
+// Sizes of every enriched bucket from the counting pass's lists (no recount):
+// unit u's entries go to cand_cnt[cand_base[u] ..] in key order.  A search that
+// keeps only its largest buckets selects on these; the trials and keys of the
+// kept ones come from the lists afterwards (kept_table_kernel).
+__global__ void __launch_bounds__(256) hash_cnt_kernel(const HashParams P) {
+    const int unit = blockIdx.x;
     const uint2 *src = P.emit + P.emit_off[unit];
     const int nb = P.part_nb[unit];
     const int64_t cb = P.cand_base[unit];
-    int64_t run = P.mem_base[unit];
-    for (int base = 0; base < nb; base += kThreads) {
-        const int i = base + tid;
-        const uint2 e = i < nb ? src[i] : make_uint2(0u, 0u);
-        int pc, pz, tc, tz;
-        block_scan2((int)e.y, 0, pc, pz, tc, tz, s_warp);
-        if (i < nb && cb + i < P.cap_cand) {
-            P.cand_trial[cb + i] = trial;
-            P.cand_key[cb + i] = lo_key + e.x;
-            P.cand_cnt[cb + i] = (int32_t)e.y;
-            P.cand_off[cb + i] = run + pc;
-        }
-        run += tc;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+        if (cb + i < P.cap_cand) P.cand_cnt[cb + i] = (int32_t)src[i].y;
+}
+
+// Trial and key of each kept candidate c = sel[i] (an index into the list of
+// all enriched buckets): its unit is the last with cand_base <= c, its entry
+// the (c - cand_base)-th of that unit's list.
+__global__ void kept_table_kernel(const int64_t *__restrict__ cbase, int64_t n_units,
+                                  const int64_t *__restrict__ emit_off, const uint2 *__restrict__ emit,
+                                  int parts, int hb, int64_t trial_begin,
+                                  const int64_t *__restrict__ sel, int64_t n,
+                                  int32_t *__restrict__ cand_trial, uint32_t *__restrict__ cand_key) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t c = sel[i];
+    int64_t lo = 0, hi = n_units - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (cbase[mid] <= c) lo = mid; else hi = mid - 1;
     }
+    const uint2 e = emit[emit_off[lo] + (c - cbase[lo])];
+    cand_trial[c] = (int32_t)(trial_begin + lo / parts);
+    cand_key[c] = (uint32_t)(lo % parts) * (uint32_t)hb + e.x;
 }
 
 // Members of selected candidates (one CTA each), ascending: the l-mers of the
@@ -1592,9 +1599,12 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
         PROJ_REQUIRE(reuse && hs && hs->emitted, "a table-only fill needs the counting call's lists");
         {
             TraceSpan ts_("hash_table", st);
-            hash_table_kernel<<<(unsigned)n_units, kThreads, 0, st>>>(P);
+            hash_cnt_kernel<<<(unsigned)n_units, 256, 0, st>>>(P);
         }
-        PROJ_LAUNCH_CHECK("hash_table_kernel");
+        PROJ_LAUNCH_CHECK("hash_cnt_kernel");
+        hs->n_units = n_units;
+        hs->trial_begin = trial_begin;
+        hs->cand_base = cbase;
         return PROJ_OK;
     }
     P.emit = nullptr;
@@ -1616,6 +1626,22 @@ int run_trial_hash(const uint32_t *packed, const Layout &L, int k, int s, uint64
         TraceSpan ts_("hash_fill", st);
         PROJ_TRY(launch_hash<true>(P, (unsigned)n_units, S2.total, st, nt));
     }
+    return PROJ_OK;
+}
+
+int run_kept_table(const HashState &hs, const int64_t *sel, int64_t n, int32_t *cand_trial,
+                   uint32_t *cand_key, cudaStream_t st) {
+    PROJ_REQUIRE(hs.valid && hs.emitted && hs.cand_base, "the kept table needs the counting call's lists");
+    if (n == 0) return PROJ_OK;
+    const int64_t *eoff = hs.emit_buf.as<int64_t>();
+    const uint2 *emit = reinterpret_cast<const uint2 *>(eoff + 2 * hs.n_units + 1);
+    {
+        TraceSpan ts_("hash_table", st);
+        kept_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+            hs.cand_base, hs.n_units, eoff, emit, hs.parts, hs.hb, hs.trial_begin, sel, n, cand_trial,
+            cand_key);
+    }
+    PROJ_LAUNCH_CHECK("kept_table_kernel");
     return PROJ_OK;
 }
 
