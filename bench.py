@@ -349,6 +349,23 @@ def em_executed_flops(inst, R, iters):
     return ct * xt * per * (2 * iters + 1)
 
 
+def fp32_roofline(inst, R, iters, em_ms, em_launches, sm_mhz=2070.0):
+    """The FP32 EM kernel against its binding resource, the shared-memory pipe:
+    per score l reads of the log-odds (E-step) and, in M-step launches, a read
+    and a write of each of the l count entries and their compensation terms
+    (4l more); 32 four-byte accesses per clock per SM on 152 SMs."""
+    if not em_launches or em_ms <= 0:
+        return None
+    steps = em_launches / (iters + 1)
+    acc = steps * inst.n_lmers * R * (iters * 5 * inst.l + inst.l)
+    achieved = acc / (em_ms * 1e-3)
+    peak = 152 * 32 * sm_mhz * 1e6
+    return {"bound": "smem", "kernel": "em_fp32_kernel", "launches": em_launches,
+            "avg_launch_ms": em_ms / em_launches, "achieved": achieved, "peak": peak,
+            "unit": "shared-memory accesses/s", "frac": achieved / peak,
+            "peak_source": "152 SMs x 32 accesses/clock x %g MHz" % sm_mhz}
+
+
 def em_roofline(P, cfg, inst, R, iters, steps, em_ms, em_launches, pk, pk_kind):
     """Roofline of the tensor-core EM kernel: algorithmic FLOPs (the one-hot
     contractions at K = 4l: 8l per score for the E-step, 8l more in M-step
@@ -485,12 +502,16 @@ def sub_workload(P, cfg, dev, stream, flush, steps, pk, pk_kind, with_extras=Fal
         flush.fill_(0)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        P.projection_trace_enable(True)
         e0.record(stream)
         r32 = P.projection_find_packed(packed, inst.seq_off, inst.l, inst.d, k, s, m, seed=seed,
                                        em_iters=iters, pseudocount=beta, precision=P.PROJ_EM_FP32)
         e1.record(stream)
         torch.cuda.synchronize()
+        P.projection_trace_enable(False)
         out["fp32_ms_per_step"] = e0.elapsed_time(e1)
+        f_ms, f_launches = P.projection_trace_read("em_fp32")
+        out["fp32_roofline"] = fp32_roofline(inst, r32["n_refined"], iters, f_ms, f_launches)
         out["motif_found_fp32"] = r32["consensus"]
         out["allpairs_enrichment"] = allpairs_measure(P, inst, packed, k, s, seed, m, res, stream)
         out["protein_search"] = protein_measure(P, stream, flush)
@@ -754,10 +775,7 @@ def main():
 
     # ---- rooflines: the EM kernel (tensor pipe) and the hashing phase
     if prec == P.PROJ_EM_FP32:
-        roof = {"bound": "alu", "kernel": "em_fp32_kernel", "launches": em_launches,
-                "avg_launch_ms": em_ms / max(1, em_launches), "achieved": None, "peak": None,
-                "unit": "TFLOP/s", "frac": None, "traffic": None,
-                "note": "the FP32 path is bound by shared-memory gathers; timed for comparison"}
+        roof = fp32_roofline(inst, R, iters, em_ms, em_launches)
     else:
         roof = em_roofline(P, cfg, inst, R, iters, args.steps, em_ms, em_launches, pk, pk_kind)
     hroof = hash_roofline(P, k, m, x, args.steps, r["phases"], pk, pk_kind)
