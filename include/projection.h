@@ -407,9 +407,10 @@ int projection_trace_enable(int on);
 
 /* Sums the records of kernels whose name starts with `prefix` ("" = all):
  * *total_ms = summed device time, *launches = number of launches.  Waits for
- * the recorded events.  Kernel names: pack, background, positions,
- * hash_count, hash_scan, hash_fill, theta0, em_fp32, em_reduce, em_tc,
- * finalize. */
+ * the recorded events.  Kernel names: pack, background, positions, params,
+ * hash_partition, hash_count, hash_scan, hash_fill, hash_table, select,
+ * hash_gather, allpairs, enrich_sort, theta0, em_xtiles, em_tc, em_fp32,
+ * em_reduce, cand_sites, finalize (protein searches record under the same names). */
 int projection_trace_read(const char *prefix, double *total_ms, int64_t *launches);
 
 #ifdef __cplusplus
