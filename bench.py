@@ -432,7 +432,8 @@ def hash_roofline(P, k, m, x, steps, phases, pk=None, pk_kind=None):
 def measure_search(P, cfg, inst, packed, k, s, m, seed, iters, beta, top, steps, warmup, flush,
                    stream, prec, zoops=0.0, clocks=None):
     """Times `steps` searches of one workload (L2 flushed before each, CUDA
-    events on the launching stream) with every library kernel traced."""
+    events on the launching stream), then the same number again with every
+    library kernel traced for the per-kernel times."""
     import torch
     off = inst.seq_off
 
@@ -451,22 +452,30 @@ def measure_search(P, cfg, inst, packed, k, s, m, seed, iters, beta, top, steps,
     for _ in range(warmup):
         res = step()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
+
+    def timed(trace):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        P.projection_trace_enable(trace)
+        w0 = time.perf_counter()
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            out = step()  # synchronises on the result
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        w = time.perf_counter() - w0
+        P.projection_trace_enable(False)
+        return out, [a.elapsed_time(b) for a, b in ev], w
+
+    # the timed steps run without the library's per-launch event trace (its
+    # event records sit between the launches); a second pass over the same
+    # number of steps, traced, gives the per-kernel times
     if clocks:
         clocks.start()
-    P.projection_trace_enable(True)
-    wall0 = time.perf_counter()
-    for i in range(steps):
-        flush.fill_(i & 0xFF)
-        ev[i][0].record(stream)
-        res = step()  # synchronises on the result
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    P.projection_trace_enable(False)
+    res, step_ms, wall = timed(False)
     clk = clocks.stop() if clocks else None
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    _, _, _ = timed(True)
     phases = {n: P.projection_trace_read(n)[0] / steps for n in PHASES}
     phases = {n: v for n, v in phases.items() if v > 0}
     all_ms, all_launches = P.projection_trace_read("")

@@ -401,72 +401,83 @@ __global__ void __launch_bounds__(tc_threads<H>(), (KP <= 80 && H == 2 ? 2 : 1))
         __syncthreads();  // W is visible to the issuer (the one-hot tiles arrive on mbXfull)
 
         if (issuer) {
-            if (lane == 0) {
-                tc::fence_after_sync();
-                // operand descriptors; a start address advances by adding (bytes >> 4)
-                const uint64_t dWhi = tc::sdesc(tc::smem_addr(sWhi), 128, KP * 16);
-                const uint64_t dWlo = tc::sdesc(tc::smem_addr(sWlo), 128, KP * 16);
-                const uint64_t dXk = tc::sdesc(tc::smem_addr(sX), 128, KP * 16);   // K-major
-                const uint64_t dXmn = tc::sdesc(tc::smem_addr(sX), KP * 16, 128);  // MN-major
-                auto issue_scores = [&](uint32_t d, uint32_t slot) {
-                    const uint64_t dx = dXk + slot * kXSlot;
+            // The whole warp runs the issue loop: every value an MMA operand or a
+            // branch depends on is made warp-uniform (broadcast from lane 0 or
+            // voted), so the operands stay in uniform registers, and one elected
+            // lane issues each MMA and commit.
+            tc::fence_after_sync();
+            const uint32_t tmu = __shfl_sync(0xffffffffu, tm, 0);
+            const uint32_t tOu = tmu + 2 * NT;
+            const int nu = __shfl_sync(0xffffffffu, n, 0);
+            const int kqu = __shfl_sync(0xffffffffu, kq, 0);
+            const uint32_t idesc_ou = tc::idesc_bf16(128, 16 * kqu, true);
+            // operand descriptors; a start address advances by adding (bytes >> 4)
+            const uint64_t dWhi = tc::sdesc(tc::smem_addr(sWhi), 128, KP * 16);
+            const uint64_t dWlo = tc::sdesc(tc::smem_addr(sWlo), 128, KP * 16);
+            const uint64_t dXk = tc::sdesc(tc::smem_addr(sX), 128, KP * 16);   // K-major
+            const uint64_t dXmn = tc::sdesc(tc::smem_addr(sX), KP * 16, 128);  // MN-major
+            auto issue_scores = [&](uint32_t d, uint32_t slot) {
+                const uint64_t dx = dXk + slot * kXSlot;
 #pragma unroll
-                    for (int s = 0; s < KP / 16; ++s)
-                        if (s < kq) tc::mma_bf16(d, dWhi + 16 * s, dx + 16 * s, IDESC_S, s > 0);
+                for (int s = 0; s < KP / 16; ++s)
+                    if (s < kqu) tc::mma_bf16_w(d, dWhi + 16 * s, dx + 16 * s, IDESC_S, s > 0);
 #pragma unroll
-                    for (int s = 0; s < KP / 16; ++s)
-                        if (s < kq) tc::mma_bf16(d, dWlo + 16 * s, dx + 16 * s, IDESC_S, 1u);
-                };
-                ok = tc::mbar_wait(&mbXfull[0], phX & 1u, kWaitNs);
-                phX ^= 1u;
+                for (int s = 0; s < KP / 16; ++s)
+                    if (s < kqu) tc::mma_bf16_w(d, dWlo + 16 * s, dx + 16 * s, IDESC_S, 1u);
+            };
+            auto wait_all = [&](uint64_t *bar, uint32_t parity) {
+                return __all_sync(0xffffffffu, tc::mbar_wait(bar, parity, kWaitNs) ? 1 : 0) != 0;
+            };
+            ok = wait_all(&mbXfull[0], phX & 1u);
+            phX ^= 1u;
+            tc::fence_after_sync();
+            issue_scores(tmu, 0);
+            tc::mma_commit_w(&mbSfull[0]);
+            if (nu > 1 && ok) {
+                ok = wait_all(&mbXfull[1], (phX >> 1) & 1u);
+                phX ^= 2u;
                 tc::fence_after_sync();
-                issue_scores(tm, 0);
-                tc::mma_commit(&mbSfull[0]);
-                if (n > 1 && ok) {
-                    ok = tc::mbar_wait(&mbXfull[1], (phX >> 1) & 1u, kWaitNs);
-                    phX ^= 2u;
+                issue_scores(tmu + NT, 1);
+                tc::mma_commit_w(&mbSfull[1]);
+            }
+            TileIt<NT> ti;
+            ti.start(in, item.seq_lo, item.seq_hi);
+            for (int j = 0; j < nu && ok; ++j) {
+                if (P.mstep) {
+                    ok = wait_all(&mbPfull, phP);
+                    phP ^= 1u;
                     tc::fence_after_sync();
-                    issue_scores(tm + NT, 1);
-                    tc::mma_commit(&mbSfull[1]);
-                }
-                TileIt<NT> ti;
-                ti.start(in, item.seq_lo, item.seq_hi);
-                for (int j = 0; j < n && ok; ++j) {
-                    if (P.mstep) {
-                        ok = tc::mbar_wait(&mbPfull, phP, kWaitNs);
-                        phP ^= 1u;
-                        tc::fence_after_sync();
-                        const uint64_t dx = dXmn + (uint32_t)(j % LY::NX) * kXSlot;
-                        const uint32_t acc0 = ti.j0 > 0 ? 1u : 0u;  // O restarts with a sequence
-                        // P(j) in score buffer j&1: l-mers 16s..16s+15 at columns
-                        // 32(s/2) + 8(s%2) (hi) and 16 further (lo)
-                        const uint32_t tP = tm + NT * (uint32_t)(j & 1);
+                    const uint64_t dx = dXmn + (uint32_t)(j % LY::NX) * kXSlot;
+                    // O restarts with a sequence
+                    const uint32_t acc0 = __shfl_sync(0xffffffffu, ti.j0 > 0 ? 1u : 0u, 0);
+                    // P(j) in score buffer j&1: l-mers 16s..16s+15 at columns
+                    // 32(s/2) + 8(s%2) (hi) and 16 further (lo)
+                    const uint32_t tP = tmu + NT * (uint32_t)(j & 1);
 #pragma unroll
-                        for (int s = 0; s < NT / 16; ++s)
-                            tc::mma_bf16_ts(tO, tP + 32 * (s >> 1) + 8 * (s & 1), dx + 2 * KP * s,
-                                            idesc_o, s > 0 ? 1u : acc0);
+                    for (int s = 0; s < NT / 16; ++s)
+                        tc::mma_bf16_ts_w(tOu, tP + 32 * (s >> 1) + 8 * (s & 1), dx + 2 * KP * s,
+                                          idesc_ou, s > 0 ? 1u : acc0);
 #pragma unroll
-                        for (int s = 0; s < NT / 16; ++s)
-                            tc::mma_bf16_ts(tO, tP + 32 * (s >> 1) + 16 + 8 * (s & 1),
-                                            dx + 2 * KP * s, idesc_o, 1u);
-                        tc::mma_commit(&mbO);
-                    }
-                    if (j + 2 < n && ok) {
-                        const uint32_t xs = (uint32_t)((j + 2) % LY::NX), b = (uint32_t)(j & 1);
-                        ok = tc::mbar_wait(&mbXfull[xs], (phX >> xs) & 1u, kWaitNs);
-                        phX ^= 1u << xs;
-                        // an M-step's count MMA j, issued above after P(j) was written
-                        // (so after S(j) was read), precedes this MMA: no release needed
-                        if (!P.mstep) {
-                            if (ok) ok = tc::mbar_wait(&mbSfree[b], (phSfree >> b) & 1u, kWaitNs);
-                            phSfree ^= 1u << b;
-                        }
-                        tc::fence_after_sync();
-                        issue_scores(tm + NT * b, xs);
-                        tc::mma_commit(&mbSfull[b]);
-                    }
-                    ti.advance(in, item.seq_hi);
+                    for (int s = 0; s < NT / 16; ++s)
+                        tc::mma_bf16_ts_w(tOu, tP + 32 * (s >> 1) + 16 + 8 * (s & 1),
+                                          dx + 2 * KP * s, idesc_ou, 1u);
+                    tc::mma_commit_w(&mbO);
                 }
+                if (j + 2 < nu && ok) {
+                    const uint32_t xs = (uint32_t)((j + 2) % LY::NX), b = (uint32_t)(j & 1);
+                    ok = wait_all(&mbXfull[xs], (phX >> xs) & 1u);
+                    phX ^= 1u << xs;
+                    // an M-step's count MMA j, issued above after P(j) was written
+                    // (so after S(j) was read), precedes this MMA: no release needed
+                    if (!P.mstep) {
+                        if (ok) ok = wait_all(&mbSfree[b], (phSfree >> b) & 1u);
+                        phSfree ^= 1u << b;
+                    }
+                    tc::fence_after_sync();
+                    issue_scores(tmu + NT * b, xs);
+                    tc::mma_commit_w(&mbSfull[b]);
+                }
+                ti.advance(in, item.seq_hi);
             }
         } else {
             // this item's normalised counts of candidate c, this thread's chunks:
@@ -712,7 +723,7 @@ __global__ void __launch_bounds__(tc_threads<H>(), (KP <= 80 && H == 2 ? 2 : 1))
         for (int s = 0; s < LY::NX; ++s)
             if (xcopies[s] > 0u) tc::mbar_wait(&mbXfull[s], (xcopies[s] - 1u) & 1u, kWaitNs);
     // every MMA this CTA issued has completed (bounded) before its memory is freed
-    if (issuer && lane == 0) tc::mma_commit(&mbEnd);
+    if (issuer) tc::mma_commit_w(&mbEnd);  // the lane that issued the MMAs
     tc::mbar_wait(&mbEnd, 0u, kWaitNs);
     tc::fence_before_sync();
     __syncthreads();
@@ -741,16 +752,17 @@ __global__ void em_tc_reduce_kernel(const float *__restrict__ part_acc,
         const int mid = (lo + hi + 1) >> 1;
         if (inst[mid].cand_begin <= (int64_t)c) lo = mid; else hi = mid - 1;
     }
-    // group sums in group order, the loads of eight groups in flight at a time
-    // (adding the zero that pads the last batch changes no sum)
+    // group sums in group order, the loads of up to 48 groups in flight at a
+    // time (adding the zero that pads the last batch changes no sum)
     auto fold = [&](auto load, auto zero) {
+        constexpr int kBatch = 48;
         auto s = zero;
-        for (int g0 = 0; g0 < G; g0 += 8) {
-            decltype(zero) v[8];
+        for (int g0 = 0; g0 < G; g0 += kBatch) {
+            decltype(zero) v[kBatch];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = g0 + u < G ? load(g0 + u) : zero;
+            for (int u = 0; u < kBatch; ++u) v[u] = g0 + u < G ? load(g0 + u) : zero;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) s += v[u];
+            for (int u = 0; u < kBatch; ++u) s += v[u];
         }
         return s;
     };
