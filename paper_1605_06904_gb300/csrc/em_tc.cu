@@ -46,6 +46,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -491,8 +492,6 @@ __global__ void __launch_bounds__(tc_threads<H>(), (KP <= 80 && H == 2 ? 2 : 1))
             const bool zoops = in.gamma < 1.0;
             const float log_gamma = zoops ? logf((float)in.gamma) : 0.f;
             const float log_no = zoops ? log1pf(-(float)in.gamma) : 0.f;
-            float m = -INFINITY, Ssum = 0.f, Scmp = 0.f;
-            bool first = true;
             // a finished sequence's O is added to tot (scaled by o_inv) during the
             // next tile, before that tile's count MMA restarts O, so the wait for
             // the sequence's last count MMA overlaps the next tile's softmax
@@ -512,129 +511,134 @@ __global__ void __launch_bounds__(tc_threads<H>(), (KP <= 80 && H == 2 ? 2 : 1))
                 o_pend = false;
             };
             o_base = o_waited;  // every count MMA of earlier items was waited for
-            TileIt<NT> tcur;
-            tcur.start(in, item.seq_lo, item.seq_hi);
+            const uint32_t tS0 = tm + 32 * half + lane_base;  // this thread's columns of buffer 0
 
-            for (int i = 0; i < n; ++i) {
-                const uint32_t b = (uint32_t)(i & 1);
-                const uint32_t tS = tm + NT * b + 32 * half + lane_base;
-                if (ok) ok = tc::mbar_wait(&mbSfull[b], (phSfull >> b) & 1u, kWaitNs);
-                phSfull ^= 1u << b;
-                tc::fence_after_sync();
-
-                const int nvalid = min(NT, tcur.ns - tcur.j0);
-                const int nv = max(0, min(32, nvalid - 32 * half));  // valid l-mers of this half
-                float v[32];
-                tc::tmem_ld32(tS, v);
-                if (first) {
-                    if (careful) {  // the first tile's exact maximum
-                        const float mh = max_half(v, nv);
-                        m = row_reduce(mh, true);
-                    } else {
-                        // every score of the row lies in [top - 200, top], so
-                        // P = 2^(S - m) stays within [2^-100, 2^100]
-                        m = row_top - 100.f;
-                    }
-                }
-                const float s0 = Ssum, c0s = Scmp;
-                float add = exp_half(v, m, nv);
-                if (careful) {
-                    const float bigf = !(add <= 18446744073709551616.f) ? 1.f : 0.f;  // 2^64
-                    // both warps of the lane group take the same branch (named barriers)
-                    if (__any_sync(0xffffffffu, row_reduce(bigf, true) > 0.f)) {
-                        // redo the tile with m raised to its exact maximum
+            // The tile loop, compiled once per (M-step, careful) pair so that the
+            // common case (M-step, fixed reference maximum) carries no branch of
+            // the other three; sequences outside, their tiles inside.
+            auto run = [&](auto ms_t, auto cf_t) {
+                constexpr bool MS = decltype(ms_t)::value, CF = decltype(cf_t)::value;
+                int i = 0;  // tile of the item
+                for (int seq = item.seq_lo; seq < item.seq_hi; ++seq) {
+                    const int ns = in.seq_off[seq + 1] - in.seq_off[seq] - l + 1;  // starts
+                    const int ntl = (ns + NT - 1) / NT;
+                    // every score of a row lies in [top - 200, top] unless the CTA
+                    // is careful, so P = 2^(S - m) stays within [2^-100, 2^100]
+                    float m = CF ? -INFINITY : row_top - 100.f;
+                    float Ssum = 0.f, Scmp = 0.f;
+                    for (int q = 0; q < ntl; ++q, ++i) {
+                        const uint32_t b = (uint32_t)(i & 1);
+                        const uint32_t tS = tS0 + NT * b;
+                        if (ok) ok = tc::mbar_wait(&mbSfull[b], (phSfull >> b) & 1u, kWaitNs);
+                        phSfull ^= 1u << b;
+                        tc::fence_after_sync();
+                        // valid l-mers of this thread's half (only a last tile is partial)
+                        const int nv = q + 1 < ntl ? 32 : max(0, min(32, ns - q * NT - 32 * half));
+                        float v[32];
                         tc::tmem_ld32(tS, v);
-                        const float mh = max_half(v, nv);
-                        const float tmax = fmaxf(row_reduce(mh, true), m);
-                        const float sc = ex2(m - tmax);
-                        Ssum = s0 * sc;
-                        Scmp = c0s * sc;
-                        m = tmax;
-                        if (P.mstep && !first) {
-                            wait_o((uint32_t)i);  // O holds every count MMA issued so far
-                            tc::fence_after_sync();
+                        if constexpr (CF) {
+                            if (q == 0) m = row_reduce(max_half(v, nv), true);  // exact maximum
+                        }
+                        const float s0 = Ssum, c0s = Scmp;
+                        float add = exp_half(v, m, nv);
+                        if constexpr (CF) {
+                            const float bigf = !(add <= 18446744073709551616.f) ? 1.f : 0.f;  // 2^64
+                            // both warps of the lane group take the same branch (named barriers)
+                            if (__any_sync(0xffffffffu, row_reduce(bigf, true) > 0.f)) {
+                                // redo the tile with m raised to its exact maximum
+                                tc::tmem_ld32(tS, v);
+                                const float mh = max_half(v, nv);
+                                const float tmax = fmaxf(row_reduce(mh, true), m);
+                                const float sc = ex2(m - tmax);
+                                Ssum = s0 * sc;
+                                Scmp = c0s * sc;
+                                m = tmax;
+                                if (MS && q > 0) {
+                                    wait_o((uint32_t)i);  // O holds every count MMA issued so far
+                                    tc::fence_after_sync();
 #pragma unroll
-                            for (int r = 0; r < CPT; ++r) {
-                                const int c8 = 8 * (half + H * r);
-                                if (c8 < KP) {
-                                    float o[8];
-                                    tc::tmem_ld8(tO + lane_base + c8, o);
+                                    for (int r = 0; r < CPT; ++r) {
+                                        const int c8 = 8 * (half + H * r);
+                                        if (c8 < KP) {
+                                            float o[8];
+                                            tc::tmem_ld8(tO + lane_base + c8, o);
 #pragma unroll
-                                    for (int q = 0; q < 8; ++q) o[q] *= sc;
-                                    tc::tmem_st8(tO + lane_base + c8, o);
+                                            for (int e = 0; e < 8; ++e) o[e] *= sc;
+                                            tc::tmem_st8(tO + lane_base + c8, o);
+                                        }
+                                    }
                                 }
+                                add = exp_half(v, m, nv);
                             }
                         }
-                        add = exp_half(v, m, nv);
-                    }
-                }
-                kahan(Ssum, Scmp, add);
-                tc::fence_before_sync();
-                if (i + 2 < n && !P.mstep) tc::mbar_arrive(&mbSfree[b]);  // the issuer may overwrite S(i)
-
-                if (P.mstep) {
-                    // P over this thread's own score columns: hi of its 32 l-mers in
-                    // the first 16, lo in the last 16 (the count MMA of tile i-2,
-                    // which read the buffer's previous P, completed before S(i))
+                        kahan(Ssum, Scmp, add);
+                        tc::fence_before_sync();
+                        if constexpr (!MS) {
+                            if (i + 2 < n) tc::mbar_arrive(&mbSfree[b]);  // the issuer may overwrite S(i)
+                        } else {
+                            // P over this thread's own score columns: hi of its 32 l-mers
+                            // in the first 16, lo in the last 16 (the count MMA of tile
+                            // i-2, which read the buffer's previous P, completed before S(i))
 #pragma unroll
-                    for (int g = 0; g < 2; ++g) {
-                        uint32_t hi[8], lo[8];
+                            for (int g = 0; g < 2; ++g) {
+                                uint32_t hi[8], lo[8];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const float a0 = v[16 * g + 2 * q], a1 = v[16 * g + 2 * q + 1];
-                            const uint32_t h = pack_bf16(a0, a1);
-                            hi[q] = h;
-                            const float2 r = __fadd2_rn(
-                                make_float2(a0, a1), make_float2(-__uint_as_float(h << 16),
-                                                                 -__uint_as_float(h & 0xFFFF0000u)));
-                            lo[q] = pack_bf16(r.x, r.y);
+                                for (int e = 0; e < 8; ++e) {
+                                    const float a0 = v[16 * g + 2 * e], a1 = v[16 * g + 2 * e + 1];
+                                    const uint32_t h = pack_bf16(a0, a1);
+                                    hi[e] = h;
+                                    const float2 r = __fadd2_rn(
+                                        make_float2(a0, a1),
+                                        make_float2(-__uint_as_float(h << 16),
+                                                    -__uint_as_float(h & 0xFFFF0000u)));
+                                    lo[e] = pack_bf16(r.x, r.y);
+                                }
+                                tc::tmem_st8u(tS + 8 * g, hi);
+                                tc::tmem_st8u(tS + 16 + 8 * g, lo);
+                            }
+                            tc::tmem_wait_st();
+                            // count MMA i-1 complete (it read X(i-1), whose slot is
+                            // rebuilt below) before count MMA i can be issued: the
+                            // parity waits on mbO never fall two phases behind
+                            wait_o((uint32_t)i);
+                            if (o_pend) {  // the previous sequence ended with tile i-1
+                                tc::fence_after_sync();
+                                read_o();
+                            }
+                            tc::fence_before_sync();
+                            tc::mbar_arrive(&mbPfull);
                         }
-                        tc::tmem_st8u(tS + 8 * g, hi);
-                        tc::tmem_st8u(tS + 16 + 8 * g, lo);
+                        // one-hot tile of i+3 into the slot of tile i-1 (its MMAs are complete)
+                        if (i + LY::NX - 1 < n && tid == 0 && ok)
+                            copy_x(item.tile0 + i + LY::NX - 1, i + LY::NX - 1);
                     }
-                    tc::tmem_wait_st();
-                    // count MMA i-1 complete (it read X(i-1), whose slot is rebuilt
-                    // below) before count MMA i can be issued: the parity waits on
-                    // mbO never fall two phases behind
-                    wait_o((uint32_t)i);
-                    if (o_pend) {  // the previous sequence ended with tile i-1
-                        tc::fence_after_sync();
-                        read_o();
-                    }
-                    tc::fence_before_sync();
-                    tc::mbar_arrive(&mbPfull);
-                }
-                // one-hot tile of i+3 into the slot of tile i-1 (its MMAs are complete)
-                if (i + LY::NX - 1 < n && tid == 0 && ok)
-                    copy_x(item.tile0 + i + LY::NX - 1, i + LY::NX - 1);
-                first = false;
-                if (tcur.last()) {
-                    const float Sh = Ssum - Scmp;
-                    const float Sf = row_reduce(Sh, false);
+                    // the sequence's log-likelihood term and (M-step) the weight of its counts
+                    const float Sf = row_reduce(Ssum - Scmp, false);
                     float w = 1.f;  // posterior probability that the sequence holds a site
                     if (zoops) {
                         // ZOOPS: L_i = log[(1 - gamma) + (gamma / ns) sum_j e^r], in FP32
                         // (FP64 transcendentals are slow here)
-                        const float lg = log_gamma - logf((float)tcur.ns) +
-                                         (m + log2f(Sf)) * 0.69314718f;
+                        const float lg = log_gamma - logf((float)ns) + (m + log2f(Sf)) * 0.69314718f;
                         const float hi = fmaxf(log_no, lg), lo = fminf(log_no, lg);
                         const float Li = hi + log1pf(expf(lo - hi));
                         w = expf(lg - Li);
                         kahan(ll_s, ll_c, Li);
                     } else {
-                        kahan(ll_s, ll_c, (m + log2f(Sf)) * 0.69314718f - logf((float)tcur.ns));
+                        kahan(ll_s, ll_c, (m + log2f(Sf)) * 0.69314718f - logf((float)ns));
                     }
                     kahan(zs_s, zs_c, w);
-                    if (P.mstep) {
+                    if constexpr (MS) {
                         o_pend = true;  // read during the next tile or after the loop
                         o_inv = w / Sf;
                     }
-                    m = -INFINITY;
-                    Ssum = 0.f;
-                    Scmp = 0.f;
-                    first = true;
                 }
-                tcur.advance(in, item.seq_hi);
+            };
+            if (P.mstep) {
+                if (careful) run(std::true_type{}, std::true_type{});
+                else run(std::true_type{}, std::false_type{});
+            } else {
+                if (careful) run(std::false_type{}, std::true_type{});
+                else run(std::false_type{}, std::false_type{});
             }
             if (o_pend) {  // the item's last sequence
                 wait_o((uint32_t)n);
