@@ -17,14 +17,14 @@
 //   1. one thread copies the one-hot tile X [NT x 4l] into shared memory with a
 //      bulk asynchronous copy (the tiles depend only on the sequences and are
 //      built once per EM run, in the MMA operand layout, by em_xtiles_kernel);
-//   2. one thread issues S = W_hi X^T + W_lo X^T (M=128, N=NT, K=16*ceil(4l/16),
+//   2. one lane of the MMA warp issues S = W_hi X^T + W_lo X^T (M=128, N=NT, K=16*ceil(4l/16),
 //      FP32 accumulation in tensor memory; W split into BF16 hi + lo parts so
 //      the product carries ~16 mantissa bits of W);
 //   3. the threads of row i (32 l-mers each) read its scores S, add 2^(S - m) to a
 //      compensated running sum for the candidate (m a reference maximum, see
 //      below) and write P = 2^(S - m) as BF16 hi + lo parts over their own
 //      columns of S in tensor memory;
-//   4. one thread issues O += P_hi X + P_lo X (M=128, N=16*ceil(4l/16), K=NT)
+//   4. one lane of the MMA warp issues O += P_hi X + P_lo X (M=128, N=16*ceil(4l/16), K=NT)
 //      with P read from tensor memory and X in MN-major form from the same
 //      shared-memory tile.
 // The steps of consecutive tiles overlap (two score buffers in tensor memory,
@@ -242,7 +242,8 @@ __device__ __forceinline__ float max_half(const float (&v)[32], int nv) {
 // reference maximum m, keep their own compensated sums (added together through
 // shared memory at a sequence end), and each reads and accumulates the 8-column
 // chunks h, h + H, ... of the row's count columns.  Warp 4H issues the MMAs
-// (one elected thread), so issuing never stalls the softmax warps.
+// (the warp runs converged and one lane chosen by elect.sync issues each MMA
+// and commit), so issuing never stalls the softmax warps.
 //
 // Pipeline over the tiles j = 0 .. n-1 of an item, linked by mbarriers:
 //   issuer: S(0), S(1); then per j: [P(j) written] O (+)= P X(j);
