@@ -91,7 +91,9 @@ __device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, ui
 
 // The same three, executed by all 32 lanes of a warp: one lane chosen by
 // elect.sync issues the instruction, so the warp stays converged and every
-// operand (computed identically by all lanes) stays warp-uniform.
+// operand (computed identically by all lanes) stays warp-uniform.  Over the
+// full mask of a converged warp elect.sync chooses the same leader lane at
+// every call, so a commit tracks every MMA the warp issued before it.
 __device__ __forceinline__ void mma_bf16_w(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                            uint32_t idesc, uint32_t accumulate) {
     asm volatile(
