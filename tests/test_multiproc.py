@@ -58,3 +58,25 @@ def test_reference_arm_runs_on_rank0_only(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     args = argparse.Namespace(config=2, steps=1, warmup=0, ref_sample=10)
     assert bench.run_reference(args) == 0  # returns at once, without oracle work
+
+
+def test_reference_arm_line_on_cpu():
+    """The reference arm (the oracle on the host's cores) prints one JSON line
+    with the contract's keys; each step is the bounded sample it times."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1")
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "3", "--ref-trials", "1", "--ref-cands", "2"],
+                         capture_output=True, text=True, timeout=300, env=env, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "scores/s"
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    assert 0 < line["ms_per_step"] < line["ms_per_search_extrapolated"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["config"]["config_index"] == 5 and line["steps"] == 1 and line["warmup"] == 3
